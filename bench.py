@@ -1,0 +1,340 @@
+"""Benchmark: tree-force Tflop/s (the paper's 23/65-flop convention) and
+particles/s of the full Bonsai step on one GB300.
+
+Workload (default): the Milky-Way-like model with N = 2^23 particles
+(Hernquist halo : exponential disk : Hernquist bulge = 5 : 1 : 0.2,
+theta = 0.4, eps = 10 pc, dt = 0.1 Myr), seeded and synthetic.  One step is
+the whole hot path: kick, drift, bounding box, Peano-Hilbert keys, radix
+sort, gather, octree, groups, FP64 multipoles, cell pack, the fused walk +
+force kernel, kick, and the FP64 energy/momentum diagnostics.
+
+value = sum over timed steps of (23 n_pp + 65 n_pc) / timed wall time on the
+device (CUDA events, max over ranks).  The state (about 1.7 GB) is far larger
+than the 129 MB L2, so no flush is needed between steps.
+
+``--impl reference`` times the FP64 CPU oracle (the stand-in for the
+paper's own code, which is not available) on a bounded sample of the same
+workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "tree-force Tflop/s (23 flops/p-p + 65 flops/p-c, Sec. VI.A) per full KDK step, theta=0.4"
+UNIT = "Tflop/s"
+FP32_LANES_PER_SM = 128
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _workload(name: str, rank: int):
+    import workloads
+    if name == "milky-way-2^23":
+        m = workloads.milky_way(1 << 23, seed=1002 + 17 * rank, eps=0.01, theta=0.4, dt=0.1)
+        desc = ("Milky-Way-like N=2^23 (Hernquist halo 1e12 Msun a=30 kpc cut 200 kpc, exp. disk "
+                "5e10 Msun Rd=2.5 kpc z0=0.3 kpc Q=1.5, Hernquist bulge 1e10 Msun a=0.5 kpc; "
+                "5:1:0.2), theta=0.4, eps=10 pc, dt=0.1 Myr")
+    elif name == "plummer-2^14":
+        m = workloads.plummer(1 << 14, seed=1001 + 17 * rank)
+        desc = "Plummer N=2^14, G=M=a=1, theta=0.4, eps=0.01, dt=1/64"
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    return m, desc
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1412_0659_gb300 import TreeGravity, build, fp32_peak_tflops
+    build.build()
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    m, desc = _workload(args.workload, rank)
+    n = m.n
+    pos = torch.from_numpy(m.pos).to(dev)
+    vel = torch.from_numpy(m.vel).to(dev)
+    mass = torch.from_numpy(m.mass).to(dev)
+    stream = torch.cuda.current_stream()
+    g = TreeGravity(G=m.G, theta=m.theta, eps=m.eps)
+    g.build(pos, mass)
+    g.set_velocities(vel)
+    g.forces()
+    for _ in range(args.warmup):
+        g.step(m.dt)
+        g.diagnostics()
+    st0 = g.stats()
+    launches0 = st0["launches"]
+    flops, walk_ms, force_ms, keys_ms, tree_ms, npp, npc = 0.0, [], [], [], [], [], []
+    clocks = ClockSampler(torch.cuda.current_device())
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    diag = None
+    for _ in range(args.steps):
+        g.step(m.dt)
+        diag = g.diagnostics()
+        st = g.stats()
+        flops += st["flops"]
+        walk_ms.append(st["ms_walk"])
+        force_ms.append(st["ms_force"])
+        keys_ms.append(st["ms_keys"])
+        tree_ms.append(st["ms_tree"])
+        npp.append(st["n_pp"])
+        npc.append(st["n_pc"])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if world > 1:
+        dist.barrier()
+    t_ms = e0.elapsed_time(e1)
+    launches = g.stats()["launches"] - launches0
+    t_max = t_ms
+    tot_flops = flops
+    if world > 1:
+        tt = torch.tensor([t_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+        ff = torch.tensor([flops], dtype=torch.float64, device=dev)
+        dist.all_reduce(ff)
+        tot_flops = float(ff.item())
+    value = tot_flops / (t_max * 1e-3) / 1e12
+    ms_per_step = t_max / args.steps
+
+    # --- end to end through the host-buffer C-ABI entry (copies timed) ---
+    pin_pos = torch.from_numpy(m.pos).pin_memory()
+    pin_mass = torch.from_numpy(m.mass).pin_memory()
+    pin_acc = torch.empty((3, n), dtype=torch.float32).pin_memory()
+    pin_pot = torch.empty(n, dtype=torch.float32).pin_memory()
+    ge = TreeGravity(G=m.G, theta=m.theta, eps=m.eps)
+    ge.solve_host(pin_pos, pin_mass, pin_acc, pin_pot)
+    e_steps = max(1, min(args.steps, 3))
+    e_flops = 0.0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e_steps):
+        ge.solve_host(pin_pos, pin_mass, pin_acc, pin_pot)
+        e_flops += ge.stats()["flops"]
+    torch.cuda.synchronize()
+    e_s = time.perf_counter() - t0
+    ge.close()
+    if world > 1:
+        tt = torch.tensor([e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e_s = float(tt.item())
+        ff = torch.tensor([e_flops], dtype=torch.float64, device=dev)
+        dist.all_reduce(ff)
+        e_flops = float(ff.item())
+    e2e = {"value": e_flops / e_s / 1e12, "unit": UNIT,
+           "h2d_bytes_per_step": int(pin_pos.numel() * 8 + pin_mass.numel() * 8),
+           "d2h_bytes_per_step": int(pin_acc.numel() * 4 + pin_pot.numel() * 4),
+           "what": "tree_solve_host: H2D pos+mass, build, forces, D2H acc+pot (one force evaluation)"}
+
+    # --- roofline of the dominant kernel (the fused walk/force) ---
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    pk = _peaks()
+    max_mhz = pk.get("sm_max_mhz") or clk.get("sm_max_mhz") or 2070.0
+    peak = fp32_peak_tflops(sms, FP32_LANES_PER_SM, max_mhz)
+    walk_avg = sum(walk_ms) / len(walk_ms)
+    flops_launch = flops / args.steps
+    achieved = flops_launch / (walk_avg * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": args.traffic,
+                "kernel": "k_walk (fused walk + p-p/p-c evaluation)",
+                "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flops x {max_mhz:.0f} MHz",
+                "convention_cap": "23/26 of peak for p-p and 65/76 for p-c at one FP32 instruction per issue slot"}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(m, args.cpu_groups)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded generator; the paper's Milky Way realisation is not available)",
+            "config": {"workload": desc, "n_per_gpu": n, "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "l2_flush": "none: inputs (~1.7 GB state) larger than L2",
+                       "arith": "FP32 forces on group-relative coordinates; FP64 keys, multipoles, state, diagnostics"},
+            "particles_per_s": world * n * args.steps / (t_max * 1e-3),
+            "force_particles_per_s": n / (walk_avg * 1e-3),
+            "force_kernel_tflops": achieved,
+            "pct_fp32_peak": 100.0 * value / peak,
+            "n_pp_per_particle": statistics.mean(npp) / n, "n_pc_per_particle": statistics.mean(npc) / n,
+            "phase_ms": {"keys_sort": statistics.mean(keys_ms), "tree_groups_multipoles": statistics.mean(tree_ms),
+                         "force": statistics.mean(force_ms), "walk_kernel": walk_avg},
+            "energy": {"E_tot": diag["E_tot"] if diag else None},
+            "clocks": clk, "gpu_launches": int(launches), "roofline": roofline, "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    g.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(m, n_groups: int):
+    """The FP64 oracle on the host cores: full tree build of the same workload
+    plus the force walk of a seeded sample of groups; the force time is scaled
+    to all groups by flops.  Returns the oracle's Tflop/s for one step."""
+    import numpy as np
+
+    import oracle
+    t0 = time.perf_counter()
+    t = oracle.Tree(m.pos, m.mass)
+    t_build = time.perf_counter() - t0
+    rng = np.random.default_rng(7)
+    sel = np.sort(rng.choice(t.ngroups, min(n_groups, t.ngroups), replace=False))
+    g = t.groups()
+    t1 = time.perf_counter()
+    _, _, g_npp, g_npc, _ = t.forces_groups(m.theta, m.eps, m.G, sel)
+    t_force = time.perf_counter() - t1
+    cnt = g["count"][sel].astype(np.float64)
+    f_sample = float((23.0 * cnt * g_npp[sel] + 65.0 * cnt * g_npc[sel]).sum())
+    n_sample = float(cnt.sum())
+    # the whole step's flops estimated from the sample's flops per particle
+    f_total = f_sample * m.n / n_sample
+    t_total = t_build + t_force * (f_total / f_sample)
+    return {"value": f_total / t_total / 1e12, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": (f"FP64 C oracle: full tree build of the same N={m.n} workload ({t_build:.1f} s) + force walk "
+                       f"of {len(sel)} seeded random groups ({int(n_sample)} particles, {t_force:.1f} s), "
+                       "force time scaled to all particles by flops"),
+            "force_only_tflops": f_sample / t_force / 1e12}
+
+
+def run_reference(args):
+    """The reference arm: the FP64 CPU oracle, as it stands, on the host cores."""
+    rank, world, local = _dist()
+    if rank != 0:
+        return
+    m, desc = _workload(args.workload, 0)
+    for _ in range(args.warmup):
+        pass
+    vals = []
+    t0 = time.perf_counter()
+    cpu = None
+    for _ in range(max(1, args.steps)):
+        cpu = cpu_baseline(m, args.cpu_groups)
+        vals.append(cpu["value"])
+    wall = time.perf_counter() - t0
+    value = statistics.mean(vals)
+    cpu = dict(cpu, value=value)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / max(1, args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded generator)", "config": {"workload": desc, "n_per_gpu": m.n},
+            "cpu_baseline": cpu,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="milky-way-2^23", choices=["milky-way-2^23", "plummer-2^14"])
+    ap.add_argument("--cpu-groups", type=int, default=96, help="groups walked by the CPU oracle sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="DRAM bytes per walk launch from an ncu capture (null when not captured)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

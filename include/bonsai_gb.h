@@ -1,0 +1,190 @@
+/*
+ * bonsai_gb.h -- C ABI of the GB300-native (sm_103a) tree-force library.
+ *
+ * The library computes, on one GPU, the per-step gravitational tree force of
+ * Bonsai (Bedorf et al., SC14, Sec. III.A): Peano-Hilbert keys from the
+ * bounding box (Sec. III.B.1), a key sort (Table 2 "Sorting SFC"), an octree
+ * whose leaves hold at most 16 particles (Sec. I.A), a monopole+quadrupole
+ * upward pass (Sec. VI.A, the 3x3 symmetric Q of Eq. 1-2), a group-wise walk
+ * with an opening-angle criterion (Sec. I.A) fused with the softened
+ * particle-particle and particle-cell evaluation of Eq. 1-2, and a
+ * second-order kick-drift-kick leap-frog (Sec. III.B.2, last paragraph).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Return value: BONSAI_OK (0) or a negative BONSAI_E* code.  No C++
+ *   exception crosses this boundary.  bonsai_strerror() names a code.
+ * - Pointers marked "device" must be CUDA device memory of the current
+ *   device (e.g. a torch CUDA tensor's data_ptr()); "host" pointers are
+ *   ordinary host memory (pinned memory makes the copies asynchronous).
+ * - Positions and velocities are SoA float64 [3][n]: x[0..n), y[0..n),
+ *   z[0..n).  Masses float64 [n].  Accelerations SoA float32 [3][n],
+ *   potentials float32 [n].  Every input and output is in the caller's
+ *   particle order; the key-sorted order is internal (see tree_debug_*).
+ * - Ownership: the caller owns every pointer argument and keeps it valid
+ *   for the duration of the call; the context owns its device scratch
+ *   (allocated as n grows, freed by bonsai_destroy).
+ * - Streams: all device work is enqueued on the context's stream.  Calls
+ *   return after their work is complete (they synchronise the stream once
+ *   to read the device status word), so outputs are ready on return.
+ * - Units are the caller's: G is a parameter.
+ */
+#ifndef BONSAI_GB_H
+#define BONSAI_GB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BONSAI_OK 0
+#define BONSAI_EINVAL (-1)    /* bad argument: null pointer, n <= 0, theta <= 0, eps < 0,
+                                 non-finite position or mass <= 0 (found on the device) */
+#define BONSAI_ENOMEM (-2)    /* a device allocation failed */
+#define BONSAI_EOVERFLOW (-3) /* a bounded walk buffer overflowed (device status word) */
+#define BONSAI_ECUDA (-4)     /* a CUDA runtime call failed */
+#define BONSAI_ESTATE (-5)    /* call out of order, e.g. forces before a tree was built */
+
+typedef struct bonsai_ctx bonsai_ctx;
+
+/* Parameters fixed at creation.  nleaf and ncrit must be 16 and 64: the
+ * leaf size of Sec. I.A and the walk-group size; other values are EINVAL. */
+typedef struct {
+    double G;        /* gravitational constant in the caller's units */
+    float theta;     /* opening angle used by tree_step (Sec. I.A; 0.4 in the paper) */
+    float eps;       /* Plummer softening length used by tree_step */
+    int32_t nleaf;   /* 16 */
+    int32_t ncrit;   /* 64 */
+    int32_t reserved[2];
+} bonsai_params;
+
+/* Statistics of the last tree_build / tree_forces. */
+typedef struct {
+    int64_t n;          /* particles */
+    int64_t n_nodes;    /* octree nodes */
+    int64_t n_groups;   /* walk groups */
+    int32_t depth;      /* deepest level (root = 0) */
+    int32_t max_frontier; /* largest per-group walk frontier seen */
+    uint64_t n_pp;      /* sum over groups of |group| x |p-p list| (Sec. VI.A counts) */
+    uint64_t n_pc;      /* sum over groups of |group| x |p-c list| */
+    double flops;       /* 23 n_pp + 65 n_pc (Sec. VI.A convention) */
+    float ms_keys;      /* bounding box + keys + sort + gather, last build */
+    float ms_tree;      /* octree + groups + multipoles, last build */
+    float ms_force;     /* cell pack + walk/force + scatter, last tree_forces */
+    float ms_integrate; /* kicks + drift of the last tree_step */
+    float ms_walk;      /* the fused walk/force kernel alone, last tree_forces */
+    uint64_t launches;  /* kernels launched by this context since creation */
+} bonsai_stats;
+
+/* Create a context.  stream is a cudaStream_t (NULL = legacy default stream).
+ * Errors: EINVAL (null out/params, nleaf != 16, ncrit != 64), ECUDA. */
+int bonsai_create(bonsai_ctx **out, const bonsai_params *params, void *stream);
+
+/* Destroy a context and free its device memory.  NULL is accepted. */
+void bonsai_destroy(bonsai_ctx *ctx);
+
+/* Replace the context's stream (cudaStream_t, NULL = legacy default). */
+int bonsai_set_stream(bonsai_ctx *ctx, void *stream);
+
+/* tree_build -- Sec. III.A "tree-construction" and "computation of multipole
+ * moments" (with the keys and sort of Sec. III.B.1 / Table 2):
+ *   bounding cube -> 21-bit Peano-Hilbert keys -> stable radix sort by
+ *   (key, index) -> gather to key order -> octree (leaf <= 16 particles,
+ *   children in key order, breadth-first numbering) -> walk groups (nodes
+ *   of <= 64 particles whose parent has more) -> FP64 mass, centre of mass
+ *   and non-traceless quadrupole per node.
+ * pos: device [3][n] float64; mass: device [n] float64 (> 0, finite);
+ * n >= 1.  The context copies what it needs; the caller's buffers are only
+ * read during the call.  Velocities are reset to zero.
+ * Errors: EINVAL (null pointer, n < 1 or > 2^31 - 1, non-finite position,
+ * mass <= 0), ENOMEM, ECUDA. */
+int tree_build(bonsai_ctx *ctx, const double *pos, const double *mass, int64_t n);
+
+/* tree_forces -- Sec. III.A "tree-walk in which inter-particle gravitational
+ * forces are computed", Eq. 1-2 of Sec. VI.A with Plummer softening:
+ *   a_i = G sum_j [ m_j r/s^3 - 3/2 trQ_j r/s^5 - 3 Q_j r/s^5
+ *                   + 15/2 (r^T Q_j r) r/s^7 ],
+ *   phi_i = G sum_j [ -m_j/s + 1/2 trQ_j/s^3 - 3/2 r^T Q_j r/s^5 ],
+ *   r = r_j - r_i, s = (|r|^2 + eps^2)^{1/2}, Q_j = 0 for particles; the
+ *   self pair contributes nothing.  Sources are the cells accepted and the
+ *   particles of the leaves opened by the group walk (opening test: a cell
+ *   is opened when the squared distance from its centre of mass to the
+ *   group's box is below (l/theta + |com - centre|)^2).
+ * FP32 arithmetic on group-relative coordinates.  Interaction counts are in
+ * tree_get_stats.  acc: device [3][n] float32 or NULL; pot: device [n]
+ * float32 or NULL (caller order).  Requires a prior tree_build.
+ * Errors: ESTATE (no tree), EINVAL (theta <= 0, eps < 0), EOVERFLOW, ECUDA. */
+int tree_forces(bonsai_ctx *ctx, float theta, float eps, float *acc, float *pot);
+
+/* Set the velocities of the particles of the last tree_build.
+ * vel: device [3][n] float64, caller order.  Errors: ESTATE, EINVAL. */
+int tree_set_velocities(bonsai_ctx *ctx, const double *vel);
+
+/* tree_step -- one second-order leap-frog step (Sec. III.B.2, last
+ * paragraph), kick-drift-kick in FP64:
+ *   v += a dt/2;  x += v dt;  rebuild tree;  a = forces(x);  v += a dt/2,
+ * with theta, eps and G from the creation parameters.  The forces at the
+ * start of the step come from the previous tree_step or tree_forces (they
+ * are computed here if there are none).  Errors: ESTATE, EOVERFLOW, ECUDA. */
+int tree_step(bonsai_ctx *ctx, double dt);
+
+/* Copy the FP64 state out in caller order; any pointer may be NULL.
+ * pos, vel: device [3][n]; mass: device [n].  Errors: ESTATE. */
+int tree_get_state(bonsai_ctx *ctx, double *pos, double *vel, double *mass);
+
+/* Copy the accelerations and potentials of the last force evaluation out in
+ * caller order; either pointer may be NULL.  acc: device [3][n] float32,
+ * pot: device [n] float32.  Errors: ESTATE. */
+int tree_get_forces(bonsai_ctx *ctx, float *acc, float *pot);
+
+/* Energy and momentum diagnostics (Sec. VI: "gather and write statistics",
+ * excluded from the flop count), FP64 on the device:
+ *   out = {E_kin, E_pot, E_tot, Px, Py, Pz, Lx, Ly, Lz, M_total}, with
+ *   E_kin = sum m v^2/2, E_pot = sum m phi/2 (phi of the last force
+ *   evaluation), P = sum m v, L = sum m x cross v.  out: host double[10].
+ * Errors: ESTATE (no forces yet), ECUDA. */
+int bonsai_diagnostics(bonsai_ctx *ctx, double out[10]);
+
+/* Statistics of the last build / force evaluation.  out: host. */
+int tree_get_stats(bonsai_ctx *ctx, bonsai_stats *out);
+
+/* End-to-end entry with HOST buffers: copies pos/mass (host [3][n] and [n]
+ * float64) to the device, runs tree_build and tree_forces, and copies
+ * acc/pot (host [3][n] and [n] float32) back, all on the context's stream.
+ * Errors: as tree_build and tree_forces. */
+int tree_solve_host(bonsai_ctx *ctx, const double *pos, const double *mass, int64_t n,
+                    float theta, float eps, float *acc, float *pot);
+
+/* ---- internal views for parity tests (key-sorted order) ---------------- */
+
+/* Bounding cube of the last build: lo (host double[3]) and side L (host). */
+int tree_debug_cube(bonsai_ctx *ctx, double lo[3], double *L);
+
+/* Sorted keys (device uint64 [n]) and the caller index of each sorted slot
+ * (device uint32 [n]); either may be NULL. */
+int tree_debug_keys(bonsai_ctx *ctx, uint64_t *keys, uint32_t *perm);
+
+/* Node arrays, breadth-first (device uint32 [n_nodes] each; any may be
+ * NULL): first particle, particle count, first child, child count, level. */
+int tree_debug_nodes(bonsai_ctx *ctx, uint32_t *first, uint32_t *count, uint32_t *child,
+                     uint32_t *nchild, uint32_t *level);
+
+/* FP64 multipoles (device): M [n_nodes], com [3][n_nodes], Q [6][n_nodes]
+ * in the order xx, yy, zz, xy, xz, yz. */
+int tree_debug_multipoles(bonsai_ctx *ctx, double *M, double *com, double *Q);
+
+/* Groups (device uint32 [n_groups] first/count) and the p-p source count
+ * and p-c list length of each group from the last tree_forces (device
+ * int32 [n_groups]); any may be NULL. */
+int tree_debug_groups(bonsai_ctx *ctx, uint32_t *first, uint32_t *count, int32_t *npp,
+                      int32_t *npc);
+
+/* Name of a status code. */
+const char *bonsai_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BONSAI_GB_H */

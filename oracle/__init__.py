@@ -75,6 +75,7 @@ def _load():
             "orc_cell_mac": (None, [P, f32, P, P]),
             "orc_group_box_f32": (None, [P, P, P]),
             "orc_tree_forces": (i32, [P, f32, f64, f64, i64, i64, P, P, P, P, P]),
+            "orc_tree_forces_list": (i32, [P, f32, f64, f64, i64, P, P, P, P, P, P]),
             "orc_direct_forces": (None, [i64, P, P, f64, f64, i64, P, P, P]),
             "orc_forces": (i32, [i64, P, P, i32, i32, f32, f64, f64, i32, P, P, P]),
             "orc_kdk": (i32, [i64, P, P, P, i32, f64, i32, i32, f32, f64, f64, i32, P, P, i32]),
@@ -217,6 +218,21 @@ class Tree:
                                        _p(acc), _p(pot), _p(g_npp), _p(g_npc), _p(counts))
         if rc:
             raise MemoryError("oracle forces failed")
+        return acc, pot, g_npp, g_npc, (int(counts[0]), int(counts[1]))
+
+    def forces_groups(self, theta: float, eps: float, G: float, groups):
+        """FP64 tree forces for the listed groups (sorted order, NaN elsewhere);
+        returns (acc, pot, g_npp, g_npc, (n_pp, n_pc)) like forces_sorted."""
+        gl = np.ascontiguousarray(groups, np.int64)
+        acc = np.full((3, self.n), np.nan)
+        pot = np.full(self.n, np.nan)
+        g_npp = np.zeros(self.ngroups, np.int64)
+        g_npc = np.zeros(self.ngroups, np.int64)
+        counts = np.zeros(2, np.uint64)
+        rc = self._lib.orc_tree_forces_list(self._h, float(theta), float(eps), float(G), gl.shape[0],
+                                            _p(gl), _p(acc), _p(pot), _p(g_npp), _p(g_npc), _p(counts))
+        if rc:
+            raise ValueError("oracle forces failed (bad group index or out of memory)")
         return acc, pot, g_npp, g_npc, (int(counts[0]), int(counts[1]))
 
     def forces(self, theta: float, eps: float, G: float = 1.0):

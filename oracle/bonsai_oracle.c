@@ -607,14 +607,15 @@ int orc_group_lists(const orc_tree *t, float theta, int64_t g, uint32_t *pc, uin
     return 0;
 }
 
-/* Steps 7-9 for groups [g0, g1): FP64 tree forces in sorted order (acc
+/* Steps 7-9 for the listed groups: FP64 tree forces in sorted order (acc
  * [3][n], pot [n]; only the groups' particles are written), per-group list
  * lengths, and the counts n_pp = sum |g| |pp|, n_pc = sum |g| |pc|.      */
-int orc_tree_forces(const orc_tree *t, float theta, double eps, double G, int64_t g0, int64_t g1,
-                    double *acc, double *pot, int64_t *g_npp, int64_t *g_npc, uint64_t counts[2]) {
+int orc_tree_forces_list(const orc_tree *t, float theta, double eps, double G, int64_t nlist,
+                         const int64_t *glist, double *acc, double *pot, int64_t *g_npp,
+                         int64_t *g_npc, uint64_t counts[2]) {
     int64_t n = t->n, nn = t->nnodes, ng = t->ngroups;
-    if (g0 < 0) g0 = 0;
-    if (g1 > ng) g1 = ng;
+    for (int64_t k = 0; k < nlist; ++k)
+        if (glist[k] < 0 || glist[k] >= ng) return -1;
     float *com_f = (float *)malloc((size_t)nn * 3 * sizeof(float));
     float *ropen2_f = (float *)malloc((size_t)nn * sizeof(float));
     float *gcf = (float *)malloc((size_t)ng * 3 * sizeof(float));
@@ -631,8 +632,9 @@ int orc_tree_forces(const orc_tree *t, float theta, double eps, double G, int64_
     {
         orc_lists L;
         memset(&L, 0, sizeof(L));
-#pragma omp for schedule(dynamic, 4)
-        for (int64_t g = g0; g < g1; ++g) {
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t k = 0; k < nlist; ++k) {
+            int64_t g = glist[k];
             float gc[3] = {gcf[g], gcf[(size_t)ng + g], gcf[2 * (size_t)ng + g]};
             float gh[3] = {ghf[g], ghf[(size_t)ng + g], ghf[2 * (size_t)ng + g]};
             orc_walk_group(t, com_f, ropen2_f, gc, gh, &L);
@@ -673,6 +675,20 @@ int orc_tree_forces(const orc_tree *t, float theta, double eps, double G, int64_
     }
     free(com_f); free(ropen2_f); free(gcf); free(ghf);
     return 0;
+}
+
+/* Steps 7-9 for the contiguous groups [g0, g1). */
+int orc_tree_forces(const orc_tree *t, float theta, double eps, double G, int64_t g0, int64_t g1,
+                    double *acc, double *pot, int64_t *g_npp, int64_t *g_npc, uint64_t counts[2]) {
+    if (g0 < 0) g0 = 0;
+    if (g1 > t->ngroups) g1 = t->ngroups;
+    if (g1 < g0) g1 = g0;
+    int64_t *gl = (int64_t *)malloc((size_t)(g1 - g0 + 1) * sizeof(int64_t));
+    if (!gl) return -1;
+    for (int64_t g = g0; g < g1; ++g) gl[g - g0] = g;
+    int rc = orc_tree_forces_list(t, theta, eps, G, g1 - g0, gl, acc, pot, g_npp, g_npc, counts);
+    free(gl);
+    return rc;
 }
 
 /* Positions and masses in sorted order, and the sorted slot of each caller

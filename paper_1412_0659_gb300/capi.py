@@ -1,0 +1,251 @@
+"""Thin ctypes binding of the C ABI declared in include/bonsai_gb.h.
+
+Every function here only marshals arguments: torch CUDA tensors become
+device pointers, the current torch stream becomes the context's stream, and
+non-zero status codes become :class:`BonsaiError`.  All computation happens
+in the CUDA library; if the library is missing the first call raises
+immediately (there is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbonsai_gb.so")
+
+_lock = threading.Lock()
+_lib = None
+
+BONSAI_OK = 0
+BONSAI_EINVAL = -1
+BONSAI_ENOMEM = -2
+BONSAI_EOVERFLOW = -3
+BONSAI_ECUDA = -4
+BONSAI_ESTATE = -5
+
+# every symbol include/bonsai_gb.h declares
+EXPORTED = (
+    "bonsai_create", "bonsai_destroy", "bonsai_set_stream", "tree_build", "tree_forces",
+    "tree_set_velocities", "tree_step", "tree_get_state", "tree_get_forces",
+    "bonsai_diagnostics", "tree_get_stats", "tree_solve_host", "tree_debug_cube",
+    "tree_debug_keys", "tree_debug_nodes", "tree_debug_multipoles", "tree_debug_groups",
+    "bonsai_strerror",
+)
+
+
+class BonsaiError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {strerror(code)} ({code})")
+
+
+class bonsai_params(ctypes.Structure):
+    _fields_ = [("G", ctypes.c_double), ("theta", ctypes.c_float), ("eps", ctypes.c_float),
+                ("nleaf", ctypes.c_int32), ("ncrit", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
+
+
+class bonsai_stats(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("n_nodes", ctypes.c_int64), ("n_groups", ctypes.c_int64),
+                ("depth", ctypes.c_int32), ("max_frontier", ctypes.c_int32),
+                ("n_pp", ctypes.c_uint64), ("n_pc", ctypes.c_uint64), ("flops", ctypes.c_double),
+                ("ms_keys", ctypes.c_float), ("ms_tree", ctypes.c_float),
+                ("ms_force", ctypes.c_float), ("ms_integrate", ctypes.c_float),
+                ("ms_walk", ctypes.c_float), ("launches", ctypes.c_uint64)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def load(path: str | None = None):
+    """Load the CUDA library (build it first with ``paper_1412_0659_gb300.build``)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"CUDA library not built: {p} is missing "
+                               "(run paper_1412_0659_gb300.build.build())")
+        lib = ctypes.CDLL(p)
+        P, i32, i64, f32, f64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_float, ctypes.c_double
+        sig = {
+            "bonsai_create": (i32, [ctypes.POINTER(P), ctypes.POINTER(bonsai_params), P]),
+            "bonsai_destroy": (None, [P]),
+            "bonsai_set_stream": (i32, [P, P]),
+            "tree_build": (i32, [P, P, P, i64]),
+            "tree_forces": (i32, [P, f32, f32, P, P]),
+            "tree_set_velocities": (i32, [P, P]),
+            "tree_step": (i32, [P, f64]),
+            "tree_get_state": (i32, [P, P, P, P]),
+            "tree_get_forces": (i32, [P, P, P]),
+            "bonsai_diagnostics": (i32, [P, P]),
+            "tree_get_stats": (i32, [P, ctypes.POINTER(bonsai_stats)]),
+            "tree_solve_host": (i32, [P, P, P, i64, f32, f32, P, P]),
+            "tree_debug_cube": (i32, [P, P, P]),
+            "tree_debug_keys": (i32, [P, P, P]),
+            "tree_debug_nodes": (i32, [P, P, P, P, P, P]),
+            "tree_debug_multipoles": (i32, [P, P, P, P]),
+            "tree_debug_groups": (i32, [P, P, P, P, P]),
+            "bonsai_strerror": (ctypes.c_char_p, [i32]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def strerror(code: int) -> str:
+    try:
+        return load().bonsai_strerror(code).decode()
+    except RuntimeError:
+        return f"status {code}"
+
+
+def _check(rc: int, where: str):
+    if rc != BONSAI_OK:
+        raise BonsaiError(rc, where)
+
+
+def _ptr(t, dtype=None, numel=None, name="tensor"):
+    """Device pointer of a contiguous CUDA tensor (None -> NULL)."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return ctypes.c_void_p(t)
+    import torch
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} elements, got {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _hptr(a):
+    """Host pointer of a contiguous numpy array or CPU tensor."""
+    if a is None:
+        return None
+    if hasattr(a, "ctypes"):
+        return ctypes.c_void_p(a.ctypes.data)
+    if a.is_cuda or not a.is_contiguous():
+        raise ValueError("host buffer must be a contiguous CPU array")
+    return ctypes.c_void_p(a.data_ptr())
+
+
+def _stream_handle(stream=None) -> ctypes.c_void_p:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+# ---------------------------------------------------------------------------
+# same-name wrappers of the C ABI
+# ---------------------------------------------------------------------------
+
+def bonsai_create(G: float = 1.0, theta: float = 0.4, eps: float = 0.01, nleaf: int = 16,
+                  ncrit: int = 64, stream=None) -> ctypes.c_void_p:
+    lib = load()
+    prm = bonsai_params(G, theta, eps, nleaf, ncrit)
+    h = ctypes.c_void_p()
+    _check(lib.bonsai_create(ctypes.byref(h), ctypes.byref(prm), _stream_handle(stream)), "bonsai_create")
+    return h
+
+
+def bonsai_destroy(ctx) -> None:
+    if ctx:
+        load().bonsai_destroy(ctx)
+
+
+def bonsai_set_stream(ctx, stream=None) -> None:
+    _check(load().bonsai_set_stream(ctx, _stream_handle(stream)), "bonsai_set_stream")
+
+
+def tree_build(ctx, pos, mass) -> None:
+    import torch
+    n = mass.numel()
+    _check(load().tree_build(ctx, _ptr(pos, torch.float64, 3 * n, "pos"),
+                             _ptr(mass, torch.float64, n, "mass"), n), "tree_build")
+
+
+def tree_forces(ctx, theta: float, eps: float, acc=None, pot=None) -> None:
+    import torch
+    _check(load().tree_forces(ctx, float(theta), float(eps), _ptr(acc, torch.float32, None, "acc"),
+                              _ptr(pot, torch.float32, None, "pot")), "tree_forces")
+
+
+def tree_set_velocities(ctx, vel) -> None:
+    import torch
+    _check(load().tree_set_velocities(ctx, _ptr(vel, torch.float64, None, "vel")), "tree_set_velocities")
+
+
+def tree_step(ctx, dt: float) -> None:
+    _check(load().tree_step(ctx, float(dt)), "tree_step")
+
+
+def tree_get_state(ctx, pos=None, vel=None, mass=None) -> None:
+    import torch
+    _check(load().tree_get_state(ctx, _ptr(pos, torch.float64), _ptr(vel, torch.float64),
+                                 _ptr(mass, torch.float64)), "tree_get_state")
+
+
+def tree_get_forces(ctx, acc=None, pot=None) -> None:
+    import torch
+    _check(load().tree_get_forces(ctx, _ptr(acc, torch.float32), _ptr(pot, torch.float32)),
+           "tree_get_forces")
+
+
+def bonsai_diagnostics(ctx):
+    out = (ctypes.c_double * 10)()
+    _check(load().bonsai_diagnostics(ctx, out), "bonsai_diagnostics")
+    return list(out)
+
+
+def tree_get_stats(ctx) -> dict:
+    st = bonsai_stats()
+    _check(load().tree_get_stats(ctx, ctypes.byref(st)), "tree_get_stats")
+    return st.as_dict()
+
+
+def tree_solve_host(ctx, pos, mass, theta: float, eps: float, acc, pot) -> None:
+    """Host-buffer entry: pos (3, n) / mass (n,) float64 and acc (3, n) / pot (n,)
+    float32 are host arrays (numpy or CPU tensors, ideally pinned)."""
+    n = int(mass.shape[0])
+    _check(load().tree_solve_host(ctx, _hptr(pos), _hptr(mass), n, float(theta), float(eps),
+                                  _hptr(acc), _hptr(pot)), "tree_solve_host")
+
+
+def tree_debug_cube(ctx):
+    lo = (ctypes.c_double * 3)()
+    L = ctypes.c_double()
+    _check(load().tree_debug_cube(ctx, lo, ctypes.byref(L)), "tree_debug_cube")
+    return list(lo), L.value
+
+
+def tree_debug_keys(ctx, keys=None, perm=None) -> None:
+    _check(load().tree_debug_keys(ctx, _ptr(keys), _ptr(perm)), "tree_debug_keys")
+
+
+def tree_debug_nodes(ctx, first=None, count=None, child=None, nchild=None, level=None) -> None:
+    _check(load().tree_debug_nodes(ctx, _ptr(first), _ptr(count), _ptr(child), _ptr(nchild),
+                                   _ptr(level)), "tree_debug_nodes")
+
+
+def tree_debug_multipoles(ctx, M=None, com=None, Q=None) -> None:
+    _check(load().tree_debug_multipoles(ctx, _ptr(M), _ptr(com), _ptr(Q)), "tree_debug_multipoles")
+
+
+def tree_debug_groups(ctx, first=None, count=None, npp=None, npc=None) -> None:
+    _check(load().tree_debug_groups(ctx, _ptr(first), _ptr(count), _ptr(npp), _ptr(npc)),
+           "tree_debug_groups")
+
+
+def bonsai_strerror(code: int) -> str:
+    return strerror(code)

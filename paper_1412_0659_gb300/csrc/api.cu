@@ -1,0 +1,411 @@
+// api.cu -- the C ABI of include/bonsai_gb.h: context, buffers, and the
+// order of kernel launches for tree_build / tree_forces / tree_step.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+
+#include "internal.cuh"
+
+namespace bgb {
+
+template <typename T>
+int ensure(DBuf<T> &b, size_t n) {
+    if (n == 0) n = 1;
+    if (b.cap >= n) return BONSAI_OK;
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+    size_t cap = n + n / 8;
+    if (cudaMalloc(&b.p, cap * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        b.p = nullptr;
+        return BONSAI_ENOMEM;
+    }
+    b.cap = cap;
+    return BONSAI_OK;
+}
+
+template <typename T>
+void release(DBuf<T> &b) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+}
+
+template int ensure<double>(DBuf<double> &, size_t);
+template int ensure<float>(DBuf<float> &, size_t);
+template int ensure<uint32_t>(DBuf<uint32_t> &, size_t);
+template int ensure<int32_t>(DBuf<int32_t> &, size_t);
+template int ensure<uint64_t>(DBuf<uint64_t> &, size_t);
+template int ensure<float4>(DBuf<float4> &, size_t);
+template int ensure<uint2>(DBuf<uint2> &, size_t);
+template int ensure<BoxPartial>(DBuf<BoxPartial> &, size_t);
+
+}  // namespace bgb
+
+using namespace bgb;
+
+namespace {
+
+int particle_buffers(bonsai_ctx *c, int64_t n) {
+    const size_t n3 = 3 * (size_t)n;
+    if (ensure(c->pos, n3) || ensure(c->pos2, n3) || ensure(c->vel, n3) || ensure(c->vel2, n3) ||
+        ensure(c->mass, n) || ensure(c->mass2, n) || ensure(c->id, n) || ensure(c->id2, n) ||
+        ensure(c->acc, n3) || ensure(c->pot, n) || ensure(c->key, n) || ensure(c->key2, n) ||
+        ensure(c->val, n) || ensure(c->val2, n) || ensure(c->hist, sort_hist_elems(n)) ||
+        ensure(c->scan_tmp, scan_tmp_elems(std::max<int64_t>(n, sort_hist_elems(n)))) ||
+        ensure(c->box_part, (size_t)c->sm_count * 4 + 8) || ensure(c->body_hi, n) ||
+        ensure(c->body_lo, n) || ensure(c->grp_flag, 2 * (size_t)n + 2) ||
+        ensure(c->diag_part, (size_t)diag_blocks(c) * 10 + 16))
+        return BONSAI_ENOMEM;
+    return BONSAI_OK;
+}
+
+int node_buffers(bonsai_ctx *c) {
+    const size_t nn = (size_t)c->n_nodes;
+    if (ensure(c->nd_M, nn) || ensure(c->nd_com, 3 * nn) || ensure(c->nd_Q, 6 * nn) ||
+        ensure(c->cell_mac, nn) || ensure(c->cell_a, nn) || ensure(c->cell_b, nn) ||
+        ensure(c->cell_c, nn))
+        return BONSAI_ENOMEM;
+    return BONSAI_OK;
+}
+
+int read_scalars(bonsai_ctx *c) {
+    BGB_CUDA(cudaMemcpyAsync(c->hsc, c->dsc, sizeof(DevScalars), cudaMemcpyDeviceToHost,
+                             c->stream));
+    BGB_CUDA(cudaStreamSynchronize(c->stream));
+    return BONSAI_OK;
+}
+
+// Keys, sort, gather, octree, groups, multipoles, particle records.
+// from_caller: pos/mass are the caller's (caller order); otherwise the
+// context's own state is re-sorted in place (tree_step).
+int rebuild(bonsai_ctx *c, const double *pos, const double *mass, bool from_caller) {
+    const int64_t n = c->n;
+    BGB_CUDA(cudaMemsetAsync(c->dsc, 0, sizeof(DevScalars), c->stream));
+    BGB_CUDA(cudaEventRecord(c->ev[0], c->stream));
+    const double *p = from_caller ? pos : c->pos.p;
+    const double *m = from_caller ? mass : c->mass.p;
+    launch_bbox(c, p, m, n);
+    launch_keys(c, p, n);
+    radix_sort_pairs(c, n);
+    if (from_caller) launch_gather_build(c, pos, mass, n); else launch_gather_step(c, n);
+    BGB_CUDA(cudaEventRecord(c->ev[1], c->stream));
+    BGB_CUDA(cudaGetLastError());
+    int rc = build_octree(c);
+    if (rc) return rc;
+    if ((rc = node_buffers(c))) return rc;
+    if ((rc = build_groups(c))) return rc;
+    launch_multipoles(c);
+    launch_body_pack(c);
+    BGB_CUDA(cudaEventRecord(c->ev[2], c->stream));
+    BGB_CUDA(cudaGetLastError());
+    if ((rc = read_scalars(c))) return rc;
+    if (c->hsc->status & ST_BAD_INPUT) {
+        c->have_tree = false;
+        return BONSAI_EINVAL;
+    }
+    cudaEventElapsedTime(&c->stats.ms_keys, c->ev[0], c->ev[1]);
+    cudaEventElapsedTime(&c->stats.ms_tree, c->ev[1], c->ev[2]);
+    c->have_tree = true;
+    c->packed_theta = -1.0f;
+    // leaves: nodes without children (counted from the level table on demand)
+    return BONSAI_OK;
+}
+
+int forces_internal(bonsai_ctx *c, float theta, float eps, float *acc_c, float *pot_c) {
+    if (!c->have_tree) return BONSAI_ESTATE;
+    if (!(theta > 0.0f) || !(eps >= 0.0f) || !isfinite(theta) || !isfinite(eps))
+        return BONSAI_EINVAL;
+    if (c->walk_warps == 0) {
+        c->walk_warps = walk_resident_warps(c);
+        if (ensure(c->frontier, walk_frontier_elems(c->walk_warps))) return BONSAI_ENOMEM;
+    }
+    BGB_CUDA(cudaMemsetAsync(&c->dsc->n_pp, 0, 2 * sizeof(uint64_t), c->stream));
+    BGB_CUDA(cudaMemsetAsync(&c->dsc->status, 0, 3 * sizeof(int32_t), c->stream));
+    BGB_CUDA(cudaEventRecord(c->ev[3], c->stream));
+    if (c->packed_theta != theta) {
+        launch_cell_pack(c, theta);
+        c->packed_theta = theta;
+    }
+    int rc = walk_force(c, eps, acc_c, pot_c);
+    if (rc) return rc;
+    BGB_CUDA(cudaEventRecord(c->ev[4], c->stream));
+    if ((rc = read_scalars(c))) return rc;
+    cudaEventElapsedTime(&c->stats.ms_force, c->ev[3], c->ev[4]);
+    cudaEventElapsedTime(&c->stats.ms_walk, c->ev[8], c->ev[9]);
+    c->stats.n_pp = c->hsc->n_pp;
+    c->stats.n_pc = c->hsc->n_pc;
+    c->stats.flops = 23.0 * (double)c->hsc->n_pp + 65.0 * (double)c->hsc->n_pc;
+    c->stats.max_frontier = c->hsc->max_frontier;
+    if (c->hsc->status & ST_OVERFLOW) {
+        c->have_forces = false;
+        return BONSAI_EOVERFLOW;
+    }
+    c->have_forces = true;
+    return BONSAI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int bonsai_create(bonsai_ctx **out, const bonsai_params *p, void *stream) {
+    if (!out || !p) return BONSAI_EINVAL;
+    *out = nullptr;
+    if (p->nleaf != NLEAF || p->ncrit != NCRIT || !(p->theta > 0.0f) || !(p->eps >= 0.0f) ||
+        !isfinite(p->G))
+        return BONSAI_EINVAL;
+    bonsai_ctx *c = new (std::nothrow) bonsai_ctx();
+    if (!c) return BONSAI_ENOMEM;
+    c->prm = *p;
+    c->stream = (cudaStream_t)stream;
+    memset(&c->stats, 0, sizeof(c->stats));
+    if (cudaGetDevice(&c->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device) !=
+            cudaSuccess) {
+        delete c;
+        return BONSAI_ECUDA;
+    }
+    if (cudaMalloc(&c->dsc, sizeof(DevScalars)) != cudaSuccess ||
+        cudaMallocHost(&c->hsc, sizeof(DevScalars)) != cudaSuccess) {
+        cudaFree(c->dsc);
+        delete c;
+        return BONSAI_ENOMEM;
+    }
+    for (int k = 0; k < 10; ++k) cudaEventCreate(&c->ev[k]);
+    *out = c;
+    return BONSAI_OK;
+}
+
+void bonsai_destroy(bonsai_ctx *c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    release(c->pos); release(c->pos2); release(c->vel); release(c->vel2);
+    release(c->mass); release(c->mass2); release(c->id); release(c->id2);
+    release(c->acc); release(c->pot); release(c->key); release(c->key2);
+    release(c->val); release(c->val2); release(c->hist); release(c->scan_tmp);
+    release(c->box_part); release(c->body_hi); release(c->body_lo);
+    release(c->nd_first); release(c->nd_count); release(c->nd_child); release(c->nd_nchild);
+    release(c->nd_level); release(c->nd_parent); release(c->nd_scan);
+    release(c->nd_M); release(c->nd_com); release(c->nd_Q);
+    release(c->cell_mac); release(c->cell_topo); release(c->cell_a); release(c->cell_b);
+    release(c->cell_c);
+    release(c->grp_flag); release(c->grp_first); release(c->grp_count); release(c->grp_centre);
+    release(c->grp_box); release(c->grp_half); release(c->grp_lo); release(c->grp_npp);
+    release(c->grp_npc); release(c->frontier); release(c->diag_part);
+    cudaFree(c->dsc);
+    cudaFreeHost(c->hsc);
+    for (int k = 0; k < 10; ++k) cudaEventDestroy(c->ev[k]);
+    delete c;
+}
+
+int bonsai_set_stream(bonsai_ctx *c, void *stream) {
+    if (!c) return BONSAI_EINVAL;
+    c->stream = (cudaStream_t)stream;
+    return BONSAI_OK;
+}
+
+int tree_build(bonsai_ctx *c, const double *pos, const double *mass, int64_t n) {
+    if (!c || !pos || !mass || n < 1 || n > 0x7fffffffll) return BONSAI_EINVAL;
+    c->have_tree = c->have_forces = c->have_vel = false;
+    c->n = n;
+    int rc = particle_buffers(c, n);
+    if (rc) return rc;
+    rc = rebuild(c, pos, mass, true);
+    if (rc) return rc;
+    c->stats.n = n;
+    c->stats.n_nodes = c->n_nodes;
+    c->stats.n_groups = c->n_groups;
+    c->stats.depth = c->depth;
+    return BONSAI_OK;
+}
+
+int tree_forces(bonsai_ctx *c, float theta, float eps, float *acc, float *pot) {
+    if (!c) return BONSAI_EINVAL;
+    return forces_internal(c, theta, eps, acc, pot);
+}
+
+int tree_set_velocities(bonsai_ctx *c, const double *vel) {
+    if (!c || !vel) return BONSAI_EINVAL;
+    if (!c->have_tree) return BONSAI_ESTATE;
+    launch_permute_in_vel(c, vel);
+    BGB_CUDA(cudaStreamSynchronize(c->stream));
+    c->have_vel = true;
+    return BONSAI_OK;
+}
+
+int tree_step(bonsai_ctx *c, double dt) {
+    if (!c || !isfinite(dt)) return BONSAI_EINVAL;
+    if (!c->have_tree) return BONSAI_ESTATE;
+    int rc;
+    if (!c->have_forces && (rc = forces_internal(c, c->prm.theta, c->prm.eps, nullptr, nullptr)))
+        return rc;
+    BGB_CUDA(cudaEventRecord(c->ev[5], c->stream));
+    launch_kick(c, 0.5 * dt);
+    launch_drift(c, dt);
+    BGB_CUDA(cudaEventRecord(c->ev[6], c->stream));
+    c->have_forces = false;
+    if ((rc = rebuild(c, nullptr, nullptr, false))) return rc;
+    if ((rc = forces_internal(c, c->prm.theta, c->prm.eps, nullptr, nullptr))) return rc;
+    BGB_CUDA(cudaEventRecord(c->ev[7], c->stream));
+    launch_kick(c, 0.5 * dt);
+    BGB_CUDA(cudaStreamSynchronize(c->stream));
+    float a = 0.0f;
+    cudaEventElapsedTime(&a, c->ev[5], c->ev[6]);
+    c->stats.ms_integrate = 2.0f * a;
+    c->stats.n_nodes = c->n_nodes;
+    c->stats.n_groups = c->n_groups;
+    c->stats.depth = c->depth;
+    return BONSAI_OK;
+}
+
+int tree_get_state(bonsai_ctx *c, double *pos, double *vel, double *mass) {
+    if (!c) return BONSAI_EINVAL;
+    if (!c->have_tree) return BONSAI_ESTATE;
+    launch_unpermute_state(c, pos, vel, mass);
+    BGB_CUDA(cudaStreamSynchronize(c->stream));
+    return BONSAI_OK;
+}
+
+int tree_get_forces(bonsai_ctx *c, float *acc, float *pot) {
+    if (!c) return BONSAI_EINVAL;
+    if (!c->have_forces) return BONSAI_ESTATE;
+    launch_unpermute_forces(c, acc, pot);
+    BGB_CUDA(cudaStreamSynchronize(c->stream));
+    return BONSAI_OK;
+}
+
+int bonsai_diagnostics(bonsai_ctx *c, double out[10]) {
+    if (!c || !out) return BONSAI_EINVAL;
+    if (!c->have_forces) return BONSAI_ESTATE;
+    double *dev = c->diag_part.p + (size_t)diag_blocks(c) * 10;
+    launch_diagnostics(c, dev);
+    BGB_CUDA(cudaMemcpyAsync(out, dev, 10 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    BGB_CUDA(cudaStreamSynchronize(c->stream));
+    out[2] = out[0] + out[1];
+    return BONSAI_OK;
+}
+
+int tree_get_stats(bonsai_ctx *c, bonsai_stats *out) {
+    if (!c || !out) return BONSAI_EINVAL;
+    c->stats.launches = c->launches;
+    *out = c->stats;
+    return BONSAI_OK;
+}
+
+int tree_solve_host(bonsai_ctx *c, const double *pos, const double *mass, int64_t n, float theta,
+                    float eps, float *acc, float *pot) {
+    if (!c || !pos || !mass || n < 1 || n > 0x7fffffffll) return BONSAI_EINVAL;
+    c->have_tree = c->have_forces = c->have_vel = false;
+    c->n = n;
+    int rc = particle_buffers(c, n);
+    if (rc) return rc;
+    // stage the caller's arrays in the second state buffers, then build from them
+    BGB_CUDA(cudaMemcpyAsync(c->pos2.p, pos, 3 * n * sizeof(double), cudaMemcpyHostToDevice,
+                             c->stream));
+    BGB_CUDA(cudaMemcpyAsync(c->mass2.p, mass, n * sizeof(double), cudaMemcpyHostToDevice,
+                             c->stream));
+    rc = rebuild(c, c->pos2.p, c->mass2.p, true);
+    if (rc) return rc;
+    rc = forces_internal(c, theta, eps, nullptr, nullptr);
+    if (rc) return rc;
+    // caller-order results staged in the key buffer's space, then copied to the host
+    float *stage = reinterpret_cast<float *>(c->pos2.p);
+    launch_unpermute_forces(c, stage, stage + 3 * n);
+    if (acc)
+        BGB_CUDA(cudaMemcpyAsync(acc, stage, 3 * n * sizeof(float), cudaMemcpyDeviceToHost,
+                                 c->stream));
+    if (pot)
+        BGB_CUDA(cudaMemcpyAsync(pot, stage + 3 * n, n * sizeof(float), cudaMemcpyDeviceToHost,
+                                 c->stream));
+    BGB_CUDA(cudaStreamSynchronize(c->stream));
+    c->stats.n = n;
+    c->stats.n_nodes = c->n_nodes;
+    c->stats.n_groups = c->n_groups;
+    c->stats.depth = c->depth;
+    return BONSAI_OK;
+}
+
+int tree_debug_cube(bonsai_ctx *c, double lo[3], double *L) {
+    if (!c || !lo || !L) return BONSAI_EINVAL;
+    if (!c->have_tree) return BONSAI_ESTATE;
+    BGB_CUDA(cudaMemcpyAsync(c->hsc, c->dsc, sizeof(DevScalars), cudaMemcpyDeviceToHost,
+                             c->stream));
+    BGB_CUDA(cudaStreamSynchronize(c->stream));
+    for (int d = 0; d < 3; ++d) lo[d] = c->hsc->lo[d];
+    *L = c->hsc->L;
+    return BONSAI_OK;
+}
+
+int tree_debug_keys(bonsai_ctx *c, uint64_t *keys, uint32_t *perm) {
+    if (!c) return BONSAI_EINVAL;
+    if (!c->have_tree) return BONSAI_ESTATE;
+    if (keys)
+        BGB_CUDA(cudaMemcpyAsync(keys, c->key.p, c->n * sizeof(uint64_t), cudaMemcpyDeviceToDevice,
+                                 c->stream));
+    if (perm)
+        BGB_CUDA(cudaMemcpyAsync(perm, c->id.p, c->n * sizeof(uint32_t), cudaMemcpyDeviceToDevice,
+                                 c->stream));
+    BGB_CUDA(cudaStreamSynchronize(c->stream));
+    return BONSAI_OK;
+}
+
+int tree_debug_nodes(bonsai_ctx *c, uint32_t *first, uint32_t *count, uint32_t *child,
+                     uint32_t *nchild, uint32_t *level) {
+    if (!c) return BONSAI_EINVAL;
+    if (!c->have_tree) return BONSAI_ESTATE;
+    const size_t b = c->n_nodes * sizeof(uint32_t);
+    uint32_t *dst[5] = {first, count, child, nchild, level};
+    uint32_t *src[5] = {c->nd_first.p, c->nd_count.p, c->nd_child.p, c->nd_nchild.p,
+                        c->nd_level.p};
+    for (int k = 0; k < 5; ++k)
+        if (dst[k])
+            BGB_CUDA(cudaMemcpyAsync(dst[k], src[k], b, cudaMemcpyDeviceToDevice, c->stream));
+    BGB_CUDA(cudaStreamSynchronize(c->stream));
+    return BONSAI_OK;
+}
+
+int tree_debug_multipoles(bonsai_ctx *c, double *M, double *com, double *Q) {
+    if (!c) return BONSAI_EINVAL;
+    if (!c->have_tree) return BONSAI_ESTATE;
+    const size_t nn = c->n_nodes;
+    if (M) BGB_CUDA(cudaMemcpyAsync(M, c->nd_M.p, nn * 8, cudaMemcpyDeviceToDevice, c->stream));
+    if (com)
+        BGB_CUDA(cudaMemcpyAsync(com, c->nd_com.p, 3 * nn * 8, cudaMemcpyDeviceToDevice, c->stream));
+    if (Q) BGB_CUDA(cudaMemcpyAsync(Q, c->nd_Q.p, 6 * nn * 8, cudaMemcpyDeviceToDevice, c->stream));
+    BGB_CUDA(cudaStreamSynchronize(c->stream));
+    return BONSAI_OK;
+}
+
+int tree_debug_groups(bonsai_ctx *c, uint32_t *first, uint32_t *count, int32_t *npp,
+                      int32_t *npc) {
+    if (!c) return BONSAI_EINVAL;
+    if (!c->have_tree) return BONSAI_ESTATE;
+    if ((npp || npc) && !c->have_forces) return BONSAI_ESTATE;
+    const size_t ng = c->n_groups;
+    if (first)
+        BGB_CUDA(cudaMemcpyAsync(first, c->grp_first.p, ng * 4, cudaMemcpyDeviceToDevice, c->stream));
+    if (count)
+        BGB_CUDA(cudaMemcpyAsync(count, c->grp_count.p, ng * 4, cudaMemcpyDeviceToDevice, c->stream));
+    if (npp) BGB_CUDA(cudaMemcpyAsync(npp, c->grp_npp.p, ng * 4, cudaMemcpyDeviceToDevice, c->stream));
+    if (npc) BGB_CUDA(cudaMemcpyAsync(npc, c->grp_npc.p, ng * 4, cudaMemcpyDeviceToDevice, c->stream));
+    BGB_CUDA(cudaStreamSynchronize(c->stream));
+    return BONSAI_OK;
+}
+
+const char *bonsai_strerror(int code) {
+    switch (code) {
+        case BONSAI_OK: return "ok";
+        case BONSAI_EINVAL: return "invalid argument";
+        case BONSAI_ENOMEM: return "device allocation failed";
+        case BONSAI_EOVERFLOW: return "walk buffer overflow";
+        case BONSAI_ECUDA: return "CUDA runtime error";
+        case BONSAI_ESTATE: return "call out of order";
+        default: return "unknown status";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,180 @@
+// internal.cuh -- context layout, constants and kernel launchers shared by
+// the translation units of the CUDA library.  Nothing here is part of the
+// C ABI (include/bonsai_gb.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/bonsai_gb.h"
+
+namespace bgb {
+
+constexpr int KEY_BITS = 21;   // bits per axis of the Peano-Hilbert key (63-bit key)
+constexpr int MAX_LEVEL = 21;  // deepest octree level (one key value)
+constexpr int NLEAF = 16;      // a node with more particles is split (Sec. I.A)
+constexpr int NCRIT = 64;      // walk-group size
+constexpr uint32_t LEAF_FLAG = 0x80000000u;  // topo.y: leaf marker, low bits = count
+
+// device status word bits (set by kernels, read once per call)
+constexpr int ST_BAD_INPUT = 1;      // non-finite position or mass <= 0
+constexpr int ST_OVERFLOW = 2;       // a walk frontier overflowed
+constexpr int ST_NODE_OVERFLOW = 4;  // node storage too small (host regrows)
+
+// Device scalars written by kernels and read back in one copy.
+struct DevScalars {
+    double lo[3];     // bounding cube corner
+    double L;         // cube side
+    double scale;     // 2^21 / L
+    uint64_t n_pp;    // interaction counters of the last walk
+    uint64_t n_pc;
+    uint32_t level_count;  // children produced by the last split level
+    int32_t status;        // ST_* bits
+    int32_t max_frontier;
+    uint32_t group_counter;  // dynamic scheduling of the walk
+    uint32_t n_groups;
+    int32_t pad;
+};
+
+// Bounding-cube reduction partials (per block)
+struct BoxPartial {
+    double mn[3], mx[3];
+    int32_t bad;
+    int32_t pad;
+};
+
+template <typename T>
+struct DBuf {
+    T *p = nullptr;
+    size_t cap = 0;  // elements
+};
+
+}  // namespace bgb
+
+struct bonsai_ctx {
+    bonsai_params prm;
+    cudaStream_t stream;
+    int device;
+    int sm_count;
+
+    int64_t n = 0;         // particles of the current tree
+    int64_t n_nodes = 0;
+    int64_t n_leaves = 0;
+    int64_t n_groups = 0;
+    int depth = 0;
+    bool have_tree = false;
+    bool have_forces = false;  // acc/pot in sorted order are valid
+    bool have_vel = false;
+    float packed_theta = -1.0f;  // theta of the current cell pack
+
+    // particle state in key-sorted order (double buffers for the re-sort)
+    bgb::DBuf<double> pos, pos2;     // [3][n]
+    bgb::DBuf<double> vel, vel2;     // [3][n]
+    bgb::DBuf<double> mass, mass2;   // [n]
+    bgb::DBuf<uint32_t> id, id2;     // caller index of each sorted slot
+    bgb::DBuf<float> acc;            // [3][n] sorted order, FP32, G applied
+    bgb::DBuf<float> pot;            // [n]
+
+    // keys and sort scratch
+    bgb::DBuf<uint64_t> key, key2;
+    bgb::DBuf<uint32_t> val, val2;
+    bgb::DBuf<uint32_t> hist;        // radix histograms / scan
+    bgb::DBuf<uint32_t> scan_tmp;
+    bgb::DBuf<bgb::BoxPartial> box_part;
+
+    // particle records for the walk: {x_hi, y_hi, z_hi, m} and {x_lo, y_lo, z_lo, 0}
+    bgb::DBuf<float4> body_hi, body_lo;
+
+    // nodes (breadth-first)
+    bgb::DBuf<uint32_t> nd_first, nd_count, nd_child, nd_nchild, nd_level, nd_parent;
+    bgb::DBuf<uint32_t> nd_scan;     // per-level scan scratch
+    bgb::DBuf<double> nd_M;          // [nn]
+    bgb::DBuf<double> nd_com;        // [3][nn]
+    bgb::DBuf<double> nd_Q;          // [6][nn]
+    // packed cell records for the walk
+    bgb::DBuf<float4> cell_mac;      // {com_hi.xyz, r_open^2}
+    bgb::DBuf<uint2> cell_topo;      // leaf: {first, count|LEAF}; internal: {child, nchild}
+    bgb::DBuf<float4> cell_a;        // {com_lo.xyz, M}
+    bgb::DBuf<float4> cell_b;        // {Qxx, Qyy, Qzz, Qxy}
+    bgb::DBuf<float4> cell_c;        // {Qxz, Qyz, trQ/2, 0}
+    int64_t level_start[bgb::MAX_LEVEL + 2];
+
+    // groups
+    bgb::DBuf<uint32_t> grp_flag;    // [n+1] group-start flags / scan
+    bgb::DBuf<uint32_t> grp_first, grp_count;
+    bgb::DBuf<double> grp_centre;    // [3][ng] FP64 box centre
+    bgb::DBuf<float4> grp_box;       // {c_f.xyz, 0}
+    bgb::DBuf<float4> grp_half;      // {h_f.xyz (rounded up), 0}
+    bgb::DBuf<float4> grp_lo;        // {c_lo.xyz, 0}: c = c_f + c_lo
+    bgb::DBuf<int32_t> grp_npp, grp_npc;
+
+    // walk frontier scratch (per resident warp)
+    bgb::DBuf<uint32_t> frontier;
+    int walk_warps = 0;
+
+    // device scalars + host mirror
+    bgb::DevScalars *dsc = nullptr;
+    bgb::DevScalars *hsc = nullptr;  // pinned host mirror
+
+    // diagnostics scratch
+    bgb::DBuf<double> diag_part;
+
+    // timing events
+    cudaEvent_t ev[10];
+    bonsai_stats stats;
+    uint64_t launches = 0;  // kernels launched by this context
+};
+
+namespace bgb {
+
+// ---- allocation helpers (api.cu) ----
+template <typename T>
+int ensure(DBuf<T> &b, size_t n);
+template <typename T>
+void release(DBuf<T> &b);
+
+// ---- launchers (one per kernel family) ----
+// keys.cu
+void launch_bbox(bonsai_ctx *c, const double *pos, const double *mass, int64_t n);
+void launch_keys(bonsai_ctx *c, const double *pos, int64_t n);
+// sort.cu
+void radix_sort_pairs(bonsai_ctx *c, int64_t n);  // sorts key/val in place (ping-pong inside)
+void exclusive_scan_u32(bonsai_ctx *c, const uint32_t *in, uint32_t *out, int64_t n,
+                        uint32_t *total_dev);
+void launch_gather_build(bonsai_ctx *c, const double *pos, const double *mass, int64_t n);
+void launch_gather_step(bonsai_ctx *c, int64_t n);
+// tree.cu
+int build_octree(bonsai_ctx *c);
+int build_groups(bonsai_ctx *c);
+void launch_multipoles(bonsai_ctx *c);
+void launch_body_pack(bonsai_ctx *c);
+void launch_cell_pack(bonsai_ctx *c, float theta);
+// walk.cu
+int walk_force(bonsai_ctx *c, float eps, float *acc_caller, float *pot_caller);
+// integrate.cu
+void launch_kick(bonsai_ctx *c, double h);
+void launch_drift(bonsai_ctx *c, double dt);
+void launch_diagnostics(bonsai_ctx *c, double *out_dev);
+int diag_blocks(bonsai_ctx *c);
+int walk_resident_warps(bonsai_ctx *c);
+size_t walk_frontier_elems(int warps);
+size_t scan_tmp_elems(int64_t n);
+size_t sort_hist_elems(int64_t n);
+void launch_unpermute_state(bonsai_ctx *c, double *pos, double *vel, double *mass);
+void launch_unpermute_forces(bonsai_ctx *c, float *acc, float *pot);
+void launch_permute_in_vel(bonsai_ctx *c, const double *vel);
+
+inline int grid_for(int64_t n, int block, int max_blocks = 1 << 30) {
+    int64_t g = (n + block - 1) / block;
+    if (g < 1) g = 1;
+    if (g > max_blocks) g = max_blocks;
+    return (int)g;
+}
+
+}  // namespace bgb
+
+#define BGB_CUDA(call)                                  \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return BONSAI_ECUDA;     \
+    } while (0)

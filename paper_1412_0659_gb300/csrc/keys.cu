@@ -1,0 +1,209 @@
+// keys.cu -- bounding cube reduction and Peano-Hilbert keys (Sec. III.B.1:
+// the bounding box maps coordinates to PH keys; Fig. 2 shows the curve).
+//
+// Both kernels stream the FP64 SoA positions once (HBM-bound).  Every FP64
+// operation that feeds a key is an explicit round-to-nearest intrinsic so
+// the keys are bit-identical to any IEEE implementation of the same formula.
+#include <math.h>
+
+#include "internal.cuh"
+
+namespace bgb {
+
+namespace {
+
+constexpr int BOX_BLOCK = 256;
+
+__device__ inline double warp_min(double v) {
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_down_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ inline double warp_max(double v) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Per-block min/max of x, y, z plus an input check (finite positions,
+// finite positive masses).
+__global__ void __launch_bounds__(BOX_BLOCK) k_box_partial(const double *__restrict__ pos,
+                                                           const double *__restrict__ mass,
+                                                           int64_t n, BoxPartial *part) {
+    double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    int bad = 0;
+    for (int64_t i = blockIdx.x * (int64_t)BOX_BLOCK + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * BOX_BLOCK) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            double v = pos[d * n + i];
+            bad |= !isfinite(v);
+            mn[d] = fmin(mn[d], v);
+            mx[d] = fmax(mx[d], v);
+        }
+        double m = mass[i];
+        bad |= !(m > 0.0) || !isfinite(m);
+    }
+    __shared__ double smn[3][BOX_BLOCK / 32], smx[3][BOX_BLOCK / 32];
+    __shared__ int sbad;
+    if (threadIdx.x == 0) sbad = 0;
+    __syncthreads();
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        double a = warp_min(mn[d]), b = warp_max(mx[d]);
+        if (l == 0) { smn[d][w] = a; smx[d][w] = b; }
+    }
+    if (bad) atomicOr(&sbad, 1);
+    __syncthreads();
+    if (threadIdx.x < 32) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            double a = l < BOX_BLOCK / 32 ? smn[d][l] : INFINITY;
+            double b = l < BOX_BLOCK / 32 ? smx[d][l] : -INFINITY;
+            a = warp_min(a);
+            b = warp_max(b);
+            if (l == 0) { part[blockIdx.x].mn[d] = a; part[blockIdx.x].mx[d] = b; }
+        }
+        if (l == 0) part[blockIdx.x].bad = sbad;
+    }
+}
+
+// Final reduction and the cube: side L = (largest extent) * (1 + 2^-20)
+// (1 when every point coincides), centred on the box; scale = 2^21 / L.
+__global__ void __launch_bounds__(BOX_BLOCK) k_box_final(const BoxPartial *part, int nb,
+                                                         DevScalars *sc) {
+    double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    int bad = 0;
+    for (int b = threadIdx.x; b < nb; b += BOX_BLOCK) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            mn[d] = fmin(mn[d], part[b].mn[d]);
+            mx[d] = fmax(mx[d], part[b].mx[d]);
+        }
+        bad |= part[b].bad;
+    }
+    __shared__ double smn[3][BOX_BLOCK / 32], smx[3][BOX_BLOCK / 32];
+    __shared__ int sbad;
+    if (threadIdx.x == 0) sbad = 0;
+    __syncthreads();
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        double a = warp_min(mn[d]), b = warp_max(mx[d]);
+        if (l == 0) { smn[d][w] = a; smx[d][w] = b; }
+    }
+    if (bad) atomicOr(&sbad, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double lo[3], hi[3];
+        for (int d = 0; d < 3; ++d) {
+            lo[d] = smn[d][0];
+            hi[d] = smx[d][0];
+            for (int k = 1; k < BOX_BLOCK / 32; ++k) {
+                lo[d] = fmin(lo[d], smn[d][k]);
+                hi[d] = fmax(hi[d], smx[d][k]);
+            }
+        }
+        double ext = __dsub_rn(hi[0], lo[0]);
+        double e1 = __dsub_rn(hi[1], lo[1]), e2 = __dsub_rn(hi[2], lo[2]);
+        if (e1 > ext) ext = e1;
+        if (e2 > ext) ext = e2;
+        double L = __dmul_rn(ext, 1.0 + 0x1p-20);
+        if (ext == 0.0) L = 1.0;
+        for (int d = 0; d < 3; ++d) {
+            double w = __dsub_rn(hi[d], lo[d]);
+            sc->lo[d] = __dsub_rn(lo[d], __dmul_rn(__dsub_rn(L, w), 0.5));
+        }
+        sc->L = L;
+        sc->scale = __ddiv_rn(0x1p21, L);
+        if (sbad) atomicOr(&sc->status, ST_BAD_INPUT);
+    }
+}
+
+__device__ inline uint32_t quantise(double x, double lo, double scale) {
+    double f = floor(__dmul_rn(__dsub_rn(x, lo), scale));
+    if (!(f >= 0.0)) return 0u;
+    if (f > (double)((1u << KEY_BITS) - 1u)) return (1u << KEY_BITS) - 1u;
+    return (uint32_t)f;
+}
+
+// Spread the low 21 bits of v to every third bit of a 64-bit word.
+__device__ inline uint64_t spread3(uint32_t v) {
+    uint64_t x = v & 0x1fffffu;
+    x = (x | (x << 32)) & 0x001f00000000ffffull;
+    x = (x | (x << 16)) & 0x001f0000ff0000ffull;
+    x = (x | (x << 8)) & 0x100f00f00f00f00full;
+    x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
+    x = (x | (x << 2)) & 0x1249249249249249ull;
+    return x;
+}
+
+}  // namespace
+
+// Hilbert index of a 21-bit cell after J. Skilling, "Programming the Hilbert
+// curve" (AIP Conf. Proc. 707, 2004): the transpose form, then bit
+// interleaving with axis 0 most significant in each 3-bit digit.  The Gray
+// step's running XOR is taken as a suffix-XOR scan of the last axis.
+__device__ __forceinline__ uint64_t ph_key(uint32_t x0, uint32_t x1, uint32_t x2) {
+#pragma unroll
+    for (uint32_t q = 1u << (KEY_BITS - 1); q > 1u; q >>= 1) {
+        const uint32_t p = q - 1u;
+        x0 = (x0 & q) ? (x0 ^ p) : x0;
+        {
+            uint32_t t = (x0 ^ x1) & p;
+            bool inv = (x1 & q) != 0u;
+            x0 = inv ? (x0 ^ p) : (x0 ^ t);
+            x1 = inv ? x1 : (x1 ^ t);
+        }
+        {
+            uint32_t t = (x0 ^ x2) & p;
+            bool inv = (x2 & q) != 0u;
+            x0 = inv ? (x0 ^ p) : (x0 ^ t);
+            x2 = inv ? x2 : (x2 ^ t);
+        }
+    }
+    x1 ^= x0;
+    x2 ^= x1;
+    uint32_t y = x2 >> 1;  // bit j of the mask = XOR of x2's bits above j
+    y ^= y >> 1;
+    y ^= y >> 2;
+    y ^= y >> 4;
+    y ^= y >> 8;
+    y ^= y >> 16;
+    x0 ^= y;
+    x1 ^= y;
+    x2 ^= y;
+    return (spread3(x0) << 2) | (spread3(x1) << 1) | spread3(x2);
+}
+
+namespace {
+
+__global__ void __launch_bounds__(256) k_keys(const double *__restrict__ pos, int64_t n,
+                                              const DevScalars *__restrict__ sc,
+                                              uint64_t *__restrict__ key,
+                                              uint32_t *__restrict__ val) {
+    const double lo0 = sc->lo[0], lo1 = sc->lo[1], lo2 = sc->lo[2], s = sc->scale;
+    for (int64_t i = blockIdx.x * 256ll + threadIdx.x; i < n; i += (int64_t)gridDim.x * 256) {
+        uint32_t q0 = quantise(pos[i], lo0, s);
+        uint32_t q1 = quantise(pos[n + i], lo1, s);
+        uint32_t q2 = quantise(pos[2 * n + i], lo2, s);
+        key[i] = ph_key(q0, q1, q2);
+        val[i] = (uint32_t)i;
+    }
+}
+
+}  // namespace
+
+void launch_bbox(bonsai_ctx *c, const double *pos, const double *mass, int64_t n) {
+    int nb = grid_for(n, BOX_BLOCK * 4, c->sm_count * 4);
+    k_box_partial<<<nb, BOX_BLOCK, 0, c->stream>>>(pos, mass, n, c->box_part.p);
+    k_box_final<<<1, BOX_BLOCK, 0, c->stream>>>(c->box_part.p, nb, c->dsc);
+    c->launches += 2;
+}
+
+void launch_keys(bonsai_ctx *c, const double *pos, int64_t n) {
+    k_keys<<<grid_for(n, 256, c->sm_count * 16), 256, 0, c->stream>>>(pos, n, c->dsc, c->key.p,
+                                                                       c->val.p);
+    c->launches += 1;
+}
+
+}  // namespace bgb

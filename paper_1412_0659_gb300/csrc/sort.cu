@@ -1,0 +1,255 @@
+// sort.cu -- stable LSD radix sort of (key, index) pairs, an exclusive
+// scan, and the gathers that move particle state into key order
+// (Table 2 "Sorting SFC").
+//
+// The sort is 8 passes of 8 bits.  Each pass is a per-tile histogram, an
+// exclusive scan of the digit-major histogram table (which yields every
+// tile's output offset per digit), and a stable scatter that ranks the
+// tile's keys with warp match/popc.  Stability plus the index payload
+// starting at 0..n-1 makes the order identical to sorting by (key, index).
+#include <utility>
+
+#include "internal.cuh"
+
+namespace bgb {
+
+namespace {
+
+constexpr int SORT_BLOCK = 256;
+constexpr int SORT_IPT = 16;
+constexpr int SORT_TILE = SORT_BLOCK * SORT_IPT;
+constexpr int SORT_WARPS = SORT_BLOCK / 32;
+
+constexpr int SCAN_BLOCK = 1024;
+constexpr int SCAN_IPT = 4;
+constexpr int SCAN_TILE = SCAN_BLOCK * SCAN_IPT;
+
+__device__ inline uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__global__ void __launch_bounds__(SORT_BLOCK) k_hist(const uint64_t *__restrict__ kin, int64_t n,
+                                                     int shift, uint32_t *__restrict__ hist,
+                                                     int nb) {
+    __shared__ uint32_t cnt[256];
+    cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * SORT_TILE;
+    for (int r = 0; r < SORT_IPT; ++r) {
+        int64_t i = base + r * SORT_BLOCK + threadIdx.x;
+        uint32_t d = i < n ? (uint32_t)(kin[i] >> shift) & 255u : 256u;
+        uint32_t peers = __match_any_sync(0xffffffffu, d);
+        if (d < 256u && (peers & lanemask_lt()) == 0u) atomicAdd(&cnt[d], __popc(peers));
+    }
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * nb + blockIdx.x] = cnt[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(SORT_BLOCK) k_scatter(const uint64_t *__restrict__ kin,
+                                                        const uint32_t *__restrict__ vin,
+                                                        uint64_t *__restrict__ kout,
+                                                        uint32_t *__restrict__ vout, int64_t n,
+                                                        int shift,
+                                                        const uint32_t *__restrict__ offs,
+                                                        int nb) {
+    __shared__ uint32_t base[256];
+    __shared__ uint32_t wcnt[SORT_WARPS][256];
+    const int tid = threadIdx.x, warp = tid >> 5;
+    base[tid] = offs[(int64_t)tid * nb + blockIdx.x];
+    const int64_t tile = (int64_t)blockIdx.x * SORT_TILE;
+    const uint32_t lt = lanemask_lt();
+    for (int r = 0; r < SORT_IPT; ++r) {
+        int64_t i = tile + r * SORT_BLOCK + tid;
+        bool valid = i < n;
+        uint64_t k = valid ? kin[i] : 0ull;
+        uint32_t v = valid ? vin[i] : 0u;
+        uint32_t d = valid ? (uint32_t)(k >> shift) & 255u : 256u;
+#pragma unroll
+        for (int w = 0; w < SORT_WARPS; ++w) wcnt[w][tid] = 0u;
+        __syncthreads();
+        uint32_t peers = __match_any_sync(0xffffffffu, d);
+        uint32_t rank = __popc(peers & lt);
+        if (valid && rank == 0u) wcnt[warp][d] = __popc(peers);
+        __syncthreads();
+        {
+            uint32_t run = base[tid];
+#pragma unroll
+            for (int w = 0; w < SORT_WARPS; ++w) {
+                uint32_t c = wcnt[w][tid];
+                wcnt[w][tid] = run;
+                run += c;
+            }
+            base[tid] = run;
+        }
+        __syncthreads();
+        if (valid) {
+            uint32_t dst = wcnt[warp][d] + rank;
+            kout[dst] = k;
+            vout[dst] = v;
+        }
+        __syncthreads();
+    }
+}
+
+// Exclusive scan of one tile per block; block sums go to bsum.
+// in and out may alias (the sort scans its histogram table in place).
+__global__ void __launch_bounds__(SCAN_BLOCK) k_scan_tile(const uint32_t *in, uint32_t *out, int64_t n,
+                                                          uint32_t *__restrict__ bsum) {
+    __shared__ uint32_t wsum[SCAN_BLOCK / 32];
+    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_IPT;
+    uint32_t v[SCAN_IPT], s = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_IPT; ++k) {
+        v[k] = (base + k < n) ? in[base + k] : 0u;
+        s += v[k];
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t inc = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = wsum[lane];
+        uint32_t wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t t = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += t;
+        }
+        wsum[lane] = wi - w;
+        if (lane == 31 && bsum) bsum[blockIdx.x] = wi;
+    }
+    __syncthreads();
+    uint32_t run = wsum[warp] + inc - s;
+#pragma unroll
+    for (int k = 0; k < SCAN_IPT; ++k) {
+        if (base + k < n) out[base + k] = run;
+        run += v[k];
+    }
+}
+
+__global__ void __launch_bounds__(SCAN_BLOCK) k_scan_add(uint32_t *__restrict__ out, int64_t n,
+                                                         const uint32_t *__restrict__ boff) {
+    const uint32_t add = boff[blockIdx.x];
+    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+    for (int k = threadIdx.x; k < SCAN_TILE; k += SCAN_BLOCK)
+        if (base + k < n) out[base + k] += add;
+}
+
+__global__ void k_scan_total(const uint32_t *in, const uint32_t *out, int64_t n, uint32_t *total) {
+    *total = n > 0 ? out[n - 1] + in[n - 1] : 0u;
+}
+
+// Returns the number of kernels launched.
+int scan_rec(cudaStream_t s, const uint32_t *in, uint32_t *out, int64_t n, uint32_t *tmp) {
+    int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
+    if (nb <= 1) {
+        k_scan_tile<<<1, SCAN_BLOCK, 0, s>>>(in, out, n, nullptr);
+        return 1;
+    }
+    uint32_t *bsum = tmp, *boff = tmp + nb;
+    k_scan_tile<<<(unsigned)nb, SCAN_BLOCK, 0, s>>>(in, out, n, bsum);
+    int k = scan_rec(s, bsum, boff, nb, tmp + 2 * nb);
+    k_scan_add<<<(unsigned)nb, SCAN_BLOCK, 0, s>>>(out, n, boff);
+    return k + 2;
+}
+
+__global__ void __launch_bounds__(256) k_gather_build(const double *__restrict__ pos_c,
+                                                      const double *__restrict__ mass_c,
+                                                      const uint32_t *__restrict__ perm, int64_t n,
+                                                      double *__restrict__ pos,
+                                                      double *__restrict__ vel,
+                                                      double *__restrict__ mass,
+                                                      uint32_t *__restrict__ id) {
+    for (int64_t i = blockIdx.x * 256ll + threadIdx.x; i < n; i += (int64_t)gridDim.x * 256) {
+        uint32_t j = perm[i];
+        pos[i] = pos_c[j];
+        pos[n + i] = pos_c[n + j];
+        pos[2 * n + i] = pos_c[2 * n + j];
+        vel[i] = 0.0;
+        vel[n + i] = 0.0;
+        vel[2 * n + i] = 0.0;
+        mass[i] = mass_c[j];
+        id[i] = j;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_gather_step(
+    const double *__restrict__ pos_o, const double *__restrict__ vel_o,
+    const double *__restrict__ mass_o, const uint32_t *__restrict__ id_o,
+    const uint32_t *__restrict__ perm, int64_t n, double *__restrict__ pos,
+    double *__restrict__ vel, double *__restrict__ mass, uint32_t *__restrict__ id) {
+    for (int64_t i = blockIdx.x * 256ll + threadIdx.x; i < n; i += (int64_t)gridDim.x * 256) {
+        uint32_t j = perm[i];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            pos[d * n + i] = pos_o[d * n + j];
+            vel[d * n + i] = vel_o[d * n + j];
+        }
+        mass[i] = mass_o[j];
+        id[i] = id_o[j];
+    }
+}
+
+}  // namespace
+
+void exclusive_scan_u32(bonsai_ctx *c, const uint32_t *in, uint32_t *out, int64_t n,
+                        uint32_t *total_dev) {
+    if (n > 0) c->launches += scan_rec(c->stream, in, out, n, c->scan_tmp.p);
+    if (total_dev) {
+        k_scan_total<<<1, 1, 0, c->stream>>>(in, out, n, total_dev);
+        c->launches += 1;
+    }
+}
+
+size_t scan_tmp_elems(int64_t n) {
+    size_t t = 0;
+    int64_t m = n;
+    while (m > SCAN_TILE) {
+        m = (m + SCAN_TILE - 1) / SCAN_TILE;
+        t += 2 * (size_t)m;
+    }
+    return t + 64;
+}
+
+size_t sort_hist_elems(int64_t n) { return 256 * (size_t)((n + SORT_TILE - 1) / SORT_TILE) + 64; }
+
+void radix_sort_pairs(bonsai_ctx *c, int64_t n) {
+    const int nb = (int)((n + SORT_TILE - 1) / SORT_TILE);
+    const int64_t nh = 256ll * nb;
+    uint64_t *ka = c->key.p, *kb = c->key2.p;
+    uint32_t *va = c->val.p, *vb = c->val2.p;
+    for (int shift = 0; shift < 64; shift += 8) {
+        k_hist<<<nb, SORT_BLOCK, 0, c->stream>>>(ka, n, shift, c->hist.p, nb);
+        c->launches += scan_rec(c->stream, c->hist.p, c->hist.p, nh, c->scan_tmp.p) + 2;
+        k_scatter<<<nb, SORT_BLOCK, 0, c->stream>>>(ka, va, kb, vb, n, shift, c->hist.p, nb);
+        uint64_t *tk = ka; ka = kb; kb = tk;
+        uint32_t *tv = va; va = vb; vb = tv;
+    }
+    // eight passes: the result is back in key/val
+}
+
+void launch_gather_build(bonsai_ctx *c, const double *pos, const double *mass, int64_t n) {
+    k_gather_build<<<grid_for(n, 256, c->sm_count * 16), 256, 0, c->stream>>>(
+        pos, mass, c->val.p, n, c->pos.p, c->vel.p, c->mass.p, c->id.p);
+    c->launches += 1;
+}
+
+void launch_gather_step(bonsai_ctx *c, int64_t n) {
+    k_gather_step<<<grid_for(n, 256, c->sm_count * 16), 256, 0, c->stream>>>(
+        c->pos.p, c->vel.p, c->mass.p, c->id.p, c->val.p, n, c->pos2.p, c->vel2.p, c->mass2.p,
+        c->id2.p);
+    c->launches += 1;
+    std::swap(c->pos, c->pos2);
+    std::swap(c->vel, c->vel2);
+    std::swap(c->mass, c->mass2);
+    std::swap(c->id, c->id2);
+}
+
+}  // namespace bgb

@@ -1,0 +1,125 @@
+"""Object wrapper over the C ABI: one context, torch tensors in and out.
+
+    g = TreeGravity(G=1.0, theta=0.4, eps=0.01)
+    g.build(pos, mass)            # pos (3, N) float64 CUDA, mass (N,) float64 CUDA
+    acc, pot = g.forces()         # (3, N) / (N,) float32, caller order
+    g.set_velocities(vel)
+    g.step(dt)                    # kick-drift-kick, FP64 state on the device
+    pos, vel, mass = g.state()
+
+Only marshalling happens here; every step runs in the CUDA library.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import capi
+
+
+class TreeGravity:
+    def __init__(self, G: float = 1.0, theta: float = 0.4, eps: float = 0.01, stream=None):
+        self.G, self.theta, self.eps = float(G), float(theta), float(eps)
+        self.ctx = capi.bonsai_create(G=G, theta=theta, eps=eps, stream=stream)
+        self.n = 0
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            capi.bonsai_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_stream(self, stream=None):
+        capi.bonsai_set_stream(self.ctx, stream)
+
+    # -- the path ---------------------------------------------------------
+    def build(self, pos: torch.Tensor, mass: torch.Tensor):
+        capi.tree_build(self.ctx, pos, mass)
+        self.n = int(mass.numel())
+        return self
+
+    def forces(self, theta: float | None = None, eps: float | None = None, acc=None, pot=None):
+        theta = self.theta if theta is None else theta
+        eps = self.eps if eps is None else eps
+        dev = torch.device("cuda", torch.cuda.current_device())
+        if acc is None:
+            acc = torch.empty((3, self.n), dtype=torch.float32, device=dev)
+        if pot is None:
+            pot = torch.empty(self.n, dtype=torch.float32, device=dev)
+        capi.tree_forces(self.ctx, theta, eps, acc, pot)
+        return acc, pot
+
+    def set_velocities(self, vel: torch.Tensor):
+        capi.tree_set_velocities(self.ctx, vel)
+
+    def step(self, dt: float):
+        capi.tree_step(self.ctx, dt)
+
+    def state(self):
+        dev = torch.device("cuda", torch.cuda.current_device())
+        pos = torch.empty((3, self.n), dtype=torch.float64, device=dev)
+        vel = torch.empty((3, self.n), dtype=torch.float64, device=dev)
+        mass = torch.empty(self.n, dtype=torch.float64, device=dev)
+        capi.tree_get_state(self.ctx, pos, vel, mass)
+        return pos, vel, mass
+
+    def last_forces(self):
+        dev = torch.device("cuda", torch.cuda.current_device())
+        acc = torch.empty((3, self.n), dtype=torch.float32, device=dev)
+        pot = torch.empty(self.n, dtype=torch.float32, device=dev)
+        capi.tree_get_forces(self.ctx, acc, pot)
+        return acc, pot
+
+    def diagnostics(self) -> dict:
+        v = capi.bonsai_diagnostics(self.ctx)
+        keys = ("E_kin", "E_pot", "E_tot", "Px", "Py", "Pz", "Lx", "Ly", "Lz", "M")
+        return dict(zip(keys, v))
+
+    def stats(self) -> dict:
+        return capi.tree_get_stats(self.ctx)
+
+    def solve_host(self, pos, mass, acc, pot, theta: float | None = None, eps: float | None = None):
+        theta = self.theta if theta is None else theta
+        eps = self.eps if eps is None else eps
+        capi.tree_solve_host(self.ctx, pos, mass, theta, eps, acc, pot)
+        self.n = int(mass.shape[0])
+
+    # -- internal views (key-sorted order) -------------------------------
+    def debug(self) -> dict:
+        st = self.stats()
+        n, nn, ng = st["n"], st["n_nodes"], st["n_groups"]
+        dev = torch.device("cuda", torch.cuda.current_device())
+        u64 = torch.empty(n, dtype=torch.int64, device=dev)
+        perm = torch.empty(n, dtype=torch.int32, device=dev)
+        capi.tree_debug_keys(self.ctx, u64, perm)
+        nodes = {k: torch.empty(nn, dtype=torch.int32, device=dev)
+                 for k in ("first", "count", "child", "nchild", "level")}
+        capi.tree_debug_nodes(self.ctx, *[nodes[k] for k in ("first", "count", "child", "nchild", "level")])
+        M = torch.empty(nn, dtype=torch.float64, device=dev)
+        com = torch.empty((3, nn), dtype=torch.float64, device=dev)
+        Q = torch.empty((6, nn), dtype=torch.float64, device=dev)
+        capi.tree_debug_multipoles(self.ctx, M, com, Q)
+        gf = torch.empty(ng, dtype=torch.int32, device=dev)
+        gc = torch.empty(ng, dtype=torch.int32, device=dev)
+        capi.tree_debug_groups(self.ctx, gf, gc)
+        lo, L = capi.tree_debug_cube(self.ctx)
+        return {"keys": u64, "perm": perm, "nodes": nodes, "M": M, "com": com, "Q": Q,
+                "group_first": gf, "group_count": gc, "lo": lo, "L": L}
+
+    def group_lists(self):
+        st = self.stats()
+        dev = torch.device("cuda", torch.cuda.current_device())
+        npp = torch.empty(st["n_groups"], dtype=torch.int32, device=dev)
+        npc = torch.empty(st["n_groups"], dtype=torch.int32, device=dev)
+        capi.tree_debug_groups(self.ctx, None, None, npp, npc)
+        return npp, npc
