@@ -114,6 +114,9 @@ def _workload(name: str, rank: int):
         desc = ("Milky-Way-like N=2^23 (Hernquist halo 1e12 Msun a=30 kpc cut 200 kpc, exp. disk "
                 "5e10 Msun Rd=2.5 kpc z0=0.3 kpc Q=1.5, Hernquist bulge 1e10 Msun a=0.5 kpc; "
                 "5:1:0.2), theta=0.4, eps=10 pc, dt=0.1 Myr")
+    elif name == "milky-way-2^20":
+        m = workloads.milky_way(1 << 20, seed=1002 + 17 * rank, eps=0.01, theta=0.4, dt=0.1)
+        desc = "Milky-Way-like N=2^20 (same profiles as the 2^23 model), theta=0.4, eps=10 pc, dt=0.1 Myr"
     elif name == "plummer-2^14":
         m = workloads.plummer(1 << 14, seed=1001 + 17 * rank)
         desc = "Plummer N=2^14, G=M=a=1, theta=0.4, eps=0.01, dt=1/64"
@@ -324,7 +327,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="milky-way-2^23", choices=["milky-way-2^23", "plummer-2^14"])
+    ap.add_argument("--workload", default="milky-way-2^23", choices=["milky-way-2^23", "milky-way-2^20", "plummer-2^14"])
     ap.add_argument("--cpu-groups", type=int, default=96, help="groups walked by the CPU oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--traffic", type=float, default=None,
