@@ -183,6 +183,46 @@ int tree_debug_groups(bonsai_ctx *ctx, uint32_t *first, uint32_t *count, int32_t
 /* Name of a status code. */
 const char *bonsai_strerror(int code);
 
+/* ---- space-filling-curve order without any device allocation ---------- */
+
+/* Largest n accepted by bonsai_sfc_order_noalloc. */
+#define BONSAI_NOALLOC_MAX_N (1 << 20)
+
+/* bonsai_sfc_order_noalloc -- the bounding cube, the 63-bit Peano-Hilbert
+ * keys and their stable sort, i.e. exactly the keys and the order that
+ * tree_build computes for the same pos/mass (see tree_debug_keys), for
+ * callers that must not allocate device memory.  There is no counterpart of
+ * this entry point in the paper; it exists for users of the library.
+ *
+ * Who needs it: code that runs where cudaMalloc is not an option, e.g. a
+ * host whose device memory is entirely owned by another allocator (a
+ * framework's caching pool that has reserved the GPU, or a fixed memory
+ * budget), a latency-critical loop that cannot afford the implicit
+ * device-wide synchronisation of cudaMalloc/cudaFree, or a plugin that is
+ * given buffers but no right to allocate.  It creates no context and calls
+ * no cudaMalloc, cudaFree or allocating library routine.
+ *
+ * Scratch: a fixed static device array of about 12.3 MB (two ping-pong
+ * halves of the sort for up to BONSAI_NOALLOC_MAX_N pairs, the histograms,
+ * the bounding-box partials and a status word), part of the library image:
+ * every GPU that loads the library keeps it until the process exits.  The
+ * first call on a device looks up that array's device address (with the
+ * device current) and caches it; make that first call before any stream
+ * capture.  Every call on a device shares the same array, so calls whose
+ * work overlaps on the GPU (different streams or threads without ordering)
+ * race and must not be issued; calls on one stream are ordered and safe.
+ *
+ * pos: device [3][n] float64, mass: device [n] float64 (> 0, finite), both
+ * read only.  keys: device uint64 [n], receives the sorted keys.  perm:
+ * device uint32 [n], receives the caller index of each sorted slot.
+ * cube: host double[4] or NULL, receives {lo_x, lo_y, lo_z, L}.  stream: a
+ * cudaStream_t (NULL = legacy default stream).  The call returns after the
+ * work is complete.
+ * Errors: EINVAL (a null pointer, n < 1, n > BONSAI_NOALLOC_MAX_N, a
+ * non-finite position or a mass <= 0), ECUDA. */
+int bonsai_sfc_order_noalloc(const double *pos, const double *mass, int64_t n, uint64_t *keys,
+                             uint32_t *perm, double cube[4], void *stream);
+
 #ifdef __cplusplus
 }
 #endif

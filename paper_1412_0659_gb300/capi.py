@@ -31,8 +31,10 @@ EXPORTED = (
     "tree_set_velocities", "tree_step", "tree_get_state", "tree_get_forces",
     "bonsai_diagnostics", "tree_get_stats", "tree_solve_host", "tree_debug_cube",
     "tree_debug_keys", "tree_debug_nodes", "tree_debug_multipoles", "tree_debug_groups",
-    "bonsai_strerror",
+    "bonsai_strerror", "bonsai_sfc_order_noalloc",
 )
+
+BONSAI_NOALLOC_MAX_N = 1 << 20
 
 
 class BonsaiError(RuntimeError):
@@ -90,6 +92,7 @@ def load(path: str | None = None):
             "tree_debug_multipoles": (i32, [P, P, P, P]),
             "tree_debug_groups": (i32, [P, P, P, P, P]),
             "bonsai_strerror": (ctypes.c_char_p, [i32]),
+            "bonsai_sfc_order_noalloc": (i32, [P, P, i64, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -249,3 +252,21 @@ def tree_debug_groups(ctx, first=None, count=None, npp=None, npc=None) -> None:
 
 def bonsai_strerror(code: int) -> str:
     return strerror(code)
+
+
+def bonsai_sfc_order_noalloc(pos, mass, keys, perm, stream=None):
+    """Sorted Peano-Hilbert keys and order of pos/mass written into the
+    caller's keys (int64/uint64 CUDA tensor, n) and perm (int32 CUDA tensor,
+    n) without any device allocation; returns the cube (lo_x, lo_y, lo_z, L).
+    n is limited to BONSAI_NOALLOC_MAX_N."""
+    import torch
+    n = int(mass.numel())
+    if n > BONSAI_NOALLOC_MAX_N:
+        raise ValueError(f"bonsai_sfc_order_noalloc: n = {n} exceeds the fixed scratch limit "
+                         f"{BONSAI_NOALLOC_MAX_N}")
+    cube = (ctypes.c_double * 4)()
+    _check(load().bonsai_sfc_order_noalloc(_ptr(pos, torch.float64, 3 * n, "pos"),
+                                           _ptr(mass, torch.float64, n, "mass"), n,
+                                           _ptr(keys, None, n, "keys"), _ptr(perm, None, n, "perm"),
+                                           cube, _stream_handle(stream)), "bonsai_sfc_order_noalloc")
+    return list(cube)

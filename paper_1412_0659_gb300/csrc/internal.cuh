@@ -163,6 +163,12 @@ size_t sort_hist_elems(int64_t n);
 void launch_unpermute_state(bonsai_ctx *c, double *pos, double *vel, double *mass);
 void launch_unpermute_forces(bonsai_ctx *c, float *acc, float *pot);
 void launch_permute_in_vel(bonsai_ctx *c, const double *vel);
+// context-free variants on explicit buffers (noalloc.cu)
+int launch_cube_keys_into(cudaStream_t s, int sm_count, const double *pos, const double *mass,
+                          int64_t n, BoxPartial *part, int max_part, DevScalars *dsc,
+                          uint64_t *key, uint32_t *val);
+int radix_sort_pairs_into(cudaStream_t s, int64_t n, uint64_t *ka, uint64_t *kb, uint32_t *va,
+                          uint32_t *vb, uint32_t *hist, uint32_t *tmp);
 
 inline int grid_for(int64_t n, int block, int max_blocks = 1 << 30) {
     int64_t g = (n + block - 1) / block;

@@ -200,6 +200,19 @@ void launch_bbox(bonsai_ctx *c, const double *pos, const double *mass, int64_t n
     c->launches += 2;
 }
 
+// Bounding cube and keys into explicit buffers (no context): part holds at
+// most max_part block partials.  Returns the number of kernels launched.
+int launch_cube_keys_into(cudaStream_t s, int sm_count, const double *pos, const double *mass,
+                          int64_t n, BoxPartial *part, int max_part, DevScalars *dsc,
+                          uint64_t *key, uint32_t *val) {
+    const int cap = sm_count * 4 < max_part ? sm_count * 4 : max_part;
+    const int nb = grid_for(n, BOX_BLOCK * 4, cap);
+    k_box_partial<<<nb, BOX_BLOCK, 0, s>>>(pos, mass, n, part);
+    k_box_final<<<1, BOX_BLOCK, 0, s>>>(part, nb, dsc);
+    k_keys<<<grid_for(n, 256, sm_count * 16), 256, 0, s>>>(pos, n, dsc, key, val);
+    return 3;
+}
+
 void launch_keys(bonsai_ctx *c, const double *pos, int64_t n) {
     k_keys<<<grid_for(n, 256, c->sm_count * 16), 256, 0, c->stream>>>(pos, n, c->dsc, c->key.p,
                                                                        c->val.p);

@@ -220,6 +220,25 @@ size_t scan_tmp_elems(int64_t n) {
 
 size_t sort_hist_elems(int64_t n) { return 256 * (size_t)((n + SORT_TILE - 1) / SORT_TILE) + 64; }
 
+// The same eight passes on explicit buffers: (ka, va) hold the input and the
+// result, (kb, vb) are the second ping-pong half, hist holds
+// sort_hist_elems(n) entries and tmp scan_tmp_elems(256 * tiles) entries.
+// Returns the number of kernels launched.
+int radix_sort_pairs_into(cudaStream_t s, int64_t n, uint64_t *ka, uint64_t *kb, uint32_t *va,
+                          uint32_t *vb, uint32_t *hist, uint32_t *tmp) {
+    const int nb = (int)((n + SORT_TILE - 1) / SORT_TILE);
+    const int64_t nh = 256ll * nb;
+    int launches = 0;
+    for (int shift = 0; shift < 64; shift += 8) {
+        k_hist<<<nb, SORT_BLOCK, 0, s>>>(ka, n, shift, hist, nb);
+        launches += scan_rec(s, hist, hist, nh, tmp) + 2;
+        k_scatter<<<nb, SORT_BLOCK, 0, s>>>(ka, va, kb, vb, n, shift, hist, nb);
+        uint64_t *tk = ka; ka = kb; kb = tk;
+        uint32_t *tv = va; va = vb; vb = tv;
+    }
+    return launches;
+}
+
 void radix_sort_pairs(bonsai_ctx *c, int64_t n) {
     const int nb = (int)((n + SORT_TILE - 1) / SORT_TILE);
     const int64_t nh = 256ll * nb;
