@@ -128,47 +128,46 @@ __device__ __forceinline__ void pp_one(const float4 s, int sid, int tid, float t
     az = fmaf(mr3, dz, az);
 }
 
+// Targets of one lane: two slots.  A group of c targets is spread over
+// T2 = ceil(c/2) lanes (slot k of lane tl holds target tl + k*T2), and the
+// S = floor(32/T2) copies of that layout each take every S-th list entry;
+// the S partial sums of a target are added with shuffles at the end.  This
+// keeps most lanes busy for the small groups that dominate real trees.
 struct Targets {
     float x[2], y[2], z[2];
     float ax[2], ay[2], az[2], ph[2];
     int id[2];
 };
 
-template <int NT>
-__device__ __forceinline__ void eval_pc(const WarpLists &L, uint32_t head, int cnt, Targets &t,
+__device__ __forceinline__ void eval_pc(const WarpLists &L, int j0, int cnt, int S, Targets &t,
                                         float eps2) {
 #pragma unroll 2
-    for (int j = 0; j < cnt; ++j) {
-        const int s = (head + j) & (RING - 1);
-        const float4 a = L.ca[s], b = L.cb[s], c = L.cc[s];
+    for (int j = j0; j < cnt; j += S) {
+        const float4 a = L.ca[j], b = L.cb[j], c = L.cc[j];
 #pragma unroll
-        for (int k = 0; k < NT; ++k)
+        for (int k = 0; k < 2; ++k)
             pc_one(a, b, c, t.x[k], t.y[k], t.z[k], eps2, t.ax[k], t.ay[k], t.az[k], t.ph[k]);
     }
 }
 
-template <int NT>
-__device__ __forceinline__ void eval_pp(const WarpLists &L, uint32_t head, int cnt, Targets &t,
+__device__ __forceinline__ void eval_pp(const WarpLists &L, int j0, int cnt, int S, Targets &t,
                                         float eps2) {
-#pragma unroll 4
-    for (int j = 0; j < cnt; ++j) {
-        const int s = (head + j) & (RING - 1);
-        const float4 p = L.pp[s];
-        const int sid = L.pid[s];
+#pragma unroll 2
+    for (int j = j0; j < cnt; j += S) {
+        const float4 p = L.pp[j];
+        const int sid = L.pid[j];
 #pragma unroll
-        for (int k = 0; k < NT; ++k)
+        for (int k = 0; k < 2; ++k)
             pp_one(p, sid, t.id[k], t.x[k], t.y[k], t.z[k], eps2, t.ax[k], t.ay[k], t.az[k],
                    t.ph[k]);
     }
 }
 
-__device__ __forceinline__ void eval_pc_any(const WarpLists &L, uint32_t head, int cnt,
-                                            Targets &t, float eps2, bool two) {
-    if (two) eval_pc<2>(L, head, cnt, t, eps2); else eval_pc<1>(L, head, cnt, t, eps2);
-}
-__device__ __forceinline__ void eval_pp_any(const WarpLists &L, uint32_t head, int cnt,
-                                            Targets &t, float eps2, bool two) {
-    if (two) eval_pp<2>(L, head, cnt, t, eps2); else eval_pp<1>(L, head, cnt, t, eps2);
+// Sum the S partial results of a target into the lanes of the first copy.
+__device__ __forceinline__ float sum_copies(float v, int lane, int T2, int S) {
+    float r = v;
+    for (int m = 1; m < S; ++m) r += __shfl_sync(0xffffffffu, v, min(lane + m * T2, 31));
+    return r;
 }
 
 __global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(const WalkArgs A) {
@@ -190,12 +189,17 @@ __global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(const WalkArgs A) {
 
         const uint32_t gf = A.gfirst[g], gc = A.gcount[g];
         const float4 box = A.gbox[g], half = A.ghalf[g], clo = A.glo[g];
-        const bool two = gc > 32u;
+        // lane layout: T2 lanes hold the targets, S copies split the sources
+        const int T2 = (int)((gc + 1u) >> 1);
+        const int S = 32 / T2;
+        const int cp = lane / T2;            // this lane's copy
+        const int tl = lane - cp * T2;       // this lane's target column
+        const bool active = cp < S;
         Targets t;
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
-            const uint32_t li = lane + 32u * k;
-            const bool v = li < gc;
+            const uint32_t li = (uint32_t)(tl + k * T2);
+            const bool v = active && li < gc;
             const int64_t i = gf + (v ? li : 0u);
             const float4 h = A.body_hi[i], l = A.body_lo[i];
             t.x[k] = (h.x - box.x) + (l.x - clo.x);
@@ -204,6 +208,7 @@ __global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(const WalkArgs A) {
             t.id[k] = v ? (int)i : -1;
             t.ax[k] = t.ay[k] = t.az[k] = t.ph[k] = 0.0f;
         }
+        const int j0 = active ? cp : 1 << 30;  // first ring entry of this lane
 
         uint32_t pc_head = 0, pc_tail = 0, pp_head = 0, pp_tail = 0;
         uint32_t npc = 0, npp = 0;
@@ -286,14 +291,17 @@ __global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(const WalkArgs A) {
                     pp_tail += min(32u, ltot - r);
                     __syncwarp();
                     if (pp_tail - pp_head >= 32u) {
-                        eval_pp_any(L, pp_head, 32, t, eps2, two);
+                        // the head is a multiple of 32: the 32 entries do not wrap
+                        const int hb = (int)(pp_head & (RING - 1));
+                        eval_pp(L, hb + j0, hb + 32, S, t, eps2);
                         pp_head += 32;
                         __syncwarp();
                     }
                 }
                 __syncwarp();
                 while (pc_tail - pc_head >= 32u) {
-                    eval_pc_any(L, pc_head, 32, t, eps2, two);
+                    const int hb = (int)(pc_head & (RING - 1));
+                    eval_pc(L, hb + j0, hb + 32, S, t, eps2);
                     pc_head += 32;
                 }
                 __syncwarp();
@@ -306,18 +314,24 @@ __global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(const WalkArgs A) {
             ncur = nnext;
             maxf = max(maxf, ncur);
         }
-        // drain the rings
-        eval_pc_any(L, pc_head, (int)(pc_tail - pc_head), t, eps2, two);
-        eval_pp_any(L, pp_head, (int)(pp_tail - pp_head), t, eps2, two);
+        // drain the rings: fewer than 32 entries each, starting at a multiple of 32
+        {
+            const int hb = (int)(pc_head & (RING - 1));
+            eval_pc(L, hb + j0, hb + (int)(pc_tail - pc_head), S, t, eps2);
+            const int hp = (int)(pp_head & (RING - 1));
+            eval_pp(L, hp + j0, hp + (int)(pp_tail - pp_head), S, t, eps2);
+        }
         __syncwarp();
 
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
-            const uint32_t li = lane + 32u * k;
-            if (li < gc) {
+            const float ax = A.G * sum_copies(t.ax[k], lane, T2, S);
+            const float ay = A.G * sum_copies(t.ay[k], lane, T2, S);
+            const float az = A.G * sum_copies(t.az[k], lane, T2, S);
+            const float ph = A.G * sum_copies(t.ph[k], lane, T2, S);
+            const uint32_t li = (uint32_t)(tl + k * T2);
+            if (cp == 0 && li < gc) {
                 const int64_t i = gf + li;
-                const float ax = A.G * t.ax[k], ay = A.G * t.ay[k], az = A.G * t.az[k];
-                const float ph = A.G * t.ph[k];
                 A.acc[i] = ax;
                 A.acc[A.n + i] = ay;
                 A.acc[2 * A.n + i] = az;
