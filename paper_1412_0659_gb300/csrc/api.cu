@@ -130,7 +130,7 @@ int forces_internal(bonsai_ctx *c, float theta, float eps, float *acc_c, float *
         launch_cell_pack(c, theta);
         c->packed_theta = theta;
     }
-    int rc = walk_force(c, eps, acc_c, pot_c);
+    int rc = walk_force(c, theta, eps, acc_c, pot_c);
     if (rc) return rc;
     BGB_CUDA(cudaEventRecord(c->ev[4], c->stream));
     if ((rc = read_scalars(c))) return rc;

@@ -6,7 +6,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "../../include/bonsai_gb.h"
+#include "bonsai_gb.h"
 
 namespace bgb {
 
@@ -95,8 +95,8 @@ struct bonsai_ctx {
     bgb::DBuf<float4> cell_mac;      // {com_hi.xyz, r_open^2}
     bgb::DBuf<uint2> cell_topo;      // leaf: {first, count|LEAF}; internal: {child, nchild}
     bgb::DBuf<float4> cell_a;        // {com_lo.xyz, M}
-    bgb::DBuf<float4> cell_b;        // {Qxx, Qyy, Qzz, Qxy}
-    bgb::DBuf<float4> cell_c;        // {Qxz, Qyz, trQ/2, 0}
+    bgb::DBuf<float4> cell_b;        // -3 x {Qxx, Qyy, Qzz, Qxy}
+    bgb::DBuf<float4> cell_c;        // {-3 Qxz, -3 Qyz, -trQ/2, -3/2 trQ}
     int64_t level_start[bgb::MAX_LEVEL + 2];
 
     // groups
@@ -150,7 +150,7 @@ void launch_multipoles(bonsai_ctx *c);
 void launch_body_pack(bonsai_ctx *c);
 void launch_cell_pack(bonsai_ctx *c, float theta);
 // walk.cu
-int walk_force(bonsai_ctx *c, float eps, float *acc_caller, float *pot_caller);
+int walk_force(bonsai_ctx *c, float theta, float eps, float *acc_caller, float *pot_caller);
 // integrate.cu
 void launch_kick(bonsai_ctx *c, double h);
 void launch_drift(bonsai_ctx *c, double dt);

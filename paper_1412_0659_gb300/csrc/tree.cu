@@ -289,7 +289,9 @@ __device__ inline uint32_t quantise_q(double x, double lo, double scale) {
 // side and centre the middle of the level-l cube holding the node (taken
 // from its first particle's quantised coordinates); r_open^2 is rounded to
 // FP32 once.  com is split into an FP32 head (used by the opening test) and
-// remainder; Q and M are rounded to FP32; trQ/2 and -3/2 trQ are folded in.
+// remainder.  The force kernel reads Q' = -3 Q and the constants -trQ/2 and
+// -3/2 trQ (FP64, rounded to FP32 once), which fold Eq. 1-2 into fewer FP32
+// operations.
 __global__ void __launch_bounds__(256) k_cell_pack(
     const double *__restrict__ pos, int64_t n, const uint32_t *__restrict__ first,
     const uint32_t *__restrict__ level, const double *__restrict__ M, const double *__restrict__ com,
@@ -320,10 +322,11 @@ __global__ void __launch_bounds__(256) k_cell_pack(
     ca[i] = make_float4(cl[0], cl[1], cl[2], __double2float_rn(M[i]));
     double qxx = Q[i], qyy = Q[nn + i], qzz = Q[2 * nn + i];
     double tr = __dadd_rn(__dadd_rn(qxx, qyy), qzz);
-    cb[i] = make_float4(__double2float_rn(qxx), __double2float_rn(qyy), __double2float_rn(qzz),
-                        __double2float_rn(Q[3 * nn + i]));
-    cc[i] = make_float4(__double2float_rn(Q[4 * nn + i]), __double2float_rn(Q[5 * nn + i]),
-                        __double2float_rn(0.5 * tr), __double2float_rn(-1.5 * tr));
+    cb[i] = make_float4(__double2float_rn(-3.0 * qxx), __double2float_rn(-3.0 * qyy),
+                        __double2float_rn(-3.0 * qzz), __double2float_rn(-3.0 * Q[3 * nn + i]));
+    cc[i] = make_float4(__double2float_rn(-3.0 * Q[4 * nn + i]),
+                        __double2float_rn(-3.0 * Q[5 * nn + i]), __double2float_rn(-0.5 * tr),
+                        __double2float_rn(-1.5 * tr));
 }
 
 }  // namespace

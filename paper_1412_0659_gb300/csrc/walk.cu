@@ -31,8 +31,8 @@ constexpr int FCAP = 16384;    // frontier entries per buffer per warp
 
 struct __align__(16) WarpLists {
     float4 ca[RING];  // {dx, dy, dz, M}: cell com relative to the group centre
-    float4 cb[RING];  // {Qxx, Qyy, Qzz, Qxy}
-    float4 cc[RING];  // {Qxz, Qyz, trQ/2, -3/2 trQ}
+    float4 cb[RING];  // -3 x {Qxx, Qyy, Qzz, Qxy}
+    float4 cc[RING];  // {-3 Qxz, -3 Qyz, -trQ/2, -3/2 trQ}
     float4 pp[RING];  // {dx, dy, dz, m}: particle relative to the group centre
     int pid[RING];    // sorted index of the particle (self-pair mask)
 };
@@ -76,41 +76,43 @@ __device__ __forceinline__ uint32_t warp_excl_scan(uint32_t v, uint32_t &total) 
     return inc - v;
 }
 
-// Eq. 1-2 for one cell on one target; Plummer-softened in every power of s.
-// r = com - x_i; s^2 = r^2 + eps^2.
+// Eq. 1-2 for one cell on one target, Plummer-softened in every power of s:
+//   r = com - x_i, s^2 = r^2 + eps^2, u = 1/s, w = u^2,
+//   phi += -u (M + w (-trQ/2 + 3/2 rQr w))
+//   a   += u w (M + w (-3/2 trQ + 15/2 rQr w)) r - 3 u^5 Q r.
+// The cell record holds Q' = -3Q, so with q = r.Q'r w = -3 rQr w the two
+// brackets are M + w (c.z - q/2) and M + w (c.w - 5q/2), with c.z = -trQ/2
+// and c.w = -3/2 trQ; the last term is u w w (Q'r).  35 FP32 instructions.
 __device__ __forceinline__ void pc_one(const float4 a, const float4 b, const float4 c, float tx,
                                        float ty, float tz, float eps2, float &ax, float &ay,
                                        float &az, float &ph) {
-    const float dx = a.x - tx, dy = a.y - ty, dz = a.z - tz;
-    float r2 = fmaf(dx, dx, eps2);
-    r2 = fmaf(dy, dy, r2);
-    r2 = fmaf(dz, dz, r2);
-    const float rinv = rsqrtf(r2);
-    const float rinv2 = rinv * rinv;
-    const float Mr = a.w * rinv;        // M/s
-    const float rinv3 = rinv * rinv2;   // 1/s^3
-    const float rinv5 = rinv3 * rinv2;  // 1/s^5
-    const float qx = fmaf(b.x, dx, fmaf(b.w, dy, c.x * dz));
-    const float qy = fmaf(b.w, dx, fmaf(b.y, dy, c.y * dz));
-    const float qz = fmaf(c.x, dx, fmaf(c.y, dy, b.z * dz));
-    const float rQr = fmaf(dx, qx, fmaf(dy, qy, dz * qz));
-    const float rQr5 = rQr * rinv5;     // r^T Q r / s^5
-    ph = ph - Mr;
-    ph = fmaf(c.z, rinv3, ph);          // + trQ/2 / s^3
-    ph = fmaf(-1.5f, rQr5, ph);         // - 3/2 rQr / s^5
-    float A = Mr * rinv2;               // M/s^3
-    A = fmaf(c.w, rinv5, A);            // - 3/2 trQ / s^5
-    A = fmaf(7.5f, rQr5 * rinv2, A);    // + 15/2 rQr / s^7
-    const float B = -3.0f * rinv5;      // - 3 (Q r) / s^5
-    ax = fmaf(A, dx, ax);
-    ay = fmaf(A, dy, ay);
-    az = fmaf(A, dz, az);
+    const float rx = a.x - tx, ry = a.y - ty, rz = a.z - tz;
+    float s2 = fmaf(rx, rx, eps2);
+    s2 = fmaf(ry, ry, s2);
+    s2 = fmaf(rz, rz, s2);
+    const float u = rsqrtf(s2);
+    const float w = u * u;
+    const float qx = fmaf(b.x, rx, fmaf(b.w, ry, c.x * rz));  // Q'r
+    const float qy = fmaf(b.w, rx, fmaf(b.y, ry, c.y * rz));
+    const float qz = fmaf(c.x, rx, fmaf(c.y, ry, b.z * rz));
+    const float q = fmaf(rx, qx, fmaf(ry, qy, rz * qz)) * w;  // r.Q'r / s^2
+    const float tp = fmaf(w, fmaf(-0.5f, q, c.z), a.w);
+    ph = fmaf(-u, tp, ph);
+    const float uw = u * w;
+    const float A = uw * fmaf(w, fmaf(-2.5f, q, c.w), a.w);
+    const float B = uw * w;
+    ax = fmaf(A, rx, ax);
+    ay = fmaf(A, ry, ay);
+    az = fmaf(A, rz, az);
     ax = fmaf(B, qx, ax);
     ay = fmaf(B, qy, ay);
     az = fmaf(B, qz, az);
 }
 
-// Monopole p-p term; the self pair (same sorted index) contributes nothing.
+// Monopole p-p term.  With MASK the self pair (same sorted index) is skipped
+// here; without it the self pair adds exactly -m_i rsqrt(eps^2) to phi and
+// nothing to a (r = 0), which the caller removes once per target.
+template <bool MASK>
 __device__ __forceinline__ void pp_one(const float4 s, int sid, int tid, float tx, float ty,
                                        float tz, float eps2, float &ax, float &ay, float &az,
                                        float &ph) {
@@ -119,7 +121,7 @@ __device__ __forceinline__ void pp_one(const float4 s, int sid, int tid, float t
     r2 = fmaf(dy, dy, r2);
     r2 = fmaf(dz, dz, r2);
     float rinv = rsqrtf(r2);
-    rinv = (sid == tid) ? 0.0f : rinv;
+    if (MASK) rinv = (sid == tid) ? 0.0f : rinv;
     const float mr = s.w * rinv;
     const float mr3 = mr * rinv * rinv;
     ph = ph - mr;
@@ -150,6 +152,7 @@ __device__ __forceinline__ void eval_pc(const WarpLists &L, int j0, int cnt, int
     }
 }
 
+template <bool MASK>
 __device__ __forceinline__ void eval_pp(const WarpLists &L, int j0, int cnt, int S, Targets &t,
                                         float eps2) {
 #pragma unroll 2
@@ -158,8 +161,8 @@ __device__ __forceinline__ void eval_pp(const WarpLists &L, int j0, int cnt, int
         const int sid = L.pid[j];
 #pragma unroll
         for (int k = 0; k < 2; ++k)
-            pp_one(p, sid, t.id[k], t.x[k], t.y[k], t.z[k], eps2, t.ax[k], t.ay[k], t.az[k],
-                   t.ph[k]);
+            pp_one<MASK>(p, sid, t.id[k], t.x[k], t.y[k], t.z[k], eps2, t.ax[k], t.ay[k], t.az[k],
+                         t.ph[k]);
     }
 }
 
@@ -170,6 +173,13 @@ __device__ __forceinline__ float sum_copies(float v, int lane, int T2, int S) {
     return r;
 }
 
+// MASK: skip the self pair inside the p-p loop (needed when eps = 0, or when
+// theta >= 1/sqrt(3) so that a target's own leaf may be accepted as a cell).
+// Otherwise every target meets itself exactly once in its p-p list: for
+// theta < 1/sqrt(3) a cell containing the group is always opened (the
+// distance from its com to the group box is at most sqrt(3) l < l/theta),
+// and the self term is removed after the loop.
+template <bool MASK>
 __global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(const WalkArgs A) {
     __shared__ WarpLists lists[WALK_WARPS];
     const int lane = threadIdx.x & 31;
@@ -196,6 +206,7 @@ __global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(const WalkArgs A) {
         const int tl = lane - cp * T2;       // this lane's target column
         const bool active = cp < S;
         Targets t;
+        float self[2];
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
             const uint32_t li = (uint32_t)(tl + k * T2);
@@ -207,6 +218,7 @@ __global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(const WalkArgs A) {
             t.z[k] = (h.z - box.z) + (l.z - clo.z);
             t.id[k] = v ? (int)i : -1;
             t.ax[k] = t.ay[k] = t.az[k] = t.ph[k] = 0.0f;
+            self[k] = h.w;
         }
         const int j0 = active ? cp : 1 << 30;  // first ring entry of this lane
 
@@ -252,10 +264,24 @@ __global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(const WalkArgs A) {
                 pc_tail += __popc(am);
                 npc += __popc(am);
 
-                // opened internal cells -> next frontier
-                uint32_t ntot;
+                // one warp scan for both the children of opened internal cells
+                // (low 9 bits: at most 8 per lane) and the particles of opened
+                // leaves (high bits); two scans when a leaf is very large
                 const uint32_t nch = (valid && open && !leaf) ? tp.y : 0u;
-                const uint32_t noff = warp_excl_scan(nch, ntot);
+                const uint32_t lc = (valid && open && leaf) ? (tp.y & ~LEAF_FLAG) : 0u;
+                uint32_t noff, ntot, loff, ltot;
+                if (__any_sync(0xffffffffu, lc > 4096u)) {
+                    noff = warp_excl_scan(nch, ntot);
+                    loff = warp_excl_scan(lc, ltot);
+                } else {
+                    uint32_t tot;
+                    const uint32_t off = warp_excl_scan(nch | (lc << 9), tot);
+                    noff = off & 511u;
+                    ntot = tot & 511u;
+                    loff = off >> 9;
+                    ltot = tot >> 9;
+                }
+                // opened internal cells -> next frontier
                 if (nnext + ntot > (uint32_t)FCAP) {
                     overflow = true;
                 } else {
@@ -264,9 +290,6 @@ __global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(const WalkArgs A) {
                 }
 
                 // opened leaves -> p-p ring, 32 particles per round
-                uint32_t ltot;
-                const uint32_t lc = (valid && open && leaf) ? (tp.y & ~LEAF_FLAG) : 0u;
-                const uint32_t loff = warp_excl_scan(lc, ltot);
                 npp += ltot;
                 for (uint32_t r = 0; r < ltot; r += 32) {
                     const uint32_t k = r + lane;
@@ -293,7 +316,7 @@ __global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(const WalkArgs A) {
                     if (pp_tail - pp_head >= 32u) {
                         // the head is a multiple of 32: the 32 entries do not wrap
                         const int hb = (int)(pp_head & (RING - 1));
-                        eval_pp(L, hb + j0, hb + 32, S, t, eps2);
+                        eval_pp<MASK>(L, hb + j0, hb + 32, S, t, eps2);
                         pp_head += 32;
                         __syncwarp();
                     }
@@ -319,7 +342,7 @@ __global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(const WalkArgs A) {
             const int hb = (int)(pc_head & (RING - 1));
             eval_pc(L, hb + j0, hb + (int)(pc_tail - pc_head), S, t, eps2);
             const int hp = (int)(pp_head & (RING - 1));
-            eval_pp(L, hp + j0, hp + (int)(pp_tail - pp_head), S, t, eps2);
+            eval_pp<MASK>(L, hp + j0, hp + (int)(pp_tail - pp_head), S, t, eps2);
         }
         __syncwarp();
 
@@ -328,7 +351,9 @@ __global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(const WalkArgs A) {
             const float ax = A.G * sum_copies(t.ax[k], lane, T2, S);
             const float ay = A.G * sum_copies(t.ay[k], lane, T2, S);
             const float az = A.G * sum_copies(t.az[k], lane, T2, S);
-            const float ph = A.G * sum_copies(t.ph[k], lane, T2, S);
+            float phs = sum_copies(t.ph[k], lane, T2, S);
+            if (!MASK) phs = phs + self[k] * rsqrtf(eps2);  // remove the self pair
+            const float ph = A.G * phs;
             const uint32_t li = (uint32_t)(tl + k * T2);
             if (cp == 0 && li < gc) {
                 const int64_t i = gf + li;
@@ -361,7 +386,7 @@ __global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(const WalkArgs A) {
 
 int walk_resident_warps(bonsai_ctx *c) {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk, WALK_WARPS * 32, 0) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk<true>, WALK_WARPS * 32, 0) !=
             cudaSuccess ||
         per_sm < 1)
         per_sm = 1;
@@ -370,7 +395,8 @@ int walk_resident_warps(bonsai_ctx *c) {
 
 size_t walk_frontier_elems(int warps) { return (size_t)warps * 2 * FCAP; }
 
-int walk_force(bonsai_ctx *c, float eps, float *acc_c, float *pot_c) {
+int walk_force(bonsai_ctx *c, float theta, float eps, float *acc_c, float *pot_c) {
+    const bool mask_self = !(eps > 0.0f) || !(theta < 0.57f);
     WalkArgs a;
     a.mac = c->cell_mac.p;
     a.topo = c->cell_topo.p;
@@ -399,7 +425,10 @@ int walk_force(bonsai_ctx *c, float eps, float *acc_c, float *pot_c) {
     a.sc = c->dsc;
     const int blocks = c->walk_warps / WALK_WARPS;
     cudaEventRecord(c->ev[8], c->stream);
-    k_walk<<<blocks, WALK_WARPS * 32, 0, c->stream>>>(a);
+    if (mask_self)
+        k_walk<true><<<blocks, WALK_WARPS * 32, 0, c->stream>>>(a);
+    else
+        k_walk<false><<<blocks, WALK_WARPS * 32, 0, c->stream>>>(a);
     cudaEventRecord(c->ev[9], c->stream);
     c->launches += 1;
     return cudaPeekAtLastError() == cudaSuccess ? BONSAI_OK : BONSAI_ECUDA;
