@@ -83,6 +83,15 @@ def _load():
             "orc_num_threads": (i32, []),
             "orc_eval_source": (None, [P, f64, P, f64, f64, P, P]),
             "orc_group_lists": (i32, [P, f32, i64, P, P, i64, P]),
+            "orc_eval_source_vjp": (None, [P, f64, P, f64, f64, P, f64, P, P, P]),
+            "orc_tree_freeze_lists": (i32, [P, f32]),
+            "orc_tree_frozen_forces": (i32, [P, f64, f64, P, P, P, P]),
+            "orc_tree_frozen_vjp": (i32, [P, f64, f64, P, P, P, P, P, P]),
+            "orc_direct_vjp": (None, [i64, P, P, f64, f64, P, P, P, P]),
+            "orc_kdk_plan_build": (P, [i64, P, P, P, i32, f64, f32, f64, f64, i32, i32]),
+            "orc_kdk_plan_free": (None, [P]),
+            "orc_kdk_plan_run": (i32, [P, P, P, P, P, P]),
+            "orc_kdk_plan_vjp": (i32, [P, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -220,6 +229,45 @@ class Tree:
             raise MemoryError("oracle forces failed")
         return acc, pot, g_npp, g_npc, (int(counts[0]), int(counts[1]))
 
+    # -- adjoint with frozen lists (sorted order unless stated) -------------
+    def freeze_lists(self, theta: float):
+        """Record every group's interaction lists at this opening angle."""
+        if self._lib.orc_tree_freeze_lists(self._h, float(theta)):
+            raise MemoryError("freeze_lists failed")
+        self._frozen = float(theta)
+
+    def to_sorted(self, a):
+        _, perm = self.keys()
+        a = np.asarray(a, np.float64)
+        return np.ascontiguousarray(a[..., perm])
+
+    def to_caller(self, a):
+        _, perm = self.keys()
+        out = np.empty_like(a)
+        out[..., perm] = a
+        return out
+
+    def frozen_forces(self, eps: float, G: float, pos_sorted, mass_sorted):
+        x = _f64(pos_sorted, (3, self.n))
+        m = _f64(mass_sorted, (self.n,))
+        acc = np.zeros((3, self.n))
+        pot = np.zeros(self.n)
+        if self._lib.orc_tree_frozen_forces(self._h, float(eps), float(G), _p(x), _p(m), _p(acc), _p(pot)):
+            raise RuntimeError("frozen_forces: call freeze_lists first")
+        return acc, pot
+
+    def frozen_vjp(self, eps: float, G: float, pos_sorted, mass_sorted, lam_sorted, mu_sorted=None):
+        x = _f64(pos_sorted, (3, self.n))
+        m = _f64(mass_sorted, (self.n,))
+        lam = _f64(lam_sorted, (3, self.n))
+        mu = None if mu_sorted is None else _f64(mu_sorted, (self.n,))
+        gx = np.zeros((3, self.n))
+        gm = np.zeros(self.n)
+        if self._lib.orc_tree_frozen_vjp(self._h, float(eps), float(G), _p(x), _p(m), _p(lam), _p(mu),
+                                         _p(gx), _p(gm)):
+            raise RuntimeError("frozen_vjp: call freeze_lists first")
+        return gx, gm
+
     def forces_groups(self, theta: float, eps: float, G: float, groups):
         """FP64 tree forces for the listed groups (sorted order, NaN elsewhere);
         returns (acc, pot, g_npp, g_npc, (n_pp, n_pc)) like forces_sorted."""
@@ -255,6 +303,75 @@ def eval_source(r, m: float, Q=None, eps: float = 0.0, G: float = 1.0):
     a = np.zeros(3)
     _load().orc_eval_source(_p(r), float(m), _p(Qa), float(eps), float(G), _p(phi), _p(a))
     return float(phi[0]), a
+
+
+def eval_source_vjp(r, m: float, Q=None, eps: float = 0.0, G: float = 1.0, lam=(0, 0, 0), mu: float = 0.0):
+    """Gradient of lam.a + mu phi for one source w.r.t. (r, m, Q)."""
+    r = _f64(r, (3,))
+    Qa = None if Q is None else _f64(Q, (6,))
+    lam = _f64(lam, (3,))
+    gr = np.zeros(3)
+    gm = np.zeros(1)
+    gq = np.zeros(6)
+    _load().orc_eval_source_vjp(_p(r), float(m), _p(Qa), float(eps), float(G), _p(lam), float(mu),
+                                _p(gr), _p(gm), _p(gq))
+    return gr, float(gm[0]), gq
+
+
+def direct_vjp(pos, mass, eps: float, G: float, lam, mu=None):
+    """O1 adjoint: gradient of sum lam.a + mu phi of direct summation."""
+    pos = _f64(pos)
+    n = pos.shape[1]
+    mass = _f64(mass, (n,))
+    lam = _f64(lam, (3, n))
+    mu = None if mu is None else _f64(mu, (n,))
+    gx = np.zeros((3, n))
+    gm = np.zeros(n)
+    _load().orc_direct_vjp(n, _p(pos), _p(mass), float(eps), float(G), _p(lam), _p(mu), _p(gx), _p(gm))
+    return gx, gm
+
+
+class KdkPlan:
+    """K kick-drift-kick steps with each step's tree and lists frozen at the
+    nominal trajectory; run() re-integrates from perturbed initial data with
+    those frozen structures, vjp() is the exact reverse of run()."""
+
+    def __init__(self, pos0, vel0, mass, nsteps: int, dt: float, theta: float, eps: float,
+                 G: float = 1.0, nleaf: int = NLEAF, ncrit: int = NCRIT):
+        self._lib = _load()
+        pos0 = _f64(pos0)
+        self.n = pos0.shape[1]
+        vel0 = _f64(vel0, (3, self.n))
+        self.mass = _f64(mass, (self.n,))
+        h = self._lib.orc_kdk_plan_build(self.n, _p(pos0), _p(vel0), _p(self.mass), int(nsteps), float(dt),
+                                         float(theta), float(eps), float(G), nleaf, ncrit)
+        if not h:
+            raise MemoryError("kdk plan failed")
+        self._h = ctypes.c_void_p(h)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None:
+            self._lib.orc_kdk_plan_free(h)
+            self._h = None
+
+    def run(self, pos0, vel0, mass=None):
+        mass = self.mass if mass is None else _f64(mass, (self.n,))
+        pos0 = _f64(pos0, (3, self.n))
+        vel0 = _f64(vel0, (3, self.n))
+        pos = np.zeros((3, self.n))
+        vel = np.zeros((3, self.n))
+        if self._lib.orc_kdk_plan_run(self._h, _p(pos0), _p(vel0), _p(mass), _p(pos), _p(vel)):
+            raise MemoryError("kdk run failed")
+        return pos, vel
+
+    def vjp(self, xbar, vbar, mbar=None):
+        xb = _f64(xbar, (3, self.n)).copy()
+        vb = _f64(vbar, (3, self.n)).copy()
+        mb = np.zeros(self.n) if mbar is None else _f64(mbar, (self.n,)).copy()
+        if self._lib.orc_kdk_plan_vjp(self._h, _p(self.mass), _p(xb), _p(vb), _p(mb)):
+            raise MemoryError("kdk vjp failed")
+        return xb, vb, mb
 
 
 def direct_forces(pos, mass, eps: float, G: float = 1.0, targets=None):

@@ -157,6 +157,9 @@ typedef struct orc_tree {
     int64_t ngroups;
     uint32_t *gfirst, *gcount;
     double *gcentre, *ghalf; /* [3][ng] */
+    /* frozen interaction lists (adjoint): per group, offsets into the lists */
+    int64_t *pc_off, *lf_off;
+    uint32_t *pc_list, *lf_list;
 } orc_tree;
 
 typedef struct {
@@ -286,22 +289,23 @@ static int orc_make_groups(orc_tree *t) {
  *    second order about the com gives exactly Eq. 1 in that case.  Leaves
  *    sum their particles; internal cells combine children by the parallel-
  *    axis rule.  Q component order: xx, yy, zz, xy, xz, yz.                 */
-static void orc_multipoles(orc_tree *t) {
+static void orc_upward(const orc_tree *t, const double *x, const double *m, double *Mo,
+                       double *como, double *Qo) {
     int64_t nn = t->nnodes, n = t->n;
     for (int64_t i = nn - 1; i >= 0; --i) {
         double M = 0.0, s[3] = {0.0, 0.0, 0.0}, com[3], Q[6] = {0, 0, 0, 0, 0, 0};
         if (t->nchild[i] == 0) {
             uint32_t f = t->first[i], c = t->count[i];
             for (uint32_t j = f; j < f + c; ++j) {
-                M = M + t->m[j];
-                for (int d = 0; d < 3; ++d) s[d] = s[d] + t->m[j] * t->x[(size_t)d * n + j];
+                M = M + m[j];
+                for (int d = 0; d < 3; ++d) s[d] = s[d] + m[j] * x[(size_t)d * n + j];
             }
             for (int d = 0; d < 3; ++d) com[d] = s[d] / M;
             for (uint32_t j = f; j < f + c; ++j) {
-                double dx = t->x[j] - com[0];
-                double dy = t->x[(size_t)n + j] - com[1];
-                double dz = t->x[2 * (size_t)n + j] - com[2];
-                double mj = t->m[j];
+                double dx = x[j] - com[0];
+                double dy = x[(size_t)n + j] - com[1];
+                double dz = x[2 * (size_t)n + j] - com[2];
+                double mj = m[j];
                 Q[0] = Q[0] + (mj * dx) * dx;
                 Q[1] = Q[1] + (mj * dy) * dy;
                 Q[2] = Q[2] + (mj * dz) * dz;
@@ -312,26 +316,33 @@ static void orc_multipoles(orc_tree *t) {
         } else {
             uint32_t c0 = t->child[i], nc = t->nchild[i];
             for (uint32_t k = c0; k < c0 + nc; ++k) {
-                M = M + t->M[k];
-                for (int d = 0; d < 3; ++d) s[d] = s[d] + t->M[k] * t->com[(size_t)d * nn + k];
+                M = M + Mo[k];
+                for (int d = 0; d < 3; ++d) s[d] = s[d] + Mo[k] * como[(size_t)d * nn + k];
             }
             for (int d = 0; d < 3; ++d) com[d] = s[d] / M;
             for (uint32_t k = c0; k < c0 + nc; ++k) {
-                double dx = t->com[k] - com[0];
-                double dy = t->com[(size_t)nn + k] - com[1];
-                double dz = t->com[2 * (size_t)nn + k] - com[2];
-                double Mk = t->M[k];
-                Q[0] = Q[0] + (t->Q[k] + (Mk * dx) * dx);
-                Q[1] = Q[1] + (t->Q[(size_t)nn + k] + (Mk * dy) * dy);
-                Q[2] = Q[2] + (t->Q[2 * (size_t)nn + k] + (Mk * dz) * dz);
-                Q[3] = Q[3] + (t->Q[3 * (size_t)nn + k] + (Mk * dx) * dy);
-                Q[4] = Q[4] + (t->Q[4 * (size_t)nn + k] + (Mk * dx) * dz);
-                Q[5] = Q[5] + (t->Q[5 * (size_t)nn + k] + (Mk * dy) * dz);
+                double dx = como[k] - com[0];
+                double dy = como[(size_t)nn + k] - com[1];
+                double dz = como[2 * (size_t)nn + k] - com[2];
+                double Mk = Mo[k];
+                Q[0] = Q[0] + (Qo[k] + (Mk * dx) * dx);
+                Q[1] = Q[1] + (Qo[(size_t)nn + k] + (Mk * dy) * dy);
+                Q[2] = Q[2] + (Qo[2 * (size_t)nn + k] + (Mk * dz) * dz);
+                Q[3] = Q[3] + (Qo[3 * (size_t)nn + k] + (Mk * dx) * dy);
+                Q[4] = Q[4] + (Qo[4 * (size_t)nn + k] + (Mk * dx) * dz);
+                Q[5] = Q[5] + (Qo[5 * (size_t)nn + k] + (Mk * dy) * dz);
             }
         }
-        t->M[i] = M;
-        for (int d = 0; d < 3; ++d) t->com[(size_t)d * nn + i] = com[d];
-        for (int k = 0; k < 6; ++k) t->Q[(size_t)k * nn + i] = Q[k];
+        Mo[i] = M;
+        for (int d = 0; d < 3; ++d) como[(size_t)d * nn + i] = com[d];
+        for (int k = 0; k < 6; ++k) Qo[(size_t)k * nn + i] = Q[k];
+    }
+}
+
+static void orc_multipoles(orc_tree *t) {
+    int64_t nn = t->nnodes, n = t->n;
+    orc_upward(t, t->x, t->m, t->M, t->com, t->Q);
+    for (int64_t i = 0; i < nn; ++i) {
         /* geometric cube: the level-l octant holding the node's particles */
         uint32_t l = t->level[i];
         double side = ldexp(t->L, -(int)l);
@@ -350,6 +361,7 @@ void orc_tree_free(orc_tree *t) {
     free(t->parent);
     free(t->M); free(t->com); free(t->Q); free(t->centre); free(t->side);
     free(t->gfirst); free(t->gcount); free(t->gcentre); free(t->ghalf);
+    free(t->pc_off); free(t->lf_off); free(t->pc_list); free(t->lf_list);
     free(t);
 }
 
@@ -809,4 +821,415 @@ int orc_num_threads(void) {
 #else
     return 1;
 #endif
+}
+
+/* ======================================================================== */
+/* Adjoint (vector-Jacobian products) with the tree and lists frozen.       */
+/* The paper has no adjoint; this is the exact derivative of the tree-force */
+/* map of Eq. 1-2 for fixed node membership and fixed interaction lists:    */
+/* the multipoles (M, com, Q) stay functions of the particles, so gradients */
+/* reach particles both as p-p sources and through every cell they are in.  */
+/* ======================================================================== */
+
+/* Gradient of  lam . a + mu phi  (Eq. 1-2 for one source, without G) with
+ * respect to r = source - target, the source mass m and its quadrupole Q
+ * (Q may be NULL).  With s^2 = |r|^2 + eps^2 and u = 1/s:
+ *   monopole:  a = m u^3 r,  phi = -m u;
+ *   quadrupole: phi_Q = trQ u^3/2 - 3/2 rQr u^5,
+ *               a_Q = (-3/2 trQ u^5 + 15/2 rQr u^7) r - 3 u^5 Qr.
+ * Adds to g_r[3], *g_m and g_Q[6] (the gradient with respect to the
+ * symmetric matrix Q, components xx, yy, zz, xy, xz, yz, not doubled).    */
+static void orc_eq12_vjp(const double r[3], double m, const double *Q, double eps2,
+                         const double lam[3], double mu, double g_r[3], double *g_m,
+                         double *g_Q) {
+    double s2 = ((r[0] * r[0] + r[1] * r[1]) + r[2] * r[2]) + eps2;
+    double u = 1.0 / sqrt(s2);
+    double u2 = u * u, u3 = u2 * u, u5 = u3 * u2, u7 = u5 * u2, u9 = u7 * u2;
+    double lr = (lam[0] * r[0] + lam[1] * r[1]) + lam[2] * r[2];
+    for (int d = 0; d < 3; ++d)
+        g_r[d] += m * (u3 * lam[d] - 3.0 * u5 * lr * r[d]) + mu * m * u3 * r[d];
+    *g_m += lr * u3 - mu * u;
+    if (!Q) return;
+    double trQ = (Q[0] + Q[1]) + Q[2];
+    double Qr[3], Ql[3];
+    Qr[0] = (Q[0] * r[0] + Q[3] * r[1]) + Q[4] * r[2];
+    Qr[1] = (Q[3] * r[0] + Q[1] * r[1]) + Q[5] * r[2];
+    Qr[2] = (Q[4] * r[0] + Q[5] * r[1]) + Q[2] * r[2];
+    Ql[0] = (Q[0] * lam[0] + Q[3] * lam[1]) + Q[4] * lam[2];
+    Ql[1] = (Q[3] * lam[0] + Q[1] * lam[1]) + Q[5] * lam[2];
+    Ql[2] = (Q[4] * lam[0] + Q[5] * lam[1]) + Q[2] * lam[2];
+    double rQr = (r[0] * Qr[0] + r[1] * Qr[1]) + r[2] * Qr[2];
+    double lQr = (lam[0] * Qr[0] + lam[1] * Qr[1]) + lam[2] * Qr[2];
+    double fQ = -1.5 * trQ * u5 + 7.5 * rQr * u7;
+    double cr = lr * (7.5 * trQ * u7 - 52.5 * rQr * u9) + 15.0 * u7 * lQr;
+    for (int d = 0; d < 3; ++d)
+        g_r[d] += fQ * lam[d] + cr * r[d] + 15.0 * u7 * lr * Qr[d] - 3.0 * u5 * Ql[d] +
+                  mu * (fQ * r[d] - 3.0 * u5 * Qr[d]);
+    static const int ia[6] = {0, 1, 2, 0, 0, 1}, ib[6] = {0, 1, 2, 1, 2, 2};
+    for (int k = 0; k < 6; ++k) {
+        int a = ia[k], b = ib[k];
+        double diag = (a == b) ? (-1.5 * u5 * lr + 0.5 * mu * u3) : 0.0;
+        g_Q[k] += diag + r[a] * r[b] * (7.5 * u7 * lr - 1.5 * mu * u5) -
+                  1.5 * u5 * (lam[a] * r[b] + r[a] * lam[b]);
+    }
+}
+
+/* exported for the tests: one source, times G */
+void orc_eval_source_vjp(const double r[3], double m, const double *Q, double eps, double G,
+                         const double lam[3], double mu, double g_r[3], double *g_m,
+                         double g_Q[6]) {
+    double gr[3] = {0, 0, 0}, gm = 0.0, gq[6] = {0, 0, 0, 0, 0, 0};
+    orc_eq12_vjp(r, m, Q, eps * eps, lam, mu, gr, &gm, Q ? gq : NULL);
+    for (int d = 0; d < 3; ++d) g_r[d] = G * gr[d];
+    *g_m = G * gm;
+    for (int k = 0; k < 6; ++k) g_Q[k] = G * gq[k];
+}
+
+/* Record every group's interaction lists for opening angle theta. */
+int orc_tree_freeze_lists(orc_tree *t, float theta) {
+    int64_t nn = t->nnodes, ng = t->ngroups;
+    float *com_f = (float *)malloc((size_t)nn * 3 * sizeof(float));
+    float *ropen2_f = (float *)malloc((size_t)nn * sizeof(float));
+    float *gcf = (float *)malloc((size_t)ng * 3 * sizeof(float));
+    float *ghf = (float *)malloc((size_t)ng * 3 * sizeof(float));
+    free(t->pc_off); free(t->lf_off); free(t->pc_list); free(t->lf_list);
+    t->pc_off = (int64_t *)calloc((size_t)ng + 1, sizeof(int64_t));
+    t->lf_off = (int64_t *)calloc((size_t)ng + 1, sizeof(int64_t));
+    t->pc_list = NULL;
+    t->lf_list = NULL;
+    if (!com_f || !ropen2_f || !gcf || !ghf || !t->pc_off || !t->lf_off) {
+        free(com_f); free(ropen2_f); free(gcf); free(ghf);
+        return -1;
+    }
+    orc_cell_mac(t, theta, com_f, ropen2_f);
+    orc_group_box_f32(t, gcf, ghf);
+    orc_lists L;
+    memset(&L, 0, sizeof(L));
+    int64_t cap_pc = 0, cap_lf = 0;
+    for (int64_t g = 0; g < ng; ++g) {
+        float gc[3] = {gcf[g], gcf[(size_t)ng + g], gcf[2 * (size_t)ng + g]};
+        float gh[3] = {ghf[g], ghf[(size_t)ng + g], ghf[2 * (size_t)ng + g]};
+        orc_walk_group(t, com_f, ropen2_f, gc, gh, &L);
+        int64_t p0 = t->pc_off[g], l0 = t->lf_off[g];
+        t->pc_off[g + 1] = p0 + L.npc;
+        t->lf_off[g + 1] = l0 + L.npp_leaves;
+        if (t->pc_off[g + 1] > cap_pc) {
+            cap_pc = 2 * t->pc_off[g + 1] + 1024;
+            t->pc_list = (uint32_t *)realloc(t->pc_list, (size_t)cap_pc * sizeof(uint32_t));
+        }
+        if (t->lf_off[g + 1] > cap_lf) {
+            cap_lf = 2 * t->lf_off[g + 1] + 1024;
+            t->lf_list = (uint32_t *)realloc(t->lf_list, (size_t)cap_lf * sizeof(uint32_t));
+        }
+        memcpy(t->pc_list + p0, L.pc, (size_t)L.npc * sizeof(uint32_t));
+        memcpy(t->lf_list + l0, L.pp, (size_t)L.npp_leaves * sizeof(uint32_t));
+    }
+    free(L.pc); free(L.pp);
+    free(com_f); free(ropen2_f); free(gcf); free(ghf);
+    return 0;
+}
+
+/* Forces (sorted order) with the frozen lists at positions x and masses m
+ * given in the tree's sorted order; the multipoles are recomputed from x, m
+ * for the same node membership.                                            */
+int orc_tree_frozen_forces(const orc_tree *t, double eps, double G, const double *x,
+                           const double *m, double *acc, double *pot) {
+    int64_t n = t->n, nn = t->nnodes, ng = t->ngroups;
+    if (!t->pc_off) return -1;
+    double *M = (double *)malloc((size_t)nn * sizeof(double));
+    double *com = (double *)malloc((size_t)nn * 3 * sizeof(double));
+    double *Q = (double *)malloc((size_t)nn * 6 * sizeof(double));
+    if (!M || !com || !Q) { free(M); free(com); free(Q); return -1; }
+    orc_upward(t, x, m, M, com, Q);
+    double eps2 = eps * eps;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t g = 0; g < ng; ++g) {
+        for (uint32_t i = t->gfirst[g]; i < t->gfirst[g] + t->gcount[g]; ++i) {
+            double xi[3] = {x[i], x[(size_t)n + i], x[2 * (size_t)n + i]};
+            double phi = 0.0, a[3] = {0, 0, 0};
+            for (int64_t k = t->pc_off[g]; k < t->pc_off[g + 1]; ++k) {
+                uint32_t c = t->pc_list[k];
+                double r[3], Qc[6];
+                for (int d = 0; d < 3; ++d) r[d] = com[(size_t)d * nn + c] - xi[d];
+                for (int q = 0; q < 6; ++q) Qc[q] = Q[(size_t)q * nn + c];
+                orc_eq12(r, M[c], Qc, eps2, &phi, a);
+            }
+            for (int64_t k = t->lf_off[g]; k < t->lf_off[g + 1]; ++k) {
+                uint32_t lf = t->lf_list[k];
+                for (uint32_t j = t->first[lf]; j < t->first[lf] + t->count[lf]; ++j) {
+                    if (j == i) continue;
+                    double r[3];
+                    for (int d = 0; d < 3; ++d) r[d] = x[(size_t)d * n + j] - xi[d];
+                    orc_eq12(r, m[j], NULL, eps2, &phi, a);
+                }
+            }
+            pot[i] = G * phi;
+            for (int d = 0; d < 3; ++d) acc[(size_t)d * n + i] = G * a[d];
+        }
+    }
+    free(M); free(com); free(Q);
+    return 0;
+}
+
+/* VJP of the frozen-list forces: given lam (3n) and mu (n, may be NULL) in
+ * sorted order, gx (3n) and gm (n) receive d(sum lam.a + mu phi)/dx, dm.
+ * Target side, p-p source side and cell side are accumulated in one plain
+ * serial loop; the cell adjoints (com, M, Q) are then pushed to every
+ * particle of the cell:  x_k gets m_k/M gcom + 2 m_k gQ (x_k - com) and m_k
+ * gets gM + gcom.(x_k - com)/M + (x_k - com)^T gQ (x_k - com).            */
+int orc_tree_frozen_vjp(const orc_tree *t, double eps, double G, const double *x,
+                        const double *m, const double *lam, const double *mu, double *gx,
+                        double *gm) {
+    int64_t n = t->n, nn = t->nnodes, ng = t->ngroups;
+    if (!t->pc_off) return -1;
+    double *M = (double *)malloc((size_t)nn * sizeof(double));
+    double *com = (double *)malloc((size_t)nn * 3 * sizeof(double));
+    double *Q = (double *)malloc((size_t)nn * 6 * sizeof(double));
+    double *gcom = (double *)calloc((size_t)nn * 3, sizeof(double));
+    double *gM = (double *)calloc((size_t)nn, sizeof(double));
+    double *gQ = (double *)calloc((size_t)nn * 6, sizeof(double));
+    if (!M || !com || !Q || !gcom || !gM || !gQ) {
+        free(M); free(com); free(Q); free(gcom); free(gM); free(gQ);
+        return -1;
+    }
+    orc_upward(t, x, m, M, com, Q);
+    memset(gx, 0, (size_t)n * 3 * sizeof(double));
+    memset(gm, 0, (size_t)n * sizeof(double));
+    double eps2 = eps * eps;
+    for (int64_t g = 0; g < ng; ++g) {
+        for (uint32_t i = t->gfirst[g]; i < t->gfirst[g] + t->gcount[g]; ++i) {
+            double xi[3] = {x[i], x[(size_t)n + i], x[2 * (size_t)n + i]};
+            double li[3] = {lam[i], lam[(size_t)n + i], lam[2 * (size_t)n + i]};
+            double mi = mu ? mu[i] : 0.0;
+            for (int64_t k = t->pc_off[g]; k < t->pc_off[g + 1]; ++k) {
+                uint32_t c = t->pc_list[k];
+                double r[3], Qc[6], gr[3] = {0, 0, 0}, gmc = 0.0, gq[6] = {0, 0, 0, 0, 0, 0};
+                for (int d = 0; d < 3; ++d) r[d] = com[(size_t)d * nn + c] - xi[d];
+                for (int q = 0; q < 6; ++q) Qc[q] = Q[(size_t)q * nn + c];
+                orc_eq12_vjp(r, M[c], Qc, eps2, li, mi, gr, &gmc, gq);
+                for (int d = 0; d < 3; ++d) {
+                    gx[(size_t)d * n + i] -= G * gr[d];
+                    gcom[(size_t)d * nn + c] += G * gr[d];
+                }
+                gM[c] += G * gmc;
+                for (int q = 0; q < 6; ++q) gQ[(size_t)q * nn + c] += G * gq[q];
+            }
+            for (int64_t k = t->lf_off[g]; k < t->lf_off[g + 1]; ++k) {
+                uint32_t lf = t->lf_list[k];
+                for (uint32_t j = t->first[lf]; j < t->first[lf] + t->count[lf]; ++j) {
+                    if (j == i) continue;
+                    double r[3], gr[3] = {0, 0, 0}, gmj = 0.0;
+                    for (int d = 0; d < 3; ++d) r[d] = x[(size_t)d * n + j] - xi[d];
+                    orc_eq12_vjp(r, m[j], NULL, eps2, li, mi, gr, &gmj, NULL);
+                    for (int d = 0; d < 3; ++d) {
+                        gx[(size_t)d * n + i] -= G * gr[d];
+                        gx[(size_t)d * n + j] += G * gr[d];
+                    }
+                    gm[j] += G * gmj;
+                }
+            }
+        }
+    }
+    /* cell adjoints to the particles of each cell */
+    for (int64_t c = 0; c < nn; ++c) {
+        double q[3][3] = {{gQ[c], gQ[3 * (size_t)nn + c], gQ[4 * (size_t)nn + c]},
+                          {gQ[3 * (size_t)nn + c], gQ[(size_t)nn + c], gQ[5 * (size_t)nn + c]},
+                          {gQ[4 * (size_t)nn + c], gQ[5 * (size_t)nn + c], gQ[2 * (size_t)nn + c]}};
+        double gc[3] = {gcom[c], gcom[(size_t)nn + c], gcom[2 * (size_t)nn + c]};
+        for (uint32_t k = t->first[c]; k < t->first[c] + t->count[c]; ++k) {
+            double d[3], qd[3];
+            for (int e = 0; e < 3; ++e) d[e] = x[(size_t)e * n + k] - com[(size_t)e * nn + c];
+            for (int e = 0; e < 3; ++e) qd[e] = (q[e][0] * d[0] + q[e][1] * d[1]) + q[e][2] * d[2];
+            for (int e = 0; e < 3; ++e)
+                gx[(size_t)e * n + k] += m[k] / M[c] * gc[e] + 2.0 * m[k] * qd[e];
+            gm[k] += gM[c] + ((gc[0] * d[0] + gc[1] * d[1]) + gc[2] * d[2]) / M[c] +
+                     ((d[0] * qd[0] + d[1] * qd[1]) + d[2] * qd[2]);
+        }
+    }
+    free(M); free(com); free(Q); free(gcom); free(gM); free(gQ);
+    return 0;
+}
+
+/* O1 adjoint: VJP of direct summation, all pairs j != i (caller order). */
+void orc_direct_vjp(int64_t n, const double *pos, const double *mass, double eps, double G,
+                    const double *lam, const double *mu, double *gpos, double *gmass) {
+    double eps2 = eps * eps;
+    memset(gpos, 0, (size_t)n * 3 * sizeof(double));
+    memset(gmass, 0, (size_t)n * sizeof(double));
+    for (int64_t i = 0; i < n; ++i) {
+        double li[3] = {lam[i], lam[n + i], lam[2 * n + i]};
+        double mi = mu ? mu[i] : 0.0;
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i) continue;
+            double r[3] = {pos[j] - pos[i], pos[n + j] - pos[n + i], pos[2 * n + j] - pos[2 * n + i]};
+            double gr[3] = {0, 0, 0}, gmj = 0.0;
+            orc_eq12_vjp(r, mass[j], NULL, eps2, li, mi, gr, &gmj, NULL);
+            for (int d = 0; d < 3; ++d) {
+                gpos[d * n + i] -= G * gr[d];
+                gpos[d * n + j] += G * gr[d];
+            }
+            gmass[j] += G * gmj;
+        }
+    }
+}
+
+/* ---- K leap-frog steps with frozen per-step trees (adjoint of KDK) ---- */
+typedef struct {
+    int64_t n;
+    int nsteps;
+    double dt, eps, G;
+    orc_tree **trees; /* tree k built at the nominal x_k, lists frozen */
+    double *xs;       /* nominal positions x_0 .. x_K, caller order [K+1][3n] */
+} orc_kdk_plan;
+
+void orc_kdk_plan_free(orc_kdk_plan *p) {
+    if (!p) return;
+    if (p->trees)
+        for (int k = 0; k <= p->nsteps; ++k) orc_tree_free(p->trees[k]);
+    free(p->trees);
+    free(p->xs);
+    free(p);
+}
+
+/* frozen-list forces at caller-order positions x with tree t's structure */
+static int orc_frozen_caller(const orc_tree *t, double eps, double G, const double *x,
+                             const double *m, double *acc) {
+    int64_t n = t->n;
+    double *xs = (double *)malloc((size_t)n * 3 * sizeof(double));
+    double *ms = (double *)malloc((size_t)n * sizeof(double));
+    double *as = (double *)malloc((size_t)n * 3 * sizeof(double));
+    double *ps = (double *)malloc((size_t)n * sizeof(double));
+    if (!xs || !ms || !as || !ps) { free(xs); free(ms); free(as); free(ps); return -1; }
+    for (int64_t s = 0; s < n; ++s) {
+        uint32_t j = t->perm[s];
+        ms[s] = m[j];
+        for (int d = 0; d < 3; ++d) xs[(size_t)d * n + s] = x[(size_t)d * n + j];
+    }
+    int rc = orc_tree_frozen_forces(t, eps, G, xs, ms, as, ps);
+    for (int64_t s = 0; s < n; ++s)
+        for (int d = 0; d < 3; ++d) acc[(size_t)d * n + t->perm[s]] = as[(size_t)d * n + s];
+    free(xs); free(ms); free(as); free(ps);
+    return rc;
+}
+
+/* frozen-list VJP at caller-order x with cotangent lam (caller order, mu = 0);
+ * adds into gx (3n) and gm (n), caller order */
+static int orc_frozen_vjp_caller(const orc_tree *t, double eps, double G, const double *x,
+                                 const double *m, const double *lam, double *gx, double *gm) {
+    int64_t n = t->n;
+    double *xs = (double *)malloc((size_t)n * 3 * sizeof(double));
+    double *ms = (double *)malloc((size_t)n * sizeof(double));
+    double *ls = (double *)malloc((size_t)n * 3 * sizeof(double));
+    double *gxs = (double *)malloc((size_t)n * 3 * sizeof(double));
+    double *gms = (double *)malloc((size_t)n * sizeof(double));
+    if (!xs || !ms || !ls || !gxs || !gms) {
+        free(xs); free(ms); free(ls); free(gxs); free(gms);
+        return -1;
+    }
+    for (int64_t s = 0; s < n; ++s) {
+        uint32_t j = t->perm[s];
+        ms[s] = m[j];
+        for (int d = 0; d < 3; ++d) {
+            xs[(size_t)d * n + s] = x[(size_t)d * n + j];
+            ls[(size_t)d * n + s] = lam[(size_t)d * n + j];
+        }
+    }
+    int rc = orc_tree_frozen_vjp(t, eps, G, xs, ms, ls, NULL, gxs, gms);
+    for (int64_t s = 0; s < n; ++s) {
+        uint32_t j = t->perm[s];
+        gm[j] += gms[s];
+        for (int d = 0; d < 3; ++d) gx[(size_t)d * n + j] += gxs[(size_t)d * n + s];
+    }
+    free(xs); free(ms); free(ls); free(gxs); free(gms);
+    return rc;
+}
+
+/* Nominal trajectory: K kick-drift-kick steps from (pos0, vel0), the tree
+ * and lists of step k built and frozen at the nominal x_k.                 */
+orc_kdk_plan *orc_kdk_plan_build(int64_t n, const double *pos0, const double *vel0,
+                                 const double *mass, int nsteps, double dt, float theta,
+                                 double eps, double G, int nleaf, int ncrit) {
+    orc_kdk_plan *p = (orc_kdk_plan *)calloc(1, sizeof(orc_kdk_plan));
+    if (!p) return NULL;
+    p->n = n;
+    p->nsteps = nsteps;
+    p->dt = dt;
+    p->eps = eps;
+    p->G = G;
+    p->trees = (orc_tree **)calloc((size_t)nsteps + 1, sizeof(orc_tree *));
+    p->xs = (double *)malloc((size_t)(nsteps + 1) * 3 * n * sizeof(double));
+    double *v = (double *)malloc((size_t)n * 3 * sizeof(double));
+    double *a = (double *)malloc((size_t)n * 3 * sizeof(double));
+    if (!p->trees || !p->xs || !v || !a) { free(v); free(a); orc_kdk_plan_free(p); return NULL; }
+    memcpy(p->xs, pos0, (size_t)n * 3 * sizeof(double));
+    memcpy(v, vel0, (size_t)n * 3 * sizeof(double));
+    double h = 0.5 * dt;
+    for (int k = 0; k <= nsteps; ++k) {
+        double *xk = p->xs + (size_t)k * 3 * n;
+        if (k > 0) {
+            double *xp = p->xs + (size_t)(k - 1) * 3 * n;
+            for (int64_t q = 0; q < 3 * n; ++q) v[q] = v[q] + a[q] * h;
+            for (int64_t q = 0; q < 3 * n; ++q) xk[q] = xp[q] + v[q] * dt;
+        }
+        p->trees[k] = orc_tree_build(n, xk, mass, nleaf, ncrit);
+        if (!p->trees[k] || orc_tree_freeze_lists(p->trees[k], theta) ||
+            orc_frozen_caller(p->trees[k], eps, G, xk, mass, a)) {
+            free(v); free(a); orc_kdk_plan_free(p);
+            return NULL;
+        }
+        if (k > 0)
+            for (int64_t q = 0; q < 3 * n; ++q) v[q] = v[q] + a[q] * h;
+    }
+    free(v); free(a);
+    return p;
+}
+
+/* Run the K steps from (pos0, vel0) with each step's frozen tree. */
+int orc_kdk_plan_run(const orc_kdk_plan *p, const double *pos0, const double *vel0,
+                     const double *mass, double *pos, double *vel) {
+    int64_t n = p->n;
+    double *a = (double *)malloc((size_t)n * 3 * sizeof(double));
+    if (!a) return -1;
+    memcpy(pos, pos0, (size_t)n * 3 * sizeof(double));
+    memcpy(vel, vel0, (size_t)n * 3 * sizeof(double));
+    double h = 0.5 * p->dt;
+    int rc = orc_frozen_caller(p->trees[0], p->eps, p->G, pos, mass, a);
+    for (int k = 1; k <= p->nsteps && !rc; ++k) {
+        for (int64_t q = 0; q < 3 * n; ++q) vel[q] = vel[q] + a[q] * h;
+        for (int64_t q = 0; q < 3 * n; ++q) pos[q] = pos[q] + vel[q] * p->dt;
+        rc = orc_frozen_caller(p->trees[k], p->eps, p->G, pos, mass, a);
+        for (int64_t q = 0; q < 3 * n; ++q) vel[q] = vel[q] + a[q] * h;
+    }
+    free(a);
+    return rc;
+}
+
+/* Reverse of the K steps at the nominal trajectory.  In: xbar, vbar (the
+ * cotangents of x_K, v_K) and mbar (direct mass cotangent, may be zero);
+ * out: the same arrays hold the cotangents of x_0, v_0, m.
+ *   a_K enters only the last half kick: abar_K = h vbar.
+ *   for k = K-1 .. 0:  vbar += dt xbar  (drift),
+ *                      abar_k = c vbar with c = dt for k > 0 (both half
+ *                      kicks use a_k) and c = h for k = 0,
+ *                      (xbar, mbar) += VJP_k(abar_k).                      */
+int orc_kdk_plan_vjp(const orc_kdk_plan *p, const double *mass, double *xbar, double *vbar,
+                     double *mbar) {
+    int64_t n = p->n;
+    double h = 0.5 * p->dt;
+    double *ab = (double *)malloc((size_t)n * 3 * sizeof(double));
+    if (!ab) return -1;
+    int K = p->nsteps, rc = 0;
+    if (K == 0) { free(ab); return 0; }
+    for (int64_t q = 0; q < 3 * n; ++q) ab[q] = h * vbar[q];
+    rc = orc_frozen_vjp_caller(p->trees[K], p->eps, p->G, p->xs + (size_t)K * 3 * n, mass, ab,
+                               xbar, mbar);
+    for (int k = K - 1; k >= 0 && !rc; --k) {
+        for (int64_t q = 0; q < 3 * n; ++q) vbar[q] = vbar[q] + p->dt * xbar[q];
+        double c = (k > 0) ? p->dt : h;
+        for (int64_t q = 0; q < 3 * n; ++q) ab[q] = c * vbar[q];
+        rc = orc_frozen_vjp_caller(p->trees[k], p->eps, p->G, p->xs + (size_t)k * 3 * n, mass,
+                                   ab, xbar, mbar);
+    }
+    free(ab);
+    return rc;
 }
