@@ -146,6 +146,41 @@ int tree_get_forces(bonsai_ctx *ctx, float *acc, float *pot);
  * Errors: ESTATE (no forces yet), ECUDA. */
 int bonsai_diagnostics(bonsai_ctx *ctx, double out[10]);
 
+/* ---- adjoint (vector-Jacobian products) ------------------------------- */
+/* The paper has no adjoint.  These give the exact derivative of the forward
+ * map with the tree and interaction lists of the forward evaluation held
+ * fixed (node membership, opened cells and leaves are piecewise constant in
+ * the positions; the multipoles stay functions of the particles). */
+
+/* tree_forces_vjp -- for cotangents lambda = dL/da (device float32 [3][n])
+ * and mu = dL/dphi (device float32 [n], or NULL for zero), writes
+ *   gpos  = d(sum_i lambda_i.a_i + mu_i phi_i)/dx   (device float64 [3][n]),
+ *   gmass = the same derivative with respect to the masses (device float64 [n]),
+ * all in caller order, for the last tree_forces (same theta, eps, lists).
+ * The walk is recomputed; p-c terms reach the particles through the
+ * quadrupole upward pass (centre of mass and Q of every accepted cell).
+ * FP32 evaluation, FP32 atomics per cell and particle, FP64 push-down.
+ * Errors: EINVAL (null pointer), ESTATE (no forces yet), EOVERFLOW, ECUDA. */
+int tree_forces_vjp(bonsai_ctx *ctx, const float *gacc, const float *gpot, double *gpos,
+                    double *gmass);
+
+/* tree_run -- nsteps calls of tree_step(dt) from the current state,
+ * recording FP64 checkpoints of (pos, vel) every ckpt_every steps for
+ * tree_run_vjp.  Errors: EINVAL, ESTATE, ENOMEM, as tree_step. */
+int tree_run(bonsai_ctx *ctx, int nsteps, double dt, int ckpt_every);
+
+/* tree_run_vjp -- reverse pass of the last tree_run.  In: xbar, vbar =
+ * dL/dx_K, dL/dv_K (device float64 [3][n]) and mbar = dL/dm taken directly
+ * (device float64 [n] or NULL).  Out: xbar0, vbar0 = dL/dx_0, dL/dv_0 and
+ * mbar0 = dL/dm (device float64, caller order).  Each segment between
+ * checkpoints is re-integrated to recover its positions; at every position
+ * x_s the tree is rebuilt and the force VJP applied with the kick
+ * cotangent (dt/2 v̄ at s = 0 and s = K, dt v̄ in between), the drift adding
+ * dt x̄ to v̄.  The context's state afterwards is undefined (rebuild it).
+ * Errors: EINVAL, ESTATE (no recorded run), ENOMEM, EOVERFLOW, ECUDA. */
+int tree_run_vjp(bonsai_ctx *ctx, const double *xbar, const double *vbar, const double *mbar,
+                 double *xbar0, double *vbar0, double *mbar0);
+
 /* Statistics of the last build / force evaluation.  out: host. */
 int tree_get_stats(bonsai_ctx *ctx, bonsai_stats *out);
 

@@ -31,7 +31,7 @@ EXPORTED = (
     "tree_set_velocities", "tree_step", "tree_get_state", "tree_get_forces",
     "bonsai_diagnostics", "tree_get_stats", "tree_solve_host", "tree_debug_cube",
     "tree_debug_keys", "tree_debug_nodes", "tree_debug_multipoles", "tree_debug_groups",
-    "bonsai_strerror", "bonsai_sfc_order_noalloc",
+    "bonsai_strerror", "bonsai_sfc_order_noalloc", "tree_forces_vjp", "tree_run", "tree_run_vjp",
 )
 
 BONSAI_NOALLOC_MAX_N = 1 << 20
@@ -93,6 +93,9 @@ def load(path: str | None = None):
             "tree_debug_groups": (i32, [P, P, P, P, P]),
             "bonsai_strerror": (ctypes.c_char_p, [i32]),
             "bonsai_sfc_order_noalloc": (i32, [P, P, i64, P, P, P, P]),
+            "tree_forces_vjp": (i32, [P, P, P, P, P]),
+            "tree_run": (i32, [P, i32, f64, i32]),
+            "tree_run_vjp": (i32, [P, P, P, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -223,6 +226,25 @@ def tree_solve_host(ctx, pos, mass, theta: float, eps: float, acc, pot) -> None:
     n = int(mass.shape[0])
     _check(load().tree_solve_host(ctx, _hptr(pos), _hptr(mass), n, float(theta), float(eps),
                                   _hptr(acc), _hptr(pot)), "tree_solve_host")
+
+
+def tree_forces_vjp(ctx, gacc, gpos, gmass, gpot=None) -> None:
+    import torch
+    _check(load().tree_forces_vjp(ctx, _ptr(gacc, torch.float32, None, "gacc"),
+                                  _ptr(gpot, torch.float32, None, "gpot"),
+                                  _ptr(gpos, torch.float64, None, "gpos"),
+                                  _ptr(gmass, torch.float64, None, "gmass")), "tree_forces_vjp")
+
+
+def tree_run(ctx, nsteps: int, dt: float, ckpt_every: int) -> None:
+    _check(load().tree_run(ctx, int(nsteps), float(dt), int(ckpt_every)), "tree_run")
+
+
+def tree_run_vjp(ctx, xbar, vbar, mbar, xbar0, vbar0, mbar0) -> None:
+    import torch
+    f64 = torch.float64
+    _check(load().tree_run_vjp(ctx, _ptr(xbar, f64), _ptr(vbar, f64), _ptr(mbar, f64),
+                               _ptr(xbar0, f64), _ptr(vbar0, f64), _ptr(mbar0, f64)), "tree_run_vjp")
 
 
 def tree_debug_cube(ctx):

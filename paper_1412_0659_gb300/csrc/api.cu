@@ -145,6 +145,20 @@ int forces_internal(bonsai_ctx *c, float theta, float eps, float *acc_c, float *
         return BONSAI_EOVERFLOW;
     }
     c->have_forces = true;
+    c->last_theta = theta;
+    c->last_eps = eps;
+    return BONSAI_OK;
+}
+
+// One reverse force VJP at the current tree: cotangent already in adj_ca
+// (caller order, FP32); adds the gradient into xbar, mbar (caller order).
+int reverse_force_step(bonsai_ctx *c, double *xbar, double *mbar) {
+    int rc = adjoint_buffers(c);
+    if (rc) return rc;
+    launch_cotangents_in(c, c->adj_ca.p, nullptr);
+    rc = forces_vjp_sorted(c, c->prm.theta, c->prm.eps, false, c->adj_gpos.p, c->adj_gmass.p);
+    if (rc) return rc;
+    launch_rev_accum(c, xbar, mbar);
     return BONSAI_OK;
 }
 
@@ -196,6 +210,9 @@ void bonsai_destroy(bonsai_ctx *c) {
     release(c->grp_flag); release(c->grp_first); release(c->grp_count); release(c->grp_centre);
     release(c->grp_box); release(c->grp_half); release(c->grp_lo); release(c->grp_npp);
     release(c->grp_npc); release(c->frontier); release(c->diag_part);
+    release(c->adj_cell); release(c->adj_part); release(c->adj_node); release(c->adj_lam);
+    release(c->adj_mu); release(c->adj_ca); release(c->leaf_of); release(c->adj_gpos);
+    release(c->adj_gmass); release(c->run_mass); release(c->ckpt); release(c->seg_pos);
     cudaFree(c->dsc);
     cudaFreeHost(c->hsc);
     for (int k = 0; k < 10; ++k) cudaEventDestroy(c->ev[k]);
@@ -293,6 +310,98 @@ int tree_get_stats(bonsai_ctx *c, bonsai_stats *out) {
     if (!c || !out) return BONSAI_EINVAL;
     c->stats.launches = c->launches;
     *out = c->stats;
+    return BONSAI_OK;
+}
+
+int tree_forces_vjp(bonsai_ctx *c, const float *gacc, const float *gpot, double *gpos,
+                    double *gmass) {
+    if (!c || !gacc || !gpos || !gmass) return BONSAI_EINVAL;
+    if (!c->have_forces) return BONSAI_ESTATE;
+    int rc = adjoint_buffers(c);
+    if (rc) return rc;
+    launch_cotangents_in(c, gacc, gpot);
+    rc = forces_vjp_sorted(c, c->last_theta, c->last_eps, gpot != nullptr, gpos, gmass);
+    if (rc) return rc;
+    if ((rc = read_scalars(c))) return rc;
+    if (c->hsc->status & ST_OVERFLOW) return BONSAI_EOVERFLOW;
+    return BONSAI_OK;
+}
+
+int tree_run(bonsai_ctx *c, int nsteps, double dt, int ckpt_every) {
+    if (!c || nsteps < 0 || ckpt_every < 1 || !isfinite(dt)) return BONSAI_EINVAL;
+    if (!c->have_tree) return BONSAI_ESTATE;
+    const int64_t n = c->n;
+    const int nck = (nsteps + ckpt_every - 1) / ckpt_every;
+    if (ensure(c->ckpt, (size_t)(nck > 0 ? nck : 1) * 6 * n) || ensure(c->run_mass, n))
+        return BONSAI_ENOMEM;
+    c->run_steps = -1;
+    launch_unpermute_state(c, nullptr, nullptr, c->run_mass.p);
+    int rc;
+    for (int s = 0; s < nsteps; ++s) {
+        if (s % ckpt_every == 0) {
+            double *ck = c->ckpt.p + (size_t)(s / ckpt_every) * 6 * n;
+            launch_unpermute_state(c, ck, ck + 3 * n, nullptr);
+        }
+        if ((rc = tree_step(c, dt))) return rc;
+    }
+    BGB_CUDA(cudaStreamSynchronize(c->stream));
+    c->run_steps = nsteps;
+    c->run_ckpt = ckpt_every;
+    c->run_dt = dt;
+    return BONSAI_OK;
+}
+
+int tree_run_vjp(bonsai_ctx *c, const double *xbar, const double *vbar, const double *mbar,
+                 double *xbar0, double *vbar0, double *mbar0) {
+    if (!c || !xbar || !vbar || !xbar0 || !vbar0 || !mbar0) return BONSAI_EINVAL;
+    if (c->run_steps < 0) return BONSAI_ESTATE;
+    const int64_t n = c->n;
+    const int K = c->run_steps, k = c->run_ckpt;
+    const double dt = c->run_dt, h = 0.5 * dt;
+    BGB_CUDA(cudaMemcpyAsync(xbar0, xbar, 3 * n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    BGB_CUDA(cudaMemcpyAsync(vbar0, vbar, 3 * n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    if (mbar)
+        BGB_CUDA(cudaMemcpyAsync(mbar0, mbar, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    else
+        BGB_CUDA(cudaMemsetAsync(mbar0, 0, n * sizeof(double), c->stream));
+    if (K == 0) {
+        BGB_CUDA(cudaStreamSynchronize(c->stream));
+        return BONSAI_OK;
+    }
+    // the reverse drift writes the kick cotangent (caller order) before the
+    // first force VJP allocates the rest of the adjoint buffers
+    if (ensure(c->seg_pos, (size_t)(k + 1) * 3 * n) || ensure(c->adj_ca, 3 * (size_t)n))
+        return BONSAI_ENOMEM;
+    int rc;
+    const int nseg = (K + k - 1) / k;
+    for (int j = nseg - 1; j >= 0; --j) {
+        const int s0 = j * k, s1 = std::min(s0 + k, K);
+        // re-run the segment from its checkpoint, keeping every position
+        const double *ck = c->ckpt.p + (size_t)j * 6 * n;
+        BGB_CUDA(cudaMemcpyAsync(c->seg_pos.p, ck, 3 * n * sizeof(double), cudaMemcpyDeviceToDevice,
+                                 c->stream));
+        if ((rc = tree_build(c, ck, c->run_mass.p, n))) return rc;
+        if ((rc = tree_set_velocities(c, ck + 3 * n))) return rc;
+        for (int s = s0; s < s1; ++s) {
+            if ((rc = tree_step(c, dt))) return rc;
+            launch_unpermute_state(c, c->seg_pos.p + (size_t)(s + 1 - s0) * 3 * n, nullptr, nullptr);
+        }
+        // positions s1 .. s0 in reverse (s1 only when it is the last position)
+        const int top = (s1 == K) ? s1 : s1 - 1;
+        for (int s = top; s >= s0; --s) {
+            // a_K enters only the last half kick; a_s (0 < s < K) both half
+            // kicks around it; a_0 only the first; the drift adds dt xbar to
+            // vbar before every position below K
+            const double drift = (s == K) ? 0.0 : dt;
+            const double coef = (s == K || s == 0) ? h : dt;
+            launch_rev_drift(c, vbar0, xbar0, drift, coef);
+            const double *xs = c->seg_pos.p + (size_t)(s - s0) * 3 * n;
+            if ((rc = tree_build(c, xs, c->run_mass.p, n))) return rc;
+            if ((rc = reverse_force_step(c, xbar0, mbar0))) return rc;
+        }
+    }
+    if ((rc = read_scalars(c))) return rc;
+    if (c->hsc->status & ST_OVERFLOW) return BONSAI_EOVERFLOW;
     return BONSAI_OK;
 }
 

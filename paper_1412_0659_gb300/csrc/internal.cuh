@@ -119,6 +119,22 @@ struct bonsai_ctx {
     // diagnostics scratch
     bgb::DBuf<double> diag_part;
 
+    // adjoint
+    float last_theta = 0.0f, last_eps = 0.0f;  // of the last force evaluation
+    bgb::DBuf<float4> adj_cell;    // [3][nn] (com, M, Q) adjoint per node, FP32
+    bgb::DBuf<float4> adj_part;    // [n] direct particle gradient {x, y, z, m}, key order
+    bgb::DBuf<double> adj_node;    // [10][nn] accumulated alpha, B, beta
+    bgb::DBuf<float> adj_lam, adj_mu;  // cotangents in key order
+    bgb::DBuf<float> adj_ca;       // [3][n] cotangent in caller order (reverse chain)
+    bgb::DBuf<uint32_t> leaf_of;   // leaf node of each key-order slot
+    bgb::DBuf<double> adj_gpos, adj_gmass;  // gradient of one VJP, caller order
+    // recorded run for the reverse chain: checkpoints of (pos, vel), caller order
+    int run_steps = -1, run_ckpt = 1;
+    double run_dt = 0.0;
+    bgb::DBuf<double> run_mass;    // [n]
+    bgb::DBuf<double> ckpt;        // [nck][6n]
+    bgb::DBuf<double> seg_pos;     // [ckpt_every + 1][3n]
+
     // timing events
     cudaEvent_t ev[10];
     bonsai_stats stats;
@@ -163,6 +179,13 @@ size_t sort_hist_elems(int64_t n);
 void launch_unpermute_state(bonsai_ctx *c, double *pos, double *vel, double *mass);
 void launch_unpermute_forces(bonsai_ctx *c, float *acc, float *pot);
 void launch_permute_in_vel(bonsai_ctx *c, const double *vel);
+// adjoint.cu
+int adjoint_buffers(bonsai_ctx *c);
+int forces_vjp_sorted(bonsai_ctx *c, float theta, float eps, bool with_mu, double *gpos,
+                      double *gmass);
+void launch_cotangents_in(bonsai_ctx *c, const float *gacc, const float *gpot);
+void launch_rev_drift(bonsai_ctx *c, double *vbar, const double *xbar, double dt, double coef);
+void launch_rev_accum(bonsai_ctx *c, double *xbar, double *mbar);
 // context-free variants on explicit buffers (noalloc.cu)
 int launch_cube_keys_into(cudaStream_t s, int sm_count, const double *pos, const double *mass,
                           int64_t n, BoxPartial *part, int max_part, DevScalars *dsc,

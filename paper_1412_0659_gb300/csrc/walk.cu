@@ -1,24 +1,28 @@
 // walk.cu -- the fused group walk and force evaluation (Sec. III.A: the
 // walk and the force computation in one kernel, interaction lists kept on
-// chip and evaluated on the fly; Eq. 1-2 of Sec. VI.A).
+// chip and evaluated on the fly; Eq. 1-2 of Sec. VI.A), and its adjoint.
 //
-// One warp owns one group of <= 64 targets (two per lane when the group has
-// more than 32).  Warps fetch groups from a global counter, so the grid is
-// persistent: one wave of resident warps.  The walk is breadth-first: each
-// lane tests one cell of the current frontier against the group's box
-// (ballot + popc compaction replaces Bonsai's shared-memory stacks):
+// One warp owns one group of <= 64 targets.  Warps fetch groups from a
+// global counter, so the grid is persistent: one wave of resident warps.
+// The walk is breadth-first: each lane tests one cell of the current
+// frontier against the group's box (ballot + popc compaction replaces
+// Bonsai's shared-memory stacks):
 //   accepted          -> its multipole record is converted to group-relative
 //                        FP32 and appended to the warp's p-c ring in smem;
 //   opened leaf       -> its particles are appended to the p-p ring (a warp
 //                        scan of the leaf sizes spreads them over lanes);
 //   opened internal   -> its children go to the next frontier (global
 //                        scratch, one region per resident warp, L2-resident).
-// Whenever a ring holds 32 entries the warp evaluates them: every lane reads
-// the same entry (shared-memory broadcast) and applies it to its targets.
-// The list never reaches DRAM.  All force arithmetic is FP32 on coordinates
-// relative to the group centre; the opening test is evaluated exactly as
-// specified (round-to-nearest FP32, fixed order) so that the interaction
-// lists are a pure function of the FP32-rounded cell and group data.
+// Whenever a ring holds 32 entries the warp evaluates them.  The list never
+// reaches DRAM.  All force arithmetic is FP32 on coordinates relative to the
+// group centre; the opening test is evaluated exactly as specified
+// (round-to-nearest FP32, fixed order) so that the interaction lists are a
+// pure function of the FP32-rounded cell and group data.
+//
+// The traversal is one template (walk_group) shared by two evaluation
+// policies: the forward one (targets in lanes, list entries broadcast from
+// shared memory) and the adjoint one (list entries in lanes, targets
+// broadcast), which recomputes exactly the same lists.
 #include "internal.cuh"
 
 namespace bgb {
@@ -34,7 +38,14 @@ struct __align__(16) WarpLists {
     float4 cb[RING];  // -3 x {Qxx, Qyy, Qzz, Qxy}
     float4 cc[RING];  // {-3 Qxz, -3 Qyz, -trQ/2, -3/2 trQ}
     float4 pp[RING];  // {dx, dy, dz, m}: particle relative to the group centre
-    int pid[RING];    // sorted index of the particle (self-pair mask)
+    int pid[RING];    // sorted index of the particle
+    int cid[RING];    // node index of the cell
+};
+
+// targets of one group for the adjoint policy
+struct __align__(16) WarpTargets {
+    float4 pos[NCRIT];  // {dx, dy, dz, sorted index as bits}
+    float4 lam[NCRIT];  // {lambda_x, lambda_y, lambda_z, mu}
 };
 
 struct WalkArgs {
@@ -48,12 +59,19 @@ struct WalkArgs {
     int64_t n;
     float eps2;
     float G;
-    float *acc;  // sorted [3][n]
-    float *pot;  // sorted [n]
+    // forward outputs
+    float *acc;    // sorted [3][n]
+    float *pot;    // sorted [n]
     float *acc_c;  // caller order [3][n] or null
     float *pot_c;  // caller order [n] or null
     const uint32_t *id;
     int32_t *gnpp, *gnpc;
+    // adjoint inputs / outputs (sorted order)
+    const float *lam;  // [3][n]
+    const float *mu;   // [n] or null
+    float4 *cell_adj;  // [3][nn]: {gcom.xyz, gM}, {gQxx, gQyy, gQzz, gQxy}, {gQxz, gQyz, 0, 0}
+    float4 *part_adj;  // [n]: {gx, gy, gz, gm}
+    int64_t nn;
     uint32_t *frontier;
     DevScalars *sc;
 };
@@ -75,6 +93,16 @@ __device__ __forceinline__ uint32_t warp_excl_scan(uint32_t v, uint32_t &total) 
     total = __shfl_sync(0xffffffffu, inc, 31);
     return inc - v;
 }
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// Forward evaluation
+// ---------------------------------------------------------------------------
 
 // Eq. 1-2 for one cell on one target, Plummer-softened in every power of s:
 //   r = com - x_i, s^2 = r^2 + eps^2, u = 1/s, w = u^2,
@@ -141,31 +169,6 @@ struct Targets {
     int id[2];
 };
 
-__device__ __forceinline__ void eval_pc(const WarpLists &L, int j0, int cnt, int S, Targets &t,
-                                        float eps2) {
-#pragma unroll 2
-    for (int j = j0; j < cnt; j += S) {
-        const float4 a = L.ca[j], b = L.cb[j], c = L.cc[j];
-#pragma unroll
-        for (int k = 0; k < 2; ++k)
-            pc_one(a, b, c, t.x[k], t.y[k], t.z[k], eps2, t.ax[k], t.ay[k], t.az[k], t.ph[k]);
-    }
-}
-
-template <bool MASK>
-__device__ __forceinline__ void eval_pp(const WarpLists &L, int j0, int cnt, int S, Targets &t,
-                                        float eps2) {
-#pragma unroll 2
-    for (int j = j0; j < cnt; j += S) {
-        const float4 p = L.pp[j];
-        const int sid = L.pid[j];
-#pragma unroll
-        for (int k = 0; k < 2; ++k)
-            pp_one<MASK>(p, sid, t.id[k], t.x[k], t.y[k], t.z[k], eps2, t.ax[k], t.ay[k], t.az[k],
-                         t.ph[k]);
-    }
-}
-
 // Sum the S partial results of a target into the lanes of the first copy.
 __device__ __forceinline__ float sum_copies(float v, int lane, int T2, int S) {
     float r = v;
@@ -180,33 +183,20 @@ __device__ __forceinline__ float sum_copies(float v, int lane, int T2, int S) {
 // distance from its com to the group box is at most sqrt(3) l < l/theta),
 // and the self term is removed after the loop.
 template <bool MASK>
-__global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(const WalkArgs A) {
-    __shared__ WarpLists lists[WALK_WARPS];
-    const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
-    WarpLists &L = lists[wib];
-    const uint32_t lt = lanemask_lt();
-    const int64_t gw = (int64_t)blockIdx.x * WALK_WARPS + wib;
-    uint32_t *fa = A.frontier + gw * 2 * FCAP;
-    uint32_t *fb = fa + FCAP;
-    const float eps2 = A.eps2;
+struct ForwardPolicy {
+    int T2, S, cp, tl, j0;
+    Targets t;
+    float self[2];
+    float eps2;
 
-    while (true) {
-        uint32_t g = 0;
-        if (lane == 0) g = atomicAdd(&A.sc->group_counter, 1u);
-        g = __shfl_sync(0xffffffffu, g, 0);
-        if (g >= A.ngroups) break;
-
-        const uint32_t gf = A.gfirst[g], gc = A.gcount[g];
-        const float4 box = A.gbox[g], half = A.ghalf[g], clo = A.glo[g];
-        // lane layout: T2 lanes hold the targets, S copies split the sources
-        const int T2 = (int)((gc + 1u) >> 1);
-        const int S = 32 / T2;
-        const int cp = lane / T2;            // this lane's copy
-        const int tl = lane - cp * T2;       // this lane's target column
+    __device__ __forceinline__ void begin(const WalkArgs &A, WarpTargets *, uint32_t gf,
+                                          uint32_t gc, float4 box, float4 clo, int lane) {
+        eps2 = A.eps2;
+        T2 = (int)((gc + 1u) >> 1);
+        S = 32 / T2;
+        cp = lane / T2;
+        tl = lane - cp * T2;
         const bool active = cp < S;
-        Targets t;
-        float self[2];
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
             const uint32_t li = (uint32_t)(tl + k * T2);
@@ -220,132 +210,35 @@ __global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(const WalkArgs A) {
             t.ax[k] = t.ay[k] = t.az[k] = t.ph[k] = 0.0f;
             self[k] = h.w;
         }
-        const int j0 = active ? cp : 1 << 30;  // first ring entry of this lane
+        j0 = active ? cp : 1 << 30;  // first ring entry of this lane
+    }
 
-        uint32_t pc_head = 0, pc_tail = 0, pp_head = 0, pp_tail = 0;
-        uint32_t npc = 0, npp = 0;
-        uint32_t *cur = fa, *nxt = fb;
-        if (lane == 0) cur[0] = 0u;  // the root
-        uint32_t ncur = 1;
-        uint32_t maxf = 1;
-        bool overflow = false;
-        __syncwarp();
-
-        while (ncur > 0) {
-            uint32_t nnext = 0;
-            for (uint32_t base = 0; base < ncur; base += 32) {
-                const uint32_t idx = base + lane;
-                const bool valid = idx < ncur;
-                const uint32_t node = valid ? cur[idx] : 0u;
-                const float4 m = A.mac[node];
-                const uint2 tp = A.topo[node];
-                // opening test: squared distance from com to the group box
-                float dx = fmaxf(__fsub_rn(fabsf(__fsub_rn(m.x, box.x)), half.x), 0.0f);
-                float dy = fmaxf(__fsub_rn(fabsf(__fsub_rn(m.y, box.y)), half.y), 0.0f);
-                float dz = fmaxf(__fsub_rn(fabsf(__fsub_rn(m.z, box.z)), half.z), 0.0f);
-                const float d2 =
-                    __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-                const bool open = d2 < m.w;
-                const bool leaf = (tp.y & LEAF_FLAG) != 0u;
-                const bool accept = valid && !open;
-
-                // accepted cells -> p-c ring
-                const uint32_t am = __ballot_sync(0xffffffffu, accept);
-                if (accept) {
-                    const uint32_t s = (pc_tail + __popc(am & lt)) & (RING - 1);
-                    const float4 a = A.ca[node];
-                    const float4 rel = make_float4((m.x - box.x) + (a.x - clo.x),
-                                                   (m.y - box.y) + (a.y - clo.y),
-                                                   (m.z - box.z) + (a.z - clo.z), a.w);
-                    L.ca[s] = rel;
-                    L.cb[s] = A.cb[node];
-                    L.cc[s] = A.cc[node];
-                }
-                pc_tail += __popc(am);
-                npc += __popc(am);
-
-                // one warp scan for both the children of opened internal cells
-                // (low 9 bits: at most 8 per lane) and the particles of opened
-                // leaves (high bits); two scans when a leaf is very large
-                const uint32_t nch = (valid && open && !leaf) ? tp.y : 0u;
-                const uint32_t lc = (valid && open && leaf) ? (tp.y & ~LEAF_FLAG) : 0u;
-                uint32_t noff, ntot, loff, ltot;
-                if (__any_sync(0xffffffffu, lc > 4096u)) {
-                    noff = warp_excl_scan(nch, ntot);
-                    loff = warp_excl_scan(lc, ltot);
-                } else {
-                    uint32_t tot;
-                    const uint32_t off = warp_excl_scan(nch | (lc << 9), tot);
-                    noff = off & 511u;
-                    ntot = tot & 511u;
-                    loff = off >> 9;
-                    ltot = tot >> 9;
-                }
-                // opened internal cells -> next frontier
-                if (nnext + ntot > (uint32_t)FCAP) {
-                    overflow = true;
-                } else {
-                    for (uint32_t k = 0; k < nch; ++k) nxt[nnext + noff + k] = tp.x + k;
-                    nnext += ntot;
-                }
-
-                // opened leaves -> p-p ring, 32 particles per round
-                npp += ltot;
-                for (uint32_t r = 0; r < ltot; r += 32) {
-                    const uint32_t k = r + lane;
-                    // owner lane: the last lane whose offset is <= k
-                    int src = 0;
+    // entries [hb, hb + cnt) of the p-c ring (hb a multiple of 32, cnt <= 32)
+    __device__ __forceinline__ void flush_pc(const WarpLists &L, int hb, int cnt) {
+        const int end = hb + cnt;
+#pragma unroll 2
+        for (int j = hb + j0; j < end; j += S) {
+            const float4 a = L.ca[j], b = L.cb[j], c = L.cc[j];
 #pragma unroll
-                    for (int step = 16; step > 0; step >>= 1) {
-                        const uint32_t o = __shfl_sync(0xffffffffu, loff, src + step);
-                        if (o <= k) src += step;
-                    }
-                    const uint32_t sfirst = __shfl_sync(0xffffffffu, tp.x, src);
-                    const uint32_t soff = __shfl_sync(0xffffffffu, loff, src);
-                    if (k < ltot) {
-                        const uint32_t j = sfirst + (k - soff);
-                        const float4 h = A.body_hi[j], l = A.body_lo[j];
-                        const uint32_t s = (pp_tail + lane) & (RING - 1);
-                        L.pp[s] = make_float4((h.x - box.x) + (l.x - clo.x),
-                                              (h.y - box.y) + (l.y - clo.y),
-                                              (h.z - box.z) + (l.z - clo.z), h.w);
-                        L.pid[s] = (int)j;
-                    }
-                    pp_tail += min(32u, ltot - r);
-                    __syncwarp();
-                    if (pp_tail - pp_head >= 32u) {
-                        // the head is a multiple of 32: the 32 entries do not wrap
-                        const int hb = (int)(pp_head & (RING - 1));
-                        eval_pp<MASK>(L, hb + j0, hb + 32, S, t, eps2);
-                        pp_head += 32;
-                        __syncwarp();
-                    }
-                }
-                __syncwarp();
-                while (pc_tail - pc_head >= 32u) {
-                    const int hb = (int)(pc_head & (RING - 1));
-                    eval_pc(L, hb + j0, hb + 32, S, t, eps2);
-                    pc_head += 32;
-                }
-                __syncwarp();
-            }
-            __threadfence_block();
-            __syncwarp();
-            uint32_t *tmp = cur;
-            cur = nxt;
-            nxt = tmp;
-            ncur = nnext;
-            maxf = max(maxf, ncur);
+            for (int k = 0; k < 2; ++k)
+                pc_one(a, b, c, t.x[k], t.y[k], t.z[k], eps2, t.ax[k], t.ay[k], t.az[k], t.ph[k]);
         }
-        // drain the rings: fewer than 32 entries each, starting at a multiple of 32
-        {
-            const int hb = (int)(pc_head & (RING - 1));
-            eval_pc(L, hb + j0, hb + (int)(pc_tail - pc_head), S, t, eps2);
-            const int hp = (int)(pp_head & (RING - 1));
-            eval_pp<MASK>(L, hp + j0, hp + (int)(pp_tail - pp_head), S, t, eps2);
-        }
-        __syncwarp();
+    }
 
+    __device__ __forceinline__ void flush_pp(const WarpLists &L, int hb, int cnt) {
+        const int end = hb + cnt;
+#pragma unroll 2
+        for (int j = hb + j0; j < end; j += S) {
+            const float4 p = L.pp[j];
+            const int sid = L.pid[j];
+#pragma unroll
+            for (int k = 0; k < 2; ++k)
+                pp_one<MASK>(p, sid, t.id[k], t.x[k], t.y[k], t.z[k], eps2, t.ax[k], t.ay[k],
+                             t.az[k], t.ph[k]);
+        }
+    }
+
+    __device__ __forceinline__ void finish(const WalkArgs &A, uint32_t gf, uint32_t gc, int lane) {
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
             const float ax = A.G * sum_copies(t.ax[k], lane, T2, S);
@@ -370,34 +263,401 @@ __global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(const WalkArgs A) {
                 if (A.pot_c) A.pot_c[A.id[i]] = ph;
             }
         }
-        if (lane == 0) {
-            A.gnpp[g] = (int32_t)npp;
-            A.gnpc[g] = (int32_t)npc;
-            atomicAdd((unsigned long long *)&A.sc->n_pp, (unsigned long long)gc * npp);
-            atomicAdd((unsigned long long *)&A.sc->n_pc, (unsigned long long)gc * npc);
-            atomicMax(&A.sc->max_frontier, (int)maxf);
-            if (overflow) atomicOr(&A.sc->status, ST_OVERFLOW);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Adjoint evaluation
+// ---------------------------------------------------------------------------
+
+// Gradient of lambda.a + mu phi for one cell on one target (without G),
+// with respect to r = com - x_i (g_r), the cell mass (gM) and the symmetric
+// quadrupole Q (gQ: xx, yy, zz, xy, xz, yz).  With u = 1/s, w = u^2,
+// Q' = -3Q (as stored), rq = r.Q'r, lq = lambda.Q'r, lr = lambda.r:
+//   fQ    = c.w u^5 - 5/2 rq u^7                  (c.w = -3/2 trQ)
+//   alpha = M u^3 + fQ
+//   beta  = -3 M u^5 lr + mu alpha + lr (-5 c.w u^7 + 35/2 rq u^9) - 5 u^7 lq
+//   g_r   = alpha lambda + beta r + (mu u^5 - 5 u^7 lr) Q'r + u^5 Q'lambda
+//   gM    = lr u^3 - mu u
+//   gQ_ab = delta_ab (mu u^3/2 - 3/2 u^5 lr) + r_a r_b (15/2 u^7 lr - 3/2 mu u^5)
+//           - 3/2 u^5 (lambda_a r_b + r_a lambda_b)
+__device__ __forceinline__ void pc_vjp(const float4 a, const float4 b, const float4 c, float4 tp,
+                                       float4 tl, float eps2, float &gx, float &gy, float &gz,
+                                       float &gM, float gQ[6]) {
+    const float rx = a.x - tp.x, ry = a.y - tp.y, rz = a.z - tp.z;
+    float s2 = fmaf(rx, rx, eps2);
+    s2 = fmaf(ry, ry, s2);
+    s2 = fmaf(rz, rz, s2);
+    const float u = rsqrtf(s2);
+    const float w = u * u;
+    const float u3 = u * w, u5 = u3 * w, u7 = u5 * w, u9 = u7 * w;
+    const float qx = fmaf(b.x, rx, fmaf(b.w, ry, c.x * rz));  // Q'r
+    const float qy = fmaf(b.w, rx, fmaf(b.y, ry, c.y * rz));
+    const float qz = fmaf(c.x, rx, fmaf(c.y, ry, b.z * rz));
+    const float px = fmaf(b.x, tl.x, fmaf(b.w, tl.y, c.x * tl.z));  // Q'lambda
+    const float py = fmaf(b.w, tl.x, fmaf(b.y, tl.y, c.y * tl.z));
+    const float pz = fmaf(c.x, tl.x, fmaf(c.y, tl.y, b.z * tl.z));
+    const float rq = fmaf(rx, qx, fmaf(ry, qy, rz * qz));
+    const float lq = fmaf(tl.x, qx, fmaf(tl.y, qy, tl.z * qz));
+    const float lr = fmaf(tl.x, rx, fmaf(tl.y, ry, tl.z * rz));
+    const float mu = tl.w;
+    const float fQ = fmaf(c.w, u5, -2.5f * rq * u7);
+    const float alpha = fmaf(a.w, u3, fQ);
+    float beta = fmaf(-3.0f * a.w * u5, lr, mu * alpha);
+    beta = fmaf(lr, fmaf(-5.0f * c.w, u7, 17.5f * rq * u9), beta);
+    beta = fmaf(-5.0f * u7, lq, beta);
+    const float gam = fmaf(mu, u5, -5.0f * u7 * lr);
+    gx = fmaf(alpha, tl.x, fmaf(beta, rx, fmaf(gam, qx, u5 * px)));
+    gy = fmaf(alpha, tl.y, fmaf(beta, ry, fmaf(gam, qy, u5 * py)));
+    gz = fmaf(alpha, tl.z, fmaf(beta, rz, fmaf(gam, qz, u5 * pz)));
+    gM = fmaf(lr, u3, -mu * u);
+    const float p0 = fmaf(0.5f * mu, u3, -1.5f * u5 * lr);
+    const float p1 = fmaf(7.5f * u7, lr, -1.5f * mu * u5);
+    const float p2 = -1.5f * u5;
+    gQ[0] = fmaf(rx, fmaf(p1, rx, 2.0f * p2 * tl.x), p0);
+    gQ[1] = fmaf(ry, fmaf(p1, ry, 2.0f * p2 * tl.y), p0);
+    gQ[2] = fmaf(rz, fmaf(p1, rz, 2.0f * p2 * tl.z), p0);
+    gQ[3] = fmaf(p1 * rx, ry, p2 * fmaf(tl.x, ry, rx * tl.y));
+    gQ[4] = fmaf(p1 * rx, rz, p2 * fmaf(tl.x, rz, rx * tl.z));
+    gQ[5] = fmaf(p1 * ry, rz, p2 * fmaf(tl.y, rz, ry * tl.z));
+}
+
+// Gradient of lambda.a + mu phi for one p-p source (without G):
+//   g_r = m u^3 (lambda + (mu - 3 w lr) r),  gm = lr u^3 - mu u.
+__device__ __forceinline__ void pp_vjp(const float4 s, float4 tp, float4 tl, float eps2,
+                                       float &gx, float &gy, float &gz, float &gm) {
+    const float rx = s.x - tp.x, ry = s.y - tp.y, rz = s.z - tp.z;
+    float s2 = fmaf(rx, rx, eps2);
+    s2 = fmaf(ry, ry, s2);
+    s2 = fmaf(rz, rz, s2);
+    const float u = rsqrtf(s2);
+    const float w = u * u;
+    const float u3 = u * w;
+    const float lr = fmaf(tl.x, rx, fmaf(tl.y, ry, tl.z * rz));
+    const float co = fmaf(-3.0f * w, lr, tl.w);
+    const float k = s.w * u3;
+    gx = k * fmaf(co, rx, tl.x);
+    gy = k * fmaf(co, ry, tl.y);
+    gz = k * fmaf(co, rz, tl.z);
+    gm = fmaf(lr, u3, -tl.w * u);
+}
+
+// The adjoint evaluates each ring flush with one list entry per lane and a
+// loop over the group's targets (broadcast from shared memory).  The cell or
+// source adjoint stays in the lane's registers; the 3-vector target
+// gradient of each (entry, target) pair is summed over the 32 lanes with
+// shuffles and kept by lane (target mod 32).  Every lane is busy whatever
+// the group size.  Source and cell adjoints go to global memory with one
+// vector atomic per 4 values per flush; target gradients once per group.
+struct AdjointPolicy {
+    WarpTargets *T;
+    int gc;
+    float eps2, G;
+    float gx[2], gy[2], gz[2];  // targets lane and lane + 32
+
+    __device__ __forceinline__ void begin(const WalkArgs &A, WarpTargets *tgt, uint32_t gf,
+                                          uint32_t gcount, float4 box, float4 clo, int lane) {
+        T = tgt;
+        gc = (int)gcount;
+        eps2 = A.eps2;
+        G = A.G;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            gx[k] = gy[k] = gz[k] = 0.0f;
+            const int li = lane + 32 * k;
+            if (li < gc) {
+                const int64_t i = gf + li;
+                const float4 h = A.body_hi[i], l = A.body_lo[i];
+                T->pos[li] = make_float4((h.x - box.x) + (l.x - clo.x), (h.y - box.y) + (l.y - clo.y),
+                                         (h.z - box.z) + (l.z - clo.z), __int_as_float((int)i));
+                T->lam[li] = make_float4(A.lam[i], A.lam[A.n + i], A.lam[2 * A.n + i],
+                                         A.mu ? A.mu[i] : 0.0f);
+            }
         }
         __syncwarp();
     }
+
+    __device__ __forceinline__ void keep(int t, int lane, float vx, float vy, float vz) {
+        vx = warp_sum(vx);
+        vy = warp_sum(vy);
+        vz = warp_sum(vz);
+        if ((t & 31) == lane) {
+            if (t < 32) { gx[0] += vx; gy[0] += vy; gz[0] += vz; }
+            else { gx[1] += vx; gy[1] += vy; gz[1] += vz; }
+        }
+    }
+
+    __device__ __forceinline__ void flush_pc(const WarpLists &L, int hb, int cnt, int lane) {
+        if (cnt <= 0) return;
+        const bool v = lane < cnt;
+        const int j = hb + (v ? lane : 0);
+        const float4 a = L.ca[j], b = L.cb[j], c = L.cc[j];
+        float ax = 0, ay = 0, az = 0, aM = 0, aQ[6] = {0, 0, 0, 0, 0, 0};
+        for (int t = 0; t < gc; ++t) {
+            const float4 tp = T->pos[t], tl = T->lam[t];
+            float rx, ry, rz, m, q[6];
+            pc_vjp(a, b, c, tp, tl, eps2, rx, ry, rz, m, q);
+            if (!v) rx = ry = rz = m = 0.0f;
+            ax += rx;
+            ay += ry;
+            az += rz;
+            aM += m;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) aQ[k] += v ? q[k] : 0.0f;
+            keep(t, lane, rx, ry, rz);  // the target side gets -g_r (applied in finish)
+        }
+        if (v) cell_add(L.cid[j], ax, ay, az, aM, aQ);
+    }
+
+    float4 *cell_adj;
+    float4 *part_adj;
+    int64_t nn;
+
+    __device__ __forceinline__ void cell_add(int node, float ax, float ay, float az, float aM,
+                                             const float aQ[6]) {
+        atomicAdd(&cell_adj[node], make_float4(G * ax, G * ay, G * az, G * aM));
+        atomicAdd(&cell_adj[nn + node], make_float4(G * aQ[0], G * aQ[1], G * aQ[2], G * aQ[3]));
+        atomicAdd(&cell_adj[2 * nn + node], make_float4(G * aQ[4], G * aQ[5], 0.0f, 0.0f));
+    }
+
+    __device__ __forceinline__ void flush_pp(const WarpLists &L, int hb, int cnt, int lane) {
+        if (cnt <= 0) return;
+        const bool v = lane < cnt;
+        const int j = hb + (v ? lane : 0);
+        const float4 s = L.pp[j];
+        const int sid = L.pid[j];
+        float ax = 0, ay = 0, az = 0, am = 0;
+        for (int t = 0; t < gc; ++t) {
+            const float4 tp = T->pos[t], tl = T->lam[t];
+            float rx, ry, rz, m;
+            pp_vjp(s, tp, tl, eps2, rx, ry, rz, m);
+            if (!v || sid == __float_as_int(tp.w)) rx = ry = rz = m = 0.0f;  // self pair
+            ax += rx;
+            ay += ry;
+            az += rz;
+            am += m;
+            keep(t, lane, rx, ry, rz);
+        }
+        if (v) atomicAdd(&part_adj[sid], make_float4(G * ax, G * ay, G * az, G * am));
+    }
+
+    __device__ __forceinline__ void finish(const WalkArgs &A, uint32_t gf, uint32_t gcount, int lane) {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int li = lane + 32 * k;
+            if (li < gc)
+                atomicAdd(&part_adj[gf + li], make_float4(-G * gx[k], -G * gy[k], -G * gz[k], 0.0f));
+        }
+        __syncwarp();
+    }
+};
+
+// Forward and adjoint policies take the lane for their flushes differently.
+template <class P>
+__device__ __forceinline__ void do_flush_pc(P &pol, const WarpLists &L, int hb, int cnt, int lane);
+template <bool MASK>
+__device__ __forceinline__ void do_flush_pc(ForwardPolicy<MASK> &pol, const WarpLists &L, int hb,
+                                            int cnt, int) {
+    pol.flush_pc(L, hb, cnt);
+}
+__device__ __forceinline__ void do_flush_pc(AdjointPolicy &pol, const WarpLists &L, int hb, int cnt,
+                                            int lane) {
+    pol.flush_pc(L, hb, cnt, lane);
+}
+template <bool MASK>
+__device__ __forceinline__ void do_flush_pp(ForwardPolicy<MASK> &pol, const WarpLists &L, int hb,
+                                            int cnt, int) {
+    pol.flush_pp(L, hb, cnt);
+}
+__device__ __forceinline__ void do_flush_pp(AdjointPolicy &pol, const WarpLists &L, int hb, int cnt,
+                                            int lane) {
+    pol.flush_pp(L, hb, cnt, lane);
 }
 
-}  // namespace
+// ---------------------------------------------------------------------------
+// The traversal
+// ---------------------------------------------------------------------------
 
-int walk_resident_warps(bonsai_ctx *c) {
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk<true>, WALK_WARPS * 32, 0) !=
-            cudaSuccess ||
-        per_sm < 1)
-        per_sm = 1;
-    return per_sm * c->sm_count * WALK_WARPS;
+template <class P>
+__device__ __forceinline__ void walk_group(const WalkArgs &A, WarpLists &L, WarpTargets *tgt, P &pol,
+                                           uint32_t g, uint32_t *fa, uint32_t *fb, int lane,
+                                           uint32_t lt) {
+    const uint32_t gf = A.gfirst[g], gc = A.gcount[g];
+    const float4 box = A.gbox[g], half = A.ghalf[g], clo = A.glo[g];
+    pol.begin(A, tgt, gf, gc, box, clo, lane);
+
+    uint32_t pc_head = 0, pc_tail = 0, pp_head = 0, pp_tail = 0;
+    uint32_t npc = 0, npp = 0;
+    uint32_t *cur = fa, *nxt = fb;
+    if (lane == 0) cur[0] = 0u;  // the root
+    uint32_t ncur = 1;
+    uint32_t maxf = 1;
+    bool overflow = false;
+    __syncwarp();
+
+    while (ncur > 0) {
+        uint32_t nnext = 0;
+        for (uint32_t base = 0; base < ncur; base += 32) {
+            const uint32_t idx = base + lane;
+            const bool valid = idx < ncur;
+            const uint32_t node = valid ? cur[idx] : 0u;
+            const float4 m = A.mac[node];
+            const uint2 tp = A.topo[node];
+            // opening test: squared distance from com to the group box
+            float dx = fmaxf(__fsub_rn(fabsf(__fsub_rn(m.x, box.x)), half.x), 0.0f);
+            float dy = fmaxf(__fsub_rn(fabsf(__fsub_rn(m.y, box.y)), half.y), 0.0f);
+            float dz = fmaxf(__fsub_rn(fabsf(__fsub_rn(m.z, box.z)), half.z), 0.0f);
+            const float d2 =
+                __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+            const bool open = d2 < m.w;
+            const bool leaf = (tp.y & LEAF_FLAG) != 0u;
+            const bool accept = valid && !open;
+
+            // accepted cells -> p-c ring
+            const uint32_t am = __ballot_sync(0xffffffffu, accept);
+            if (accept) {
+                const uint32_t s = (pc_tail + __popc(am & lt)) & (RING - 1);
+                const float4 a = A.ca[node];
+                const float4 rel = make_float4((m.x - box.x) + (a.x - clo.x),
+                                               (m.y - box.y) + (a.y - clo.y),
+                                               (m.z - box.z) + (a.z - clo.z), a.w);
+                L.ca[s] = rel;
+                L.cb[s] = A.cb[node];
+                L.cc[s] = A.cc[node];
+                L.cid[s] = (int)node;
+            }
+            pc_tail += __popc(am);
+            npc += __popc(am);
+
+            // one warp scan for both the children of opened internal cells
+            // (low 9 bits: at most 8 per lane) and the particles of opened
+            // leaves (high bits); two scans when a leaf is very large
+            const uint32_t nch = (valid && open && !leaf) ? tp.y : 0u;
+            const uint32_t lc = (valid && open && leaf) ? (tp.y & ~LEAF_FLAG) : 0u;
+            uint32_t noff, ntot, loff, ltot;
+            if (__any_sync(0xffffffffu, lc > 4096u)) {
+                noff = warp_excl_scan(nch, ntot);
+                loff = warp_excl_scan(lc, ltot);
+            } else {
+                uint32_t tot;
+                const uint32_t off = warp_excl_scan(nch | (lc << 9), tot);
+                noff = off & 511u;
+                ntot = tot & 511u;
+                loff = off >> 9;
+                ltot = tot >> 9;
+            }
+            // opened internal cells -> next frontier
+            if (nnext + ntot > (uint32_t)FCAP) {
+                overflow = true;
+            } else {
+                for (uint32_t k = 0; k < nch; ++k) nxt[nnext + noff + k] = tp.x + k;
+                nnext += ntot;
+            }
+
+            // opened leaves -> p-p ring, 32 particles per round
+            npp += ltot;
+            for (uint32_t r = 0; r < ltot; r += 32) {
+                const uint32_t k = r + lane;
+                // owner lane: the last lane whose offset is <= k
+                int src = 0;
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1) {
+                    const uint32_t o = __shfl_sync(0xffffffffu, loff, src + step);
+                    if (o <= k) src += step;
+                }
+                const uint32_t sfirst = __shfl_sync(0xffffffffu, tp.x, src);
+                const uint32_t soff = __shfl_sync(0xffffffffu, loff, src);
+                if (k < ltot) {
+                    const uint32_t j = sfirst + (k - soff);
+                    const float4 h = A.body_hi[j], l = A.body_lo[j];
+                    const uint32_t s = (pp_tail + lane) & (RING - 1);
+                    L.pp[s] = make_float4((h.x - box.x) + (l.x - clo.x),
+                                          (h.y - box.y) + (l.y - clo.y),
+                                          (h.z - box.z) + (l.z - clo.z), h.w);
+                    L.pid[s] = (int)j;
+                }
+                pp_tail += min(32u, ltot - r);
+                __syncwarp();
+                if (pp_tail - pp_head >= 32u) {
+                    // the head is a multiple of 32: the 32 entries do not wrap
+                    do_flush_pp(pol, L, (int)(pp_head & (RING - 1)), 32, lane);
+                    pp_head += 32;
+                    __syncwarp();
+                }
+            }
+            __syncwarp();
+            while (pc_tail - pc_head >= 32u) {
+                do_flush_pc(pol, L, (int)(pc_head & (RING - 1)), 32, lane);
+                pc_head += 32;
+            }
+            __syncwarp();
+        }
+        __threadfence_block();
+        __syncwarp();
+        uint32_t *tmp = cur;
+        cur = nxt;
+        nxt = tmp;
+        ncur = nnext;
+        maxf = max(maxf, ncur);
+    }
+    // drain the rings: fewer than 32 entries each, starting at a multiple of 32
+    do_flush_pc(pol, L, (int)(pc_head & (RING - 1)), (int)(pc_tail - pc_head), lane);
+    do_flush_pp(pol, L, (int)(pp_head & (RING - 1)), (int)(pp_tail - pp_head), lane);
+    __syncwarp();
+    pol.finish(A, gf, gc, lane);
+    if (lane == 0) {
+        if (A.gnpp) A.gnpp[g] = (int32_t)npp;
+        if (A.gnpc) A.gnpc[g] = (int32_t)npc;
+        atomicAdd((unsigned long long *)&A.sc->n_pp, (unsigned long long)gc * npp);
+        atomicAdd((unsigned long long *)&A.sc->n_pc, (unsigned long long)gc * npc);
+        atomicMax(&A.sc->max_frontier, (int)maxf);
+        if (overflow) atomicOr(&A.sc->status, ST_OVERFLOW);
+    }
+    __syncwarp();
 }
 
-size_t walk_frontier_elems(int warps) { return (size_t)warps * 2 * FCAP; }
+template <bool MASK>
+__global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(const WalkArgs A) {
+    __shared__ WarpLists lists[WALK_WARPS];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const uint32_t lt = lanemask_lt();
+    const int64_t gw = (int64_t)blockIdx.x * WALK_WARPS + wib;
+    uint32_t *fa = A.frontier + gw * 2 * FCAP;
+    uint32_t *fb = fa + FCAP;
+    while (true) {
+        uint32_t g = 0;
+        if (lane == 0) g = atomicAdd(&A.sc->group_counter, 1u);
+        g = __shfl_sync(0xffffffffu, g, 0);
+        if (g >= A.ngroups) break;
+        ForwardPolicy<MASK> pol;
+        walk_group(A, lists[wib], nullptr, pol, g, fa, fb, lane, lt);
+    }
+}
 
-int walk_force(bonsai_ctx *c, float theta, float eps, float *acc_c, float *pot_c) {
-    const bool mask_self = !(eps > 0.0f) || !(theta < 0.57f);
-    WalkArgs a;
+__global__ void __launch_bounds__(WALK_WARPS * 32) k_walk_adjoint(const WalkArgs A) {
+    __shared__ WarpLists lists[WALK_WARPS];
+    __shared__ WarpTargets targets[WALK_WARPS];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const uint32_t lt = lanemask_lt();
+    const int64_t gw = (int64_t)blockIdx.x * WALK_WARPS + wib;
+    uint32_t *fa = A.frontier + gw * 2 * FCAP;
+    uint32_t *fb = fa + FCAP;
+    while (true) {
+        uint32_t g = 0;
+        if (lane == 0) g = atomicAdd(&A.sc->group_counter, 1u);
+        g = __shfl_sync(0xffffffffu, g, 0);
+        if (g >= A.ngroups) break;
+        AdjointPolicy pol;
+        pol.cell_adj = A.cell_adj;
+        pol.part_adj = A.part_adj;
+        pol.nn = A.nn;
+        walk_group(A, lists[wib], &targets[wib], pol, g, fa, fb, lane, lt);
+    }
+}
+
+void fill_args(bonsai_ctx *c, float eps, WalkArgs &a) {
     a.mac = c->cell_mac.p;
     a.topo = c->cell_topo.p;
     a.ca = c->cell_a.p;
@@ -416,20 +676,82 @@ int walk_force(bonsai_ctx *c, float theta, float eps, float *acc_c, float *pot_c
     a.G = (float)c->prm.G;
     a.acc = c->acc.p;
     a.pot = c->pot.p;
-    a.acc_c = acc_c;
-    a.pot_c = pot_c;
+    a.acc_c = nullptr;
+    a.pot_c = nullptr;
     a.id = c->id.p;
     a.gnpp = c->grp_npp.p;
     a.gnpc = c->grp_npc.p;
+    a.lam = nullptr;
+    a.mu = nullptr;
+    a.cell_adj = nullptr;
+    a.part_adj = nullptr;
+    a.nn = c->n_nodes;
     a.frontier = c->frontier.p;
     a.sc = c->dsc;
-    const int blocks = c->walk_warps / WALK_WARPS;
+}
+
+}  // namespace
+
+int walk_resident_warps(bonsai_ctx *c) {
+    int a = 0, b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_walk<true>, WALK_WARPS * 32, 0) !=
+            cudaSuccess || a < 1)
+        a = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_walk<false>, WALK_WARPS * 32, 0) !=
+            cudaSuccess || b < 1)
+        b = 1;
+    int d = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d, k_walk_adjoint, WALK_WARPS * 32, 0) !=
+            cudaSuccess || d < 1)
+        d = 1;
+    const int per_sm = a > b ? (a > d ? a : d) : (b > d ? b : d);
+    return per_sm * c->sm_count * WALK_WARPS;
+}
+
+size_t walk_frontier_elems(int warps) { return (size_t)warps * 2 * FCAP; }
+
+static int launch_blocks(const void *fn, bonsai_ctx *c) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, WALK_WARPS * 32, 0) !=
+            cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    int blocks = per_sm * c->sm_count;
+    const int cap = c->walk_warps / WALK_WARPS;  // frontier scratch is sized for this many
+    return blocks < cap ? blocks : cap;
+}
+
+int walk_force(bonsai_ctx *c, float theta, float eps, float *acc_c, float *pot_c) {
+    const bool mask_self = !(eps > 0.0f) || !(theta < 0.57f);
+    WalkArgs a;
+    fill_args(c, eps, a);
+    a.acc_c = acc_c;
+    a.pot_c = pot_c;
     cudaEventRecord(c->ev[8], c->stream);
     if (mask_self)
-        k_walk<true><<<blocks, WALK_WARPS * 32, 0, c->stream>>>(a);
+        k_walk<true><<<launch_blocks((const void *)k_walk<true>, c), WALK_WARPS * 32, 0, c->stream>>>(a);
     else
-        k_walk<false><<<blocks, WALK_WARPS * 32, 0, c->stream>>>(a);
+        k_walk<false><<<launch_blocks((const void *)k_walk<false>, c), WALK_WARPS * 32, 0, c->stream>>>(a);
     cudaEventRecord(c->ev[9], c->stream);
+    c->launches += 1;
+    return cudaPeekAtLastError() == cudaSuccess ? BONSAI_OK : BONSAI_ECUDA;
+}
+
+// The adjoint walk: lam [3][n] and mu [n] (or null) in sorted order; adds the
+// source-side and target-side gradients (times G) into part_adj [n] and the
+// cell adjoints into cell_adj [3][nn].
+int walk_adjoint(bonsai_ctx *c, float eps, const float *lam, const float *mu, float4 *cell_adj,
+                 float4 *part_adj) {
+    WalkArgs a;
+    fill_args(c, eps, a);
+    a.acc = nullptr;
+    a.pot = nullptr;
+    a.gnpp = nullptr;
+    a.gnpc = nullptr;
+    a.lam = lam;
+    a.mu = mu;
+    a.cell_adj = cell_adj;
+    a.part_adj = part_adj;
+    k_walk_adjoint<<<launch_blocks((const void *)k_walk_adjoint, c), WALK_WARPS * 32, 0, c->stream>>>(a);
     c->launches += 1;
     return cudaPeekAtLastError() == cudaSuccess ? BONSAI_OK : BONSAI_ECUDA;
 }

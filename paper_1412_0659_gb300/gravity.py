@@ -94,6 +94,27 @@ class TreeGravity:
         capi.tree_solve_host(self.ctx, pos, mass, theta, eps, acc, pot)
         self.n = int(mass.shape[0])
 
+    # -- adjoint -----------------------------------------------------------
+    def forces_vjp(self, gacc: torch.Tensor, gpot: torch.Tensor | None = None):
+        """(dL/dx, dL/dm) for L = sum gacc.a + gpot.phi of the last forces()."""
+        dev = torch.device("cuda", torch.cuda.current_device())
+        gpos = torch.empty((3, self.n), dtype=torch.float64, device=dev)
+        gmass = torch.empty(self.n, dtype=torch.float64, device=dev)
+        capi.tree_forces_vjp(self.ctx, gacc.contiguous(), gpos, gmass,
+                             None if gpot is None else gpot.contiguous())
+        return gpos, gmass
+
+    def run(self, nsteps: int, dt: float, ckpt_every: int = 8):
+        capi.tree_run(self.ctx, nsteps, dt, ckpt_every)
+
+    def run_vjp(self, xbar: torch.Tensor, vbar: torch.Tensor, mbar: torch.Tensor | None = None):
+        dev = torch.device("cuda", torch.cuda.current_device())
+        out = [torch.empty((3, self.n), dtype=torch.float64, device=dev) for _ in range(2)]
+        mb = torch.empty(self.n, dtype=torch.float64, device=dev)
+        capi.tree_run_vjp(self.ctx, xbar.contiguous(), vbar.contiguous(),
+                          None if mbar is None else mbar.contiguous(), out[0], out[1], mb)
+        return out[0], out[1], mb
+
     # -- internal views (key-sorted order) -------------------------------
     def debug(self) -> dict:
         st = self.stats()
