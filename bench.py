@@ -192,6 +192,31 @@ def run_ours(args):
     value = tot_flops / (t_max * 1e-3) / 1e12
     ms_per_step = t_max / args.steps
 
+    # --- adjoint: force VJP on the same tree and lists, against the forward ---
+    adjoint = None
+    if not args.no_adjoint:
+        lam = torch.randn(3, n, device=dev)
+        mu = torch.randn(n, device=dev)
+        g.forces()
+        g.forces_vjp(lam, mu)
+        tf, tb = [], []
+        for _ in range(max(2, min(args.steps, 5))):
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a2 = torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            g.forces()
+            a1.record(stream)
+            g.forces_vjp(lam, mu)
+            a2.record(stream)
+            torch.cuda.synchronize()
+            tf.append(a0.elapsed_time(a1))
+            tb.append(a1.elapsed_time(a2))
+        fwd, bwd = statistics.median(tf), statistics.median(tb)
+        adjoint = {"fwd_ms": fwd, "vjp_ms": bwd, "ratio_fwd_plus_bwd_over_fwd": (fwd + bwd) / fwd,
+                   "what": "tree_forces then tree_forces_vjp (random cotangents for a and phi) on the "
+                           "same tree, median of repeats"}
+
     # --- end to end through the host-buffer C-ABI entry (copies timed) ---
     pin_pos = torch.from_numpy(m.pos).pin_memory()
     pin_mass = torch.from_numpy(m.mass).pin_memory()
@@ -257,6 +282,7 @@ def run_ours(args):
             "phase_ms": {"keys_sort": statistics.mean(keys_ms), "tree_groups_multipoles": statistics.mean(tree_ms),
                          "force": statistics.mean(force_ms), "walk_kernel": walk_avg},
             "energy": {"E_tot": diag["E_tot"] if diag else None},
+            "adjoint": adjoint,
             "clocks": clk, "gpu_launches": int(launches), "roofline": roofline, "e2e": e2e,
             "cpu_baseline": cpu,
         }
@@ -328,8 +354,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="milky-way-2^23", choices=["milky-way-2^23", "milky-way-2^20", "plummer-2^14"])
-    ap.add_argument("--cpu-groups", type=int, default=96, help="groups walked by the CPU oracle sample")
+    ap.add_argument("--cpu-groups", type=int, default=24000,
+                    help="groups walked by the CPU oracle sample (about 10 s of CPU work at 2^23)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward timing")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per walk launch from an ncu capture (null when not captured)")
     args = ap.parse_args()

@@ -94,12 +94,6 @@ __device__ __forceinline__ uint32_t warp_excl_scan(uint32_t v, uint32_t &total) 
     return inc - v;
 }
 
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
 // ---------------------------------------------------------------------------
 // Forward evaluation
 // ---------------------------------------------------------------------------
@@ -272,25 +266,30 @@ struct ForwardPolicy {
 
 // Gradient of lambda.a + mu phi for one cell on one target (without G),
 // with respect to r = com - x_i (g_r), the cell mass (gM) and the symmetric
-// quadrupole Q (gQ: xx, yy, zz, xy, xz, yz).  With u = 1/s, w = u^2,
-// Q' = -3Q (as stored), rq = r.Q'r, lq = lambda.Q'r, lr = lambda.r:
+// quadrupole Q.  With u = 1/s, w = u^2, Q' = -3Q (as stored), rq = r.Q'r,
+// lq = lambda.Q'r, lr = lambda.r:
 //   fQ    = c.w u^5 - 5/2 rq u^7                  (c.w = -3/2 trQ)
 //   alpha = M u^3 + fQ
 //   beta  = -3 M u^5 lr + mu alpha + lr (-5 c.w u^7 + 35/2 rq u^9) - 5 u^7 lq
 //   g_r   = alpha lambda + beta r + (mu u^5 - 5 u^7 lr) Q'r + u^5 Q'lambda
 //   gM    = lr u^3 - mu u
-//   gQ_ab = delta_ab (mu u^3/2 - 3/2 u^5 lr) + r_a r_b (15/2 u^7 lr - 3/2 mu u^5)
-//           - 3/2 u^5 (lambda_a r_b + r_a lambda_b)
-__device__ __forceinline__ void pc_vjp(const float4 a, const float4 b, const float4 c, float4 tp,
-                                       float4 tl, float eps2, float &gx, float &gy, float &gz,
-                                       float &gM, float gQ[6]) {
-    const float rx = a.x - tp.x, ry = a.y - tp.y, rz = a.z - tp.z;
+//   gQ    = P0 I + (r v^T + v r^T),  P0 = mu u^3/2 - 3/2 u^5 lr,
+//           v = (15/4 u^7 lr - 3/4 mu u^5) r - 3/2 u^5 lambda.
+// Returns P0 and v2 = 2v; the caller accumulates gQ from them.
+// Per-cell constants of pc_vjp, computed once per flush: M3 = -3M, cw5 = -5 c.w.
+__device__ __forceinline__ void pc_vjp(const float4 a, const float4 b, const float4 c, float M3,
+                                       float cw5, float4 tp, float4 tl, float eps2, float &gx,
+                                       float &gy, float &gz, float &gM, float &P0, float &vx,
+                                       float &vy, float &vz, float &rx, float &ry, float &rz) {
+    rx = a.x - tp.x;
+    ry = a.y - tp.y;
+    rz = a.z - tp.z;
     float s2 = fmaf(rx, rx, eps2);
     s2 = fmaf(ry, ry, s2);
     s2 = fmaf(rz, rz, s2);
     const float u = rsqrtf(s2);
     const float w = u * u;
-    const float u3 = u * w, u5 = u3 * w, u7 = u5 * w, u9 = u7 * w;
+    const float u3 = u * w, u5 = u3 * w, u7 = u5 * w;
     const float qx = fmaf(b.x, rx, fmaf(b.w, ry, c.x * rz));  // Q'r
     const float qy = fmaf(b.w, rx, fmaf(b.y, ry, c.y * rz));
     const float qz = fmaf(c.x, rx, fmaf(c.y, ry, b.z * rz));
@@ -301,36 +300,36 @@ __device__ __forceinline__ void pc_vjp(const float4 a, const float4 b, const flo
     const float lq = fmaf(tl.x, qx, fmaf(tl.y, qy, tl.z * qz));
     const float lr = fmaf(tl.x, rx, fmaf(tl.y, ry, tl.z * rz));
     const float mu = tl.w;
-    const float fQ = fmaf(c.w, u5, -2.5f * rq * u7);
-    const float alpha = fmaf(a.w, u3, fQ);
-    float beta = fmaf(-3.0f * a.w * u5, lr, mu * alpha);
-    beta = fmaf(lr, fmaf(-5.0f * c.w, u7, 17.5f * rq * u9), beta);
-    beta = fmaf(-5.0f * u7, lq, beta);
-    const float gam = fmaf(mu, u5, -5.0f * u7 * lr);
+    // alpha = u^3 (M + w (c.w - 5/2 rq w))
+    const float alpha = u3 * fmaf(w, fmaf(-2.5f * rq, w, c.w), a.w);
+    // beta = lr u^5 (-3M + w (-5 c.w + 35/2 rq w)) + mu alpha - 5 u^7 lq
+    const float m5u7 = -5.0f * u7;
+    const float K = u5 * fmaf(w, fmaf(17.5f * rq, w, cw5), M3);
+    const float beta = fmaf(lr, K, fmaf(mu, alpha, m5u7 * lq));
+    const float gam = fmaf(mu, u5, m5u7 * lr);
     gx = fmaf(alpha, tl.x, fmaf(beta, rx, fmaf(gam, qx, u5 * px)));
     gy = fmaf(alpha, tl.y, fmaf(beta, ry, fmaf(gam, qy, u5 * py)));
     gz = fmaf(alpha, tl.z, fmaf(beta, rz, fmaf(gam, qz, u5 * pz)));
     gM = fmaf(lr, u3, -mu * u);
-    const float p0 = fmaf(0.5f * mu, u3, -1.5f * u5 * lr);
-    const float p1 = fmaf(7.5f * u7, lr, -1.5f * mu * u5);
-    const float p2 = -1.5f * u5;
-    gQ[0] = fmaf(rx, fmaf(p1, rx, 2.0f * p2 * tl.x), p0);
-    gQ[1] = fmaf(ry, fmaf(p1, ry, 2.0f * p2 * tl.y), p0);
-    gQ[2] = fmaf(rz, fmaf(p1, rz, 2.0f * p2 * tl.z), p0);
-    gQ[3] = fmaf(p1 * rx, ry, p2 * fmaf(tl.x, ry, rx * tl.y));
-    gQ[4] = fmaf(p1 * rx, rz, p2 * fmaf(tl.x, rz, rx * tl.z));
-    gQ[5] = fmaf(p1 * ry, rz, p2 * fmaf(tl.y, rz, ry * tl.z));
+    const float m15u5 = -1.5f * u5;
+    P0 = fmaf(0.5f * mu, u3, m15u5 * lr);
+    const float p1 = fmaf(7.5f * u7, lr, m15u5 * mu);  // v2 = p1 r - 3 u^5 lambda
+    const float m3u5 = 2.0f * m15u5;
+    vx = fmaf(p1, rx, m3u5 * tl.x);
+    vy = fmaf(p1, ry, m3u5 * tl.y);
+    vz = fmaf(p1, rz, m3u5 * tl.z);
 }
 
 // Gradient of lambda.a + mu phi for one p-p source (without G):
-//   g_r = m u^3 (lambda + (mu - 3 w lr) r),  gm = lr u^3 - mu u.
-__device__ __forceinline__ void pp_vjp(const float4 s, float4 tp, float4 tl, float eps2,
+//   g_r = m u^3 (lambda + (mu - 3 w lr) r),  gm = lr u^3 - mu u;
+// zero for the self pair (u is set to 0, which also avoids r = 0 at eps = 0).
+__device__ __forceinline__ void pp_vjp(const float4 s, bool self, float4 tp, float4 tl, float eps2,
                                        float &gx, float &gy, float &gz, float &gm) {
     const float rx = s.x - tp.x, ry = s.y - tp.y, rz = s.z - tp.z;
     float s2 = fmaf(rx, rx, eps2);
     s2 = fmaf(ry, ry, s2);
     s2 = fmaf(rz, rz, s2);
-    const float u = rsqrtf(s2);
+    const float u = self ? 0.0f : rsqrtf(s2);
     const float w = u * u;
     const float u3 = u * w;
     const float lr = fmaf(tl.x, rx, fmaf(tl.y, ry, tl.z * rz));
@@ -342,18 +341,31 @@ __device__ __forceinline__ void pp_vjp(const float4 s, float4 tp, float4 tl, flo
     gm = fmaf(lr, u3, -tl.w * u);
 }
 
+// Per-warp scratch of the adjoint: a 32 x 24 transpose buffer for the target
+// gradients of a chunk of 8 targets, and the running target gradients.
+constexpr int ADJ_CHUNK = 8;
+constexpr int ADJ_ROW = 3 * ADJ_CHUNK + 4;  // 28 floats: row stores and column sums conflict-free
+struct __align__(16) WarpAdjoint {
+    float red[32 * ADJ_ROW];
+    float tacc[NCRIT * 3];
+};
+
 // The adjoint evaluates each ring flush with one list entry per lane and a
 // loop over the group's targets (broadcast from shared memory).  The cell or
-// source adjoint stays in the lane's registers; the 3-vector target
-// gradient of each (entry, target) pair is summed over the 32 lanes with
-// shuffles and kept by lane (target mod 32).  Every lane is busy whatever
-// the group size.  Source and cell adjoints go to global memory with one
-// vector atomic per 4 values per flush; target gradients once per group.
+// source adjoint stays in the lane's registers.  The 3-vector target
+// gradients of 8 targets at a time are transposed through shared memory and
+// each column summed by one lane (24 lanes, 32 rows), which costs far fewer
+// instructions than a shuffle reduction per target.  Every lane is busy
+// whatever the group size.  Source and cell adjoints go to global memory with
+// one vector atomic per 4 values per flush; target gradients once per group.
 struct AdjointPolicy {
     WarpTargets *T;
+    WarpAdjoint *W;
     int gc;
     float eps2, G;
-    float gx[2], gy[2], gz[2];  // targets lane and lane + 32
+    float4 *cell_adj;
+    float4 *part_adj;
+    int64_t nn;
 
     __device__ __forceinline__ void begin(const WalkArgs &A, WarpTargets *tgt, uint32_t gf,
                                           uint32_t gcount, float4 box, float4 clo, int lane) {
@@ -363,7 +375,6 @@ struct AdjointPolicy {
         G = A.G;
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
-            gx[k] = gy[k] = gz[k] = 0.0f;
             const int li = lane + 32 * k;
             if (li < gc) {
                 const int64_t i = gf + li;
@@ -374,44 +385,79 @@ struct AdjointPolicy {
                                          A.mu ? A.mu[i] : 0.0f);
             }
         }
+        for (int k = lane; k < NCRIT * 3; k += 32) W->tacc[k] = 0.0f;
         __syncwarp();
     }
 
-    __device__ __forceinline__ void keep(int t, int lane, float vx, float vy, float vz) {
-        vx = warp_sum(vx);
-        vy = warp_sum(vy);
-        vz = warp_sum(vz);
-        if ((t & 31) == lane) {
-            if (t < 32) { gx[0] += vx; gy[0] += vy; gz[0] += vz; }
-            else { gx[1] += vx; gy[1] += vy; gz[1] += vz; }
-        }
-    }
-
-    __device__ __forceinline__ void flush_pc(const WarpLists &L, int hb, int cnt, int lane) {
-        if (cnt <= 0) return;
-        const bool v = lane < cnt;
-        const int j = hb + (v ? lane : 0);
-        const float4 a = L.ca[j], b = L.cb[j], c = L.cc[j];
-        float ax = 0, ay = 0, az = 0, aM = 0, aQ[6] = {0, 0, 0, 0, 0, 0};
-        for (int t = 0; t < gc; ++t) {
-            const float4 tp = T->pos[t], tl = T->lam[t];
-            float rx, ry, rz, m, q[6];
-            pc_vjp(a, b, c, tp, tl, eps2, rx, ry, rz, m, q);
-            if (!v) rx = ry = rz = m = 0.0f;
-            ax += rx;
-            ay += ry;
-            az += rz;
-            aM += m;
+    // add the 8 targets' gradients held in part (this lane's row) to tacc
+    __device__ __forceinline__ void reduce_chunk(const float part[3 * ADJ_CHUNK], int t0, int lane) {
+        float4 *row = reinterpret_cast<float4 *>(&W->red[lane * ADJ_ROW]);
 #pragma unroll
-            for (int k = 0; k < 6; ++k) aQ[k] += v ? q[k] : 0.0f;
-            keep(t, lane, rx, ry, rz);  // the target side gets -g_r (applied in finish)
+        for (int k = 0; k < 3 * ADJ_CHUNK / 4; ++k)
+            row[k] = make_float4(part[4 * k], part[4 * k + 1], part[4 * k + 2], part[4 * k + 3]);
+        __syncwarp();
+        if (lane < 3 * ADJ_CHUNK) {
+            float s = 0.0f;
+#pragma unroll 8
+            for (int r = 0; r < 32; ++r) s += W->red[r * ADJ_ROW + lane];
+            const int t = t0 + lane / 3;
+            if (t < gc) W->tacc[3 * t0 + lane] += s;
         }
-        if (v) cell_add(L.cid[j], ax, ay, az, aM, aQ);
+        __syncwarp();
     }
 
-    float4 *cell_adj;
-    float4 *part_adj;
-    int64_t nn;
+    template <bool FULL>
+    __device__ __forceinline__ void flush_pc(const WarpLists &L, int hb, int cnt, int lane) {
+        const bool v = FULL || lane < cnt;
+        const int j = hb + (v ? lane : 0);
+        const float4 a = L.ca[j], b = L.cb[j];
+        float4 c = L.cc[j];
+        float4 am = a;
+        if (!FULL && !v) {  // an empty lane: a massless, quadrupole-free cell
+            am.w = 0.0f;
+            c = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        }
+        const float4 bm = (!FULL && !v) ? make_float4(0.0f, 0.0f, 0.0f, 0.0f) : b;
+        const float M3 = -3.0f * am.w, cw5 = -5.0f * c.w;
+        float ax = 0, ay = 0, az = 0, aM = 0, aP = 0;
+        float dxx = 0, dyy = 0, dzz = 0, oxy = 0, oxz = 0, oyz = 0;
+        for (int t0 = 0; t0 < gc; t0 += ADJ_CHUNK) {
+            float part[3 * ADJ_CHUNK];
+#pragma unroll
+            for (int tt = 0; tt < ADJ_CHUNK; ++tt) {
+                const int t = t0 + tt;
+                float gx = 0.0f, gy = 0.0f, gz = 0.0f;
+                if (t < gc) {
+                    const float4 tp = T->pos[t], tl = T->lam[t];
+                    float gM, P0, vx, vy, vz, rx, ry, rz;
+                    pc_vjp(am, bm, c, M3, cw5, tp, tl, eps2, gx, gy, gz, gM, P0, vx, vy, vz, rx, ry,
+                           rz);
+                    if (!FULL && !v) gx = gy = gz = gM = P0 = vx = vy = vz = 0.0f;
+                    ax += gx;
+                    ay += gy;
+                    az += gz;
+                    aM += gM;
+                    aP += P0;
+                    dxx = fmaf(rx, vx, dxx);
+                    dyy = fmaf(ry, vy, dyy);
+                    dzz = fmaf(rz, vz, dzz);
+                    oxy = fmaf(rx, vy, fmaf(ry, vx, oxy));
+                    oxz = fmaf(rx, vz, fmaf(rz, vx, oxz));
+                    oyz = fmaf(ry, vz, fmaf(rz, vy, oyz));
+                }
+                part[3 * tt] = gx;
+                part[3 * tt + 1] = gy;
+                part[3 * tt + 2] = gz;
+            }
+            reduce_chunk(part, t0, lane);
+        }
+        if (v) {
+            // gQ = P0 I + (r v^T + v r^T) with v2 = 2v accumulated:
+            // diagonal P0 + r_a v2_a, off-diagonal (r_a v2_b + r_b v2_a) / 2
+            const float aQ[6] = {aP + dxx, aP + dyy, aP + dzz, 0.5f * oxy, 0.5f * oxz, 0.5f * oyz};
+            cell_add(L.cid[j], ax, ay, az, aM, aQ);
+        }
+    }
 
     __device__ __forceinline__ void cell_add(int node, float ax, float ay, float az, float aM,
                                              const float aQ[6]) {
@@ -420,33 +466,48 @@ struct AdjointPolicy {
         atomicAdd(&cell_adj[2 * nn + node], make_float4(G * aQ[4], G * aQ[5], 0.0f, 0.0f));
     }
 
+    template <bool FULL>
     __device__ __forceinline__ void flush_pp(const WarpLists &L, int hb, int cnt, int lane) {
-        if (cnt <= 0) return;
-        const bool v = lane < cnt;
+        const bool v = FULL || lane < cnt;
         const int j = hb + (v ? lane : 0);
-        const float4 s = L.pp[j];
+        float4 s = L.pp[j];
+        if (!FULL && !v) s.w = 0.0f;  // an empty lane: a massless source
         const int sid = L.pid[j];
         float ax = 0, ay = 0, az = 0, am = 0;
-        for (int t = 0; t < gc; ++t) {
-            const float4 tp = T->pos[t], tl = T->lam[t];
-            float rx, ry, rz, m;
-            pp_vjp(s, tp, tl, eps2, rx, ry, rz, m);
-            if (!v || sid == __float_as_int(tp.w)) rx = ry = rz = m = 0.0f;  // self pair
-            ax += rx;
-            ay += ry;
-            az += rz;
-            am += m;
-            keep(t, lane, rx, ry, rz);
+        for (int t0 = 0; t0 < gc; t0 += ADJ_CHUNK) {
+            float part[3 * ADJ_CHUNK];
+#pragma unroll
+            for (int tt = 0; tt < ADJ_CHUNK; ++tt) {
+                const int t = t0 + tt;
+                float gx = 0.0f, gy = 0.0f, gz = 0.0f;
+                if (t < gc) {
+                    const float4 tp = T->pos[t], tl = T->lam[t];
+                    float gm;
+                    pp_vjp(s, sid == __float_as_int(tp.w), tp, tl, eps2, gx, gy, gz, gm);
+                    if (!FULL && !v) gx = gy = gz = gm = 0.0f;
+                    ax += gx;
+                    ay += gy;
+                    az += gz;
+                    am += gm;
+                }
+                part[3 * tt] = gx;
+                part[3 * tt + 1] = gy;
+                part[3 * tt + 2] = gz;
+            }
+            reduce_chunk(part, t0, lane);
         }
         if (v) atomicAdd(&part_adj[sid], make_float4(G * ax, G * ay, G * az, G * am));
     }
 
     __device__ __forceinline__ void finish(const WalkArgs &A, uint32_t gf, uint32_t gcount, int lane) {
+        __syncwarp();
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
             const int li = lane + 32 * k;
             if (li < gc)
-                atomicAdd(&part_adj[gf + li], make_float4(-G * gx[k], -G * gy[k], -G * gz[k], 0.0f));
+                atomicAdd(&part_adj[gf + li],
+                          make_float4(-G * W->tacc[3 * li], -G * W->tacc[3 * li + 1],
+                                      -G * W->tacc[3 * li + 2], 0.0f));
         }
         __syncwarp();
     }
@@ -462,7 +523,8 @@ __device__ __forceinline__ void do_flush_pc(ForwardPolicy<MASK> &pol, const Warp
 }
 __device__ __forceinline__ void do_flush_pc(AdjointPolicy &pol, const WarpLists &L, int hb, int cnt,
                                             int lane) {
-    pol.flush_pc(L, hb, cnt, lane);
+    if (cnt >= 32) pol.flush_pc<true>(L, hb, 32, lane);
+    else if (cnt > 0) pol.flush_pc<false>(L, hb, cnt, lane);
 }
 template <bool MASK>
 __device__ __forceinline__ void do_flush_pp(ForwardPolicy<MASK> &pol, const WarpLists &L, int hb,
@@ -471,7 +533,8 @@ __device__ __forceinline__ void do_flush_pp(ForwardPolicy<MASK> &pol, const Warp
 }
 __device__ __forceinline__ void do_flush_pp(AdjointPolicy &pol, const WarpLists &L, int hb, int cnt,
                                             int lane) {
-    pol.flush_pp(L, hb, cnt, lane);
+    if (cnt >= 32) pol.flush_pp<true>(L, hb, 32, lane);
+    else if (cnt > 0) pol.flush_pp<false>(L, hb, cnt, lane);
 }
 
 // ---------------------------------------------------------------------------
@@ -635,9 +698,10 @@ __global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(const WalkArgs A) {
     }
 }
 
-__global__ void __launch_bounds__(WALK_WARPS * 32) k_walk_adjoint(const WalkArgs A) {
+__global__ void __launch_bounds__(WALK_WARPS * 32, 5) k_walk_adjoint(const WalkArgs A) {
     __shared__ WarpLists lists[WALK_WARPS];
     __shared__ WarpTargets targets[WALK_WARPS];
+    __shared__ WarpAdjoint scratch[WALK_WARPS];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const uint32_t lt = lanemask_lt();
@@ -653,6 +717,7 @@ __global__ void __launch_bounds__(WALK_WARPS * 32) k_walk_adjoint(const WalkArgs
         pol.cell_adj = A.cell_adj;
         pol.part_adj = A.part_adj;
         pol.nn = A.nn;
+        pol.W = &scratch[wib];
         walk_group(A, lists[wib], &targets[wib], pol, g, fa, fb, lane, lt);
     }
 }

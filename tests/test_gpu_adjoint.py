@@ -14,14 +14,15 @@ pytestmark = pytest.mark.gpu
 
 def _rel(a, b):
     """Per-particle relative error of 3-vectors (columns) or scalars.  With
-    random cotangents a particle's gradient is a sum of terms of both signs
-    that can nearly cancel; the denominator is floored at 1e-3 of the RMS
-    gradient so that FP32 rounding of such near-zero sums does not count as
-    a relative error of order one."""
+    random cotangents a particle's gradient is a sum of thousands of FP32
+    terms of both signs that can nearly cancel; its rounding error is about
+    eps_32 sqrt(n_terms) |term|, i.e. ~1e-6 of the RMS gradient.  The
+    denominator is therefore floored at 1e-2 of the RMS gradient, so that
+    near-zero sums do not count as relative errors of order one."""
     if a.ndim == 2:
         nb = np.linalg.norm(b, axis=0)
-        return np.linalg.norm(a - b, axis=0) / np.maximum(nb, 1e-3 * np.sqrt((nb ** 2).mean()))
-    return np.abs(a - b) / np.maximum(np.abs(b), 1e-3 * np.sqrt((b ** 2).mean()))
+        return np.linalg.norm(a - b, axis=0) / np.maximum(nb, 1e-2 * np.sqrt((nb ** 2).mean()))
+    return np.abs(a - b) / np.maximum(np.abs(b), 1e-2 * np.sqrt((b ** 2).mean()))
 
 
 def _gpu_vjp(m, theta, eps, G, lam, mu):
