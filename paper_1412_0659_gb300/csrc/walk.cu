@@ -210,7 +210,7 @@ struct ForwardPolicy {
     // entries [hb, hb + cnt) of the p-c ring (hb a multiple of 32, cnt <= 32)
     __device__ __forceinline__ void flush_pc(const WarpLists &L, int hb, int cnt) {
         const int end = hb + cnt;
-#pragma unroll 2
+#pragma unroll 1
         for (int j = hb + j0; j < end; j += S) {
             const float4 a = L.ca[j], b = L.cb[j], c = L.cc[j];
 #pragma unroll
@@ -221,7 +221,7 @@ struct ForwardPolicy {
 
     __device__ __forceinline__ void flush_pp(const WarpLists &L, int hb, int cnt) {
         const int end = hb + cnt;
-#pragma unroll 2
+#pragma unroll 1
         for (int j = hb + j0; j < end; j += S) {
             const float4 p = L.pp[j];
             const int sid = L.pid[j];
