@@ -117,6 +117,16 @@ int tree_build(bonsai_ctx *ctx, const double *pos, const double *mass, int64_t n
  * Errors: ESTATE (no tree), EINVAL (theta <= 0, eps < 0), EOVERFLOW, ECUDA. */
 int tree_forces(bonsai_ctx *ctx, float theta, float eps, float *acc, float *pot);
 
+/* tree_forces_fp64 -- the all-FP64 variant of tree_forces (the paper runs
+ * FP32 only; this is the reference of a precision study): the same walk and
+ * interaction lists (the opening test stays the FP32 test), with every p-p
+ * and p-c term of Eq. 1-2 evaluated in FP64 on the FP64 multipoles and
+ * positions relative to the FP64 group centre.  Much slower than
+ * tree_forces (FP64 pipe).  acc: device float64 [3][n] or NULL; pot:
+ * device float64 [n] or NULL (caller order).  The FP32 results of the last
+ * tree_forces are left untouched.  Errors: as tree_forces. */
+int tree_forces_fp64(bonsai_ctx *ctx, float theta, float eps, double *acc, double *pot);
+
 /* Set the velocities of the particles of the last tree_build.
  * vel: device [3][n] float64, caller order.  Errors: ESTATE, EINVAL. */
 int tree_set_velocities(bonsai_ctx *ctx, const double *vel);
@@ -214,6 +224,12 @@ int tree_debug_multipoles(bonsai_ctx *ctx, double *M, double *com, double *Q);
  * int32 [n_groups]); any may be NULL. */
 int tree_debug_groups(bonsai_ctx *ctx, uint32_t *first, uint32_t *count, int32_t *npp,
                       int32_t *npc);
+
+/* Limit the walk's per-warp frontier to cap entries (0 restores the full
+ * capacity of 16384).  For tests of the overflow path: a walk that needs
+ * more sets the device status word, and tree_forces / tree_forces_vjp
+ * return BONSAI_EOVERFLOW; the context stays usable.  Errors: EINVAL. */
+int tree_debug_set_frontier_capacity(bonsai_ctx *ctx, int cap);
 
 /* Name of a status code. */
 const char *bonsai_strerror(int code);

@@ -32,6 +32,7 @@ EXPORTED = (
     "bonsai_diagnostics", "tree_get_stats", "tree_solve_host", "tree_debug_cube",
     "tree_debug_keys", "tree_debug_nodes", "tree_debug_multipoles", "tree_debug_groups",
     "bonsai_strerror", "bonsai_sfc_order_noalloc", "tree_forces_vjp", "tree_run", "tree_run_vjp",
+    "tree_debug_set_frontier_capacity", "tree_forces_fp64",
 )
 
 BONSAI_NOALLOC_MAX_N = 1 << 20
@@ -96,6 +97,8 @@ def load(path: str | None = None):
             "tree_forces_vjp": (i32, [P, P, P, P, P]),
             "tree_run": (i32, [P, i32, f64, i32]),
             "tree_run_vjp": (i32, [P, P, P, P, P, P, P]),
+            "tree_debug_set_frontier_capacity": (i32, [P, i32]),
+            "tree_forces_fp64": (i32, [P, f32, f32, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -187,6 +190,12 @@ def tree_forces(ctx, theta: float, eps: float, acc=None, pot=None) -> None:
                               _ptr(pot, torch.float32, None, "pot")), "tree_forces")
 
 
+def tree_forces_fp64(ctx, theta: float, eps: float, acc=None, pot=None) -> None:
+    import torch
+    _check(load().tree_forces_fp64(ctx, float(theta), float(eps), _ptr(acc, torch.float64, None, "acc"),
+                                   _ptr(pot, torch.float64, None, "pot")), "tree_forces_fp64")
+
+
 def tree_set_velocities(ctx, vel) -> None:
     import torch
     _check(load().tree_set_velocities(ctx, _ptr(vel, torch.float64, None, "vel")), "tree_set_velocities")
@@ -245,6 +254,10 @@ def tree_run_vjp(ctx, xbar, vbar, mbar, xbar0, vbar0, mbar0) -> None:
     f64 = torch.float64
     _check(load().tree_run_vjp(ctx, _ptr(xbar, f64), _ptr(vbar, f64), _ptr(mbar, f64),
                                _ptr(xbar0, f64), _ptr(vbar0, f64), _ptr(mbar0, f64)), "tree_run_vjp")
+
+
+def tree_debug_set_frontier_capacity(ctx, cap: int) -> None:
+    _check(load().tree_debug_set_frontier_capacity(ctx, int(cap)), "tree_debug_set_frontier_capacity")
 
 
 def tree_debug_cube(ctx):

@@ -245,6 +245,31 @@ int tree_forces(bonsai_ctx *c, float theta, float eps, float *acc, float *pot) {
     return forces_internal(c, theta, eps, acc, pot);
 }
 
+int tree_forces_fp64(bonsai_ctx *c, float theta, float eps, double *acc, double *pot) {
+    if (!c) return BONSAI_EINVAL;
+    if (!c->have_tree) return BONSAI_ESTATE;
+    if (!(theta > 0.0f) || !(eps >= 0.0f) || !isfinite(theta) || !isfinite(eps))
+        return BONSAI_EINVAL;
+    if (c->walk_warps == 0) {
+        c->walk_warps = walk_resident_warps(c);
+        if (ensure(c->frontier, walk_frontier_elems(c->walk_warps))) return BONSAI_ENOMEM;
+    }
+    BGB_CUDA(cudaMemsetAsync(&c->dsc->n_pp, 0, 2 * sizeof(uint64_t), c->stream));
+    BGB_CUDA(cudaMemsetAsync(&c->dsc->status, 0, 3 * sizeof(int32_t), c->stream));
+    if (c->packed_theta != theta) {
+        launch_cell_pack(c, theta);
+        c->packed_theta = theta;
+    }
+    int rc = walk_force_fp64(c, eps, acc, pot);
+    if (rc) return rc;
+    if ((rc = read_scalars(c))) return rc;
+    c->stats.n_pp = c->hsc->n_pp;
+    c->stats.n_pc = c->hsc->n_pc;
+    c->stats.flops = 23.0 * (double)c->hsc->n_pp + 65.0 * (double)c->hsc->n_pc;
+    if (c->hsc->status & ST_OVERFLOW) return BONSAI_EOVERFLOW;
+    return BONSAI_OK;
+}
+
 int tree_set_velocities(bonsai_ctx *c, const double *vel) {
     if (!c || !vel) return BONSAI_EINVAL;
     if (!c->have_tree) return BONSAI_ESTATE;
@@ -502,6 +527,12 @@ int tree_debug_groups(bonsai_ctx *c, uint32_t *first, uint32_t *count, int32_t *
     if (npp) BGB_CUDA(cudaMemcpyAsync(npp, c->grp_npp.p, ng * 4, cudaMemcpyDeviceToDevice, c->stream));
     if (npc) BGB_CUDA(cudaMemcpyAsync(npc, c->grp_npc.p, ng * 4, cudaMemcpyDeviceToDevice, c->stream));
     BGB_CUDA(cudaStreamSynchronize(c->stream));
+    return BONSAI_OK;
+}
+
+int tree_debug_set_frontier_capacity(bonsai_ctx *c, int cap) {
+    if (!c || cap < 0) return BONSAI_EINVAL;
+    c->walk_fcap = cap;
     return BONSAI_OK;
 }
 

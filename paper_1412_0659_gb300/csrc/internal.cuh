@@ -111,6 +111,7 @@ struct bonsai_ctx {
     // walk frontier scratch (per resident warp)
     bgb::DBuf<uint32_t> frontier;
     int walk_warps = 0;
+    int walk_fcap = 0;  // 0: the full per-warp frontier; smaller values only for tests
 
     // device scalars + host mirror
     bgb::DevScalars *dsc = nullptr;
@@ -167,6 +168,7 @@ void launch_body_pack(bonsai_ctx *c);
 void launch_cell_pack(bonsai_ctx *c, float theta);
 // walk.cu
 int walk_force(bonsai_ctx *c, float theta, float eps, float *acc_caller, float *pot_caller);
+int walk_force_fp64(bonsai_ctx *c, float eps, double *acc, double *pot);
 // integrate.cu
 void launch_kick(bonsai_ctx *c, double h);
 void launch_drift(bonsai_ctx *c, double dt);

@@ -73,7 +73,14 @@ struct WalkArgs {
     float4 *part_adj;  // [n]: {gx, gy, gz, gm}
     int64_t nn;
     uint32_t *frontier;
+    uint32_t fcap;  // usable entries of each frontier buffer (<= FCAP)
     DevScalars *sc;
+    // all-FP64 evaluation
+    const double *pos64, *mass64;  // sorted [3][n], [n]
+    const double *gcentre;         // [3][ngroups]
+    const double *ndM, *ndcom, *ndQ;  // [nn], [3][nn], [6][nn]
+    double *acc64, *pot64;         // caller order [3][n], [n] or null
+    double G64, eps2_64;
 };
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
@@ -176,14 +183,37 @@ __device__ __forceinline__ float sum_copies(float v, int lane, int T2, int S) {
 // theta < 1/sqrt(3) a cell containing the group is always opened (the
 // distance from its com to the group box is at most sqrt(3) l < l/theta),
 // and the self term is removed after the loop.
+// Ring appends of the FP32 policies: a cell's com relative to the group
+// centre is (com_hi - c_hi) + (com_lo - c_lo), each difference rounded once,
+// so the FP32 record is accurate relative to the separation.
+struct Fp32Rings {
+    __device__ __forceinline__ void append_cell(const WalkArgs &A, WarpLists &L, uint32_t s,
+                                                uint32_t node, float4 m, float4 box, float4 clo,
+                                                uint32_t) {
+        const float4 a = A.ca[node];
+        L.ca[s] = make_float4((m.x - box.x) + (a.x - clo.x), (m.y - box.y) + (a.y - clo.y),
+                              (m.z - box.z) + (a.z - clo.z), a.w);
+        L.cb[s] = A.cb[node];
+        L.cc[s] = A.cc[node];
+        L.cid[s] = (int)node;
+    }
+    __device__ __forceinline__ void append_particle(const WalkArgs &A, WarpLists &L, uint32_t s,
+                                                    uint32_t j, float4 box, float4 clo, uint32_t) {
+        const float4 h = A.body_hi[j], l = A.body_lo[j];
+        L.pp[s] = make_float4((h.x - box.x) + (l.x - clo.x), (h.y - box.y) + (l.y - clo.y),
+                              (h.z - box.z) + (l.z - clo.z), h.w);
+        L.pid[s] = (int)j;
+    }
+};
+
 template <bool MASK>
-struct ForwardPolicy {
+struct ForwardPolicy : Fp32Rings {
     int T2, S, cp, tl, j0;
     Targets t;
     float self[2];
     float eps2;
 
-    __device__ __forceinline__ void begin(const WalkArgs &A, WarpTargets *, uint32_t gf,
+    __device__ __forceinline__ void begin(const WalkArgs &A, WarpTargets *, uint32_t, uint32_t gf,
                                           uint32_t gc, float4 box, float4 clo, int lane) {
         eps2 = A.eps2;
         T2 = (int)((gc + 1u) >> 1);
@@ -358,7 +388,7 @@ struct __align__(16) WarpAdjoint {
 // instructions than a shuffle reduction per target.  Every lane is busy
 // whatever the group size.  Source and cell adjoints go to global memory with
 // one vector atomic per 4 values per flush; target gradients once per group.
-struct AdjointPolicy {
+struct AdjointPolicy : Fp32Rings {
     WarpTargets *T;
     WarpAdjoint *W;
     int gc;
@@ -367,8 +397,9 @@ struct AdjointPolicy {
     float4 *part_adj;
     int64_t nn;
 
-    __device__ __forceinline__ void begin(const WalkArgs &A, WarpTargets *tgt, uint32_t gf,
-                                          uint32_t gcount, float4 box, float4 clo, int lane) {
+    __device__ __forceinline__ void begin(const WalkArgs &A, WarpTargets *tgt, uint32_t,
+                                          uint32_t gf, uint32_t gcount, float4 box, float4 clo,
+                                          int lane) {
         T = tgt;
         gc = (int)gcount;
         eps2 = A.eps2;
@@ -538,16 +569,147 @@ __device__ __forceinline__ void do_flush_pp(AdjointPolicy &pol, const WarpLists 
 }
 
 // ---------------------------------------------------------------------------
+// All-FP64 evaluation: the same walk and lists (the opening test is the same
+// FP32 test), with the p-p and p-c terms of Eq. 1-2 evaluated in FP64 on the
+// FP64 multipoles and positions, relative to the FP64 group centre.  The
+// paper runs FP32 only; this variant is the reference of the precision
+// study and is slow on purpose (FP64 pipe).
+// ---------------------------------------------------------------------------
+
+struct __align__(16) WarpLists64 {
+    double cx[RING], cy[RING], cz[RING], cm[RING];
+    double q[6][RING];  // xx yy zz xy xz yz
+    double px[RING], py[RING], pz[RING], pm[RING];
+    int pid[RING];
+};
+
+__device__ __forceinline__ void pc_one64(double rx, double ry, double rz, double M, double qxx,
+                                         double qyy, double qzz, double qxy, double qxz,
+                                         double qyz, double eps2, double &ax, double &ay,
+                                         double &az, double &ph) {
+    const double s2 = fma(rz, rz, fma(ry, ry, fma(rx, rx, eps2)));
+    const double u = 1.0 / sqrt(s2);
+    const double w = u * u, u3 = u * w, u5 = u3 * w, u7 = u5 * w;
+    const double tr = qxx + qyy + qzz;
+    const double qx = qxx * rx + qxy * ry + qxz * rz;
+    const double qy = qxy * rx + qyy * ry + qyz * rz;
+    const double qz = qxz * rx + qyz * ry + qzz * rz;
+    const double rQr = rx * qx + ry * qy + rz * qz;
+    ph += -M * u + 0.5 * tr * u3 - 1.5 * rQr * u5;
+    const double A = M * u3 - 1.5 * tr * u5 + 7.5 * rQr * u7;
+    const double B = -3.0 * u5;
+    ax += A * rx + B * qx;
+    ay += A * ry + B * qy;
+    az += A * rz + B * qz;
+}
+
+struct Fp64Policy {
+    int gc;
+    bool two;
+    double eps2, cx, cy, cz;
+    double tx[2], ty[2], tz[2], ax[2], ay[2], az[2], ph[2];
+    int id[2];
+
+    __device__ __forceinline__ void begin(const WalkArgs &A, WarpTargets *, uint32_t g,
+                                          uint32_t gf, uint32_t gcount, float4, float4, int lane) {
+        gc = (int)gcount;
+        two = gc > 32;
+        eps2 = A.eps2_64;
+        cx = A.gcentre[g];
+        cy = A.gcentre[A.ngroups + g];
+        cz = A.gcentre[2 * A.ngroups + g];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int li = lane + 32 * k;
+            const bool v = li < gc;
+            const int64_t i = gf + (v ? li : 0);
+            tx[k] = A.pos64[i] - cx;
+            ty[k] = A.pos64[A.n + i] - cy;
+            tz[k] = A.pos64[2 * A.n + i] - cz;
+            id[k] = v ? (int)i : -1;
+            ax[k] = ay[k] = az[k] = ph[k] = 0.0;
+        }
+    }
+    __device__ __forceinline__ void append_cell(const WalkArgs &A, WarpLists64 &L, uint32_t s,
+                                                uint32_t node, float4, float4, float4, uint32_t) {
+        const int64_t nn = A.nn;
+        L.cx[s] = A.ndcom[node] - cx;
+        L.cy[s] = A.ndcom[nn + node] - cy;
+        L.cz[s] = A.ndcom[2 * nn + node] - cz;
+        L.cm[s] = A.ndM[node];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) L.q[k][s] = A.ndQ[k * nn + node];
+    }
+    __device__ __forceinline__ void append_particle(const WalkArgs &A, WarpLists64 &L, uint32_t s,
+                                                    uint32_t j, float4, float4, uint32_t) {
+        L.px[s] = A.pos64[j] - cx;
+        L.py[s] = A.pos64[A.n + j] - cy;
+        L.pz[s] = A.pos64[2 * A.n + j] - cz;
+        L.pm[s] = A.mass64[j];
+        L.pid[s] = (int)j;
+    }
+    __device__ __forceinline__ void flush_pc(const WarpLists64 &L, int hb, int cnt) {
+        for (int j = hb; j < hb + cnt; ++j) {
+            const int nk = two ? 2 : 1;
+            for (int k = 0; k < nk; ++k)
+                pc_one64(L.cx[j] - tx[k], L.cy[j] - ty[k], L.cz[j] - tz[k], L.cm[j], L.q[0][j],
+                         L.q[1][j], L.q[2][j], L.q[3][j], L.q[4][j], L.q[5][j], eps2, ax[k], ay[k],
+                         az[k], ph[k]);
+        }
+    }
+    __device__ __forceinline__ void flush_pp(const WarpLists64 &L, int hb, int cnt) {
+        for (int j = hb; j < hb + cnt; ++j) {
+            const int nk = two ? 2 : 1;
+            for (int k = 0; k < nk; ++k) {
+                if (L.pid[j] == id[k]) continue;  // the self pair
+                const double rx = L.px[j] - tx[k], ry = L.py[j] - ty[k], rz = L.pz[j] - tz[k];
+                const double s2 = fma(rz, rz, fma(ry, ry, fma(rx, rx, eps2)));
+                const double u = 1.0 / sqrt(s2);
+                const double mu = L.pm[j] * u, mu3 = mu * u * u;
+                ph[k] -= mu;
+                ax[k] += mu3 * rx;
+                ay[k] += mu3 * ry;
+                az[k] += mu3 * rz;
+            }
+        }
+    }
+    __device__ __forceinline__ void finish(const WalkArgs &A, uint32_t gf, uint32_t, int lane) {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int li = lane + 32 * k;
+            if (li < gc) {
+                const uint32_t o = A.id[gf + li];
+                if (A.acc64) {
+                    A.acc64[o] = A.G64 * ax[k];
+                    A.acc64[A.n + o] = A.G64 * ay[k];
+                    A.acc64[2 * A.n + o] = A.G64 * az[k];
+                }
+                if (A.pot64) A.pot64[o] = A.G64 * ph[k];
+            }
+        }
+    }
+};
+
+__device__ __forceinline__ void do_flush_pc(Fp64Policy &pol, const WarpLists64 &L, int hb, int cnt,
+                                            int) {
+    pol.flush_pc(L, hb, cnt);
+}
+__device__ __forceinline__ void do_flush_pp(Fp64Policy &pol, const WarpLists64 &L, int hb, int cnt,
+                                            int) {
+    pol.flush_pp(L, hb, cnt);
+}
+
+// ---------------------------------------------------------------------------
 // The traversal
 // ---------------------------------------------------------------------------
 
-template <class P>
-__device__ __forceinline__ void walk_group(const WalkArgs &A, WarpLists &L, WarpTargets *tgt, P &pol,
+template <class P, class LT>
+__device__ __forceinline__ void walk_group(const WalkArgs &A, LT &L, WarpTargets *tgt, P &pol,
                                            uint32_t g, uint32_t *fa, uint32_t *fb, int lane,
                                            uint32_t lt) {
     const uint32_t gf = A.gfirst[g], gc = A.gcount[g];
     const float4 box = A.gbox[g], half = A.ghalf[g], clo = A.glo[g];
-    pol.begin(A, tgt, gf, gc, box, clo, lane);
+    pol.begin(A, tgt, g, gf, gc, box, clo, lane);
 
     uint32_t pc_head = 0, pc_tail = 0, pp_head = 0, pp_tail = 0;
     uint32_t npc = 0, npp = 0;
@@ -578,17 +740,9 @@ __device__ __forceinline__ void walk_group(const WalkArgs &A, WarpLists &L, Warp
 
             // accepted cells -> p-c ring
             const uint32_t am = __ballot_sync(0xffffffffu, accept);
-            if (accept) {
-                const uint32_t s = (pc_tail + __popc(am & lt)) & (RING - 1);
-                const float4 a = A.ca[node];
-                const float4 rel = make_float4((m.x - box.x) + (a.x - clo.x),
-                                               (m.y - box.y) + (a.y - clo.y),
-                                               (m.z - box.z) + (a.z - clo.z), a.w);
-                L.ca[s] = rel;
-                L.cb[s] = A.cb[node];
-                L.cc[s] = A.cc[node];
-                L.cid[s] = (int)node;
-            }
+            if (accept)
+                pol.append_cell(A, L, (pc_tail + __popc(am & lt)) & (RING - 1), node, m, box, clo,
+                                g);
             pc_tail += __popc(am);
             npc += __popc(am);
 
@@ -610,7 +764,7 @@ __device__ __forceinline__ void walk_group(const WalkArgs &A, WarpLists &L, Warp
                 ltot = tot >> 9;
             }
             // opened internal cells -> next frontier
-            if (nnext + ntot > (uint32_t)FCAP) {
+            if (nnext + ntot > A.fcap) {
                 overflow = true;
             } else {
                 for (uint32_t k = 0; k < nch; ++k) nxt[nnext + noff + k] = tp.x + k;
@@ -630,15 +784,9 @@ __device__ __forceinline__ void walk_group(const WalkArgs &A, WarpLists &L, Warp
                 }
                 const uint32_t sfirst = __shfl_sync(0xffffffffu, tp.x, src);
                 const uint32_t soff = __shfl_sync(0xffffffffu, loff, src);
-                if (k < ltot) {
-                    const uint32_t j = sfirst + (k - soff);
-                    const float4 h = A.body_hi[j], l = A.body_lo[j];
-                    const uint32_t s = (pp_tail + lane) & (RING - 1);
-                    L.pp[s] = make_float4((h.x - box.x) + (l.x - clo.x),
-                                          (h.y - box.y) + (l.y - clo.y),
-                                          (h.z - box.z) + (l.z - clo.z), h.w);
-                    L.pid[s] = (int)j;
-                }
+                if (k < ltot)
+                    pol.append_particle(A, L, (pp_tail + lane) & (RING - 1), sfirst + (k - soff),
+                                        box, clo, g);
                 pp_tail += min(32u, ltot - r);
                 __syncwarp();
                 if (pp_tail - pp_head >= 32u) {
@@ -722,6 +870,24 @@ __global__ void __launch_bounds__(WALK_WARPS * 32, 5) k_walk_adjoint(const WalkA
     }
 }
 
+__global__ void __launch_bounds__(WALK_WARPS * 32) k_walk_fp64(const WalkArgs A) {
+    __shared__ WarpLists64 lists[WALK_WARPS];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const uint32_t lt = lanemask_lt();
+    const int64_t gw = (int64_t)blockIdx.x * WALK_WARPS + wib;
+    uint32_t *fa = A.frontier + gw * 2 * FCAP;
+    uint32_t *fb = fa + FCAP;
+    while (true) {
+        uint32_t g = 0;
+        if (lane == 0) g = atomicAdd(&A.sc->group_counter, 1u);
+        g = __shfl_sync(0xffffffffu, g, 0);
+        if (g >= A.ngroups) break;
+        Fp64Policy pol;
+        walk_group(A, lists[wib], nullptr, pol, g, fa, fb, lane, lt);
+    }
+}
+
 void fill_args(bonsai_ctx *c, float eps, WalkArgs &a) {
     a.mac = c->cell_mac.p;
     a.topo = c->cell_topo.p;
@@ -752,7 +918,18 @@ void fill_args(bonsai_ctx *c, float eps, WalkArgs &a) {
     a.part_adj = nullptr;
     a.nn = c->n_nodes;
     a.frontier = c->frontier.p;
+    a.fcap = (c->walk_fcap > 0 && c->walk_fcap < FCAP) ? (uint32_t)c->walk_fcap : (uint32_t)FCAP;
     a.sc = c->dsc;
+    a.pos64 = c->pos.p;
+    a.mass64 = c->mass.p;
+    a.gcentre = c->grp_centre.p;
+    a.ndM = c->nd_M.p;
+    a.ndcom = c->nd_com.p;
+    a.ndQ = c->nd_Q.p;
+    a.acc64 = nullptr;
+    a.pot64 = nullptr;
+    a.G64 = c->prm.G;
+    a.eps2_64 = (double)eps * (double)eps;
 }
 
 }  // namespace
@@ -817,6 +994,19 @@ int walk_adjoint(bonsai_ctx *c, float eps, const float *lam, const float *mu, fl
     a.cell_adj = cell_adj;
     a.part_adj = part_adj;
     k_walk_adjoint<<<launch_blocks((const void *)k_walk_adjoint, c), WALK_WARPS * 32, 0, c->stream>>>(a);
+    c->launches += 1;
+    return cudaPeekAtLastError() == cudaSuccess ? BONSAI_OK : BONSAI_ECUDA;
+}
+
+// The all-FP64 evaluation of the current tree and lists; outputs in caller order.
+int walk_force_fp64(bonsai_ctx *c, float eps, double *acc, double *pot) {
+    WalkArgs a;
+    fill_args(c, eps, a);
+    a.acc = nullptr;
+    a.pot = nullptr;
+    a.acc64 = acc;
+    a.pot64 = pot;
+    k_walk_fp64<<<launch_blocks((const void *)k_walk_fp64, c), WALK_WARPS * 32, 0, c->stream>>>(a);
     c->launches += 1;
     return cudaPeekAtLastError() == cudaSuccess ? BONSAI_OK : BONSAI_ECUDA;
 }

@@ -59,6 +59,16 @@ class TreeGravity:
         capi.tree_forces(self.ctx, theta, eps, acc, pot)
         return acc, pot
 
+    def forces_fp64(self, theta: float | None = None, eps: float | None = None):
+        """All-FP64 evaluation of the same lists; (3, N) / (N,) float64."""
+        theta = self.theta if theta is None else theta
+        eps = self.eps if eps is None else eps
+        dev = torch.device("cuda", torch.cuda.current_device())
+        acc = torch.empty((3, self.n), dtype=torch.float64, device=dev)
+        pot = torch.empty(self.n, dtype=torch.float64, device=dev)
+        capi.tree_forces_fp64(self.ctx, theta, eps, acc, pot)
+        return acc, pot
+
     def set_velocities(self, vel: torch.Tensor):
         capi.tree_set_velocities(self.ctx, vel)
 

@@ -179,3 +179,52 @@ def test_host_buffer_entry_matches_device_path():
     assert np.array_equal(pot.numpy(), ref["pot"].astype(np.float32))
     g.close()
     ref["g"].close()
+
+
+def test_frontier_overflow_is_reported_and_recoverable():
+    """A walk whose frontier exceeds the (test-reduced) capacity stops adding
+    cells, sets the device status word and returns BONSAI_EOVERFLOW from the
+    forward and the adjoint; the context is usable afterwards."""
+    import torch
+
+    from gpu_helpers import DEV, assert_force_tolerance, oracle_tree
+    from paper_1412_0659_gb300 import TreeGravity, capi
+    m = workloads.plummer(6000, seed=91)
+    g = TreeGravity(theta=0.4, eps=0.01)
+    g.build(torch.from_numpy(m.pos).to(DEV), torch.from_numpy(m.mass).to(DEV))
+    capi.tree_debug_set_frontier_capacity(g.ctx, 8)
+    with pytest.raises(capi.BonsaiError) as e:
+        g.forces()
+    assert e.value.code == capi.BONSAI_EOVERFLOW
+    capi.tree_debug_set_frontier_capacity(g.ctx, 0)
+    acc, pot = g.forces()
+    acc_o, pot_o, _ = oracle_tree(m.pos, m.mass).forces(0.4, 0.01)
+    assert_force_tolerance(acc.double().cpu().numpy(), pot.double().cpu().numpy(), acc_o, pot_o)
+    capi.tree_debug_set_frontier_capacity(g.ctx, 8)
+    with pytest.raises(capi.BonsaiError) as e:
+        g.forces_vjp(torch.ones((3, m.n), dtype=torch.float32, device=DEV))
+    assert e.value.code == capi.BONSAI_EOVERFLOW
+    g.close()
+
+
+@pytest.mark.parametrize("name", ["plummer20011", "milkyway30000", "coincident1500"])
+def test_fp64_variant_matches_oracle_to_round_off(name):
+    """The all-FP64 evaluation of the same lists equals the FP64 oracle tree
+    to summation-order round-off (1e-12 relative), with identical counts."""
+    import torch
+
+    from gpu_helpers import DEV, oracle_tree
+    from paper_1412_0659_gb300 import TreeGravity
+    pos, mass, eps = CASES[name]
+    G = 4.498502151469554e-12 if name.startswith("milky") else 1.0
+    g = TreeGravity(G=G, theta=0.4, eps=eps)
+    g.build(torch.from_numpy(pos).to(DEV), torch.from_numpy(mass).to(DEV))
+    acc, pot = g.forces_fp64(0.4, eps)
+    st = g.stats()
+    g.close()
+    # the C ABI takes eps as float: give the oracle the same FP32-rounded value
+    acc_o, pot_o, counts = oracle_tree(pos, mass).forces(0.4, float(np.float32(eps)), G)
+    assert (st["n_pp"], st["n_pc"]) == counts
+    e = np.linalg.norm(acc.cpu().numpy() - acc_o, axis=0) / np.linalg.norm(acc_o, axis=0)
+    pe = np.abs(pot.cpu().numpy() - pot_o) / np.abs(pot_o)
+    assert e.max() <= 1e-12 and pe.max() <= 1e-12, (e.max(), pe.max())
