@@ -107,6 +107,21 @@ def _dist():
     return rank, world, local
 
 
+def aggregate(t_ms: float, work: float, world: int, device=None):
+    """Whole-job figures of a timed region: the maximum wall time over ranks
+    and the sum of the work (flops) done by all ranks.  Every rank calls it;
+    with one rank it returns its inputs."""
+    if world <= 1:
+        return t_ms, work
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([t_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    ww = torch.tensor([work], dtype=torch.float64, device=device)
+    dist.all_reduce(ww)
+    return float(tt.item()), float(ww.item())
+
+
 def _workload(name: str, rank: int):
     import workloads
     if name == "milky-way-2^23":
@@ -180,15 +195,7 @@ def run_ours(args):
         dist.barrier()
     t_ms = e0.elapsed_time(e1)
     launches = g.stats()["launches"] - launches0
-    t_max = t_ms
-    tot_flops = flops
-    if world > 1:
-        tt = torch.tensor([t_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-        ff = torch.tensor([flops], dtype=torch.float64, device=dev)
-        dist.all_reduce(ff)
-        tot_flops = float(ff.item())
+    t_max, tot_flops = aggregate(t_ms, flops, world, dev)
     value = tot_flops / (t_max * 1e-3) / 1e12
     ms_per_step = t_max / args.steps
 
@@ -234,13 +241,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     e_s = time.perf_counter() - t0
     ge.close()
-    if world > 1:
-        tt = torch.tensor([e_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e_s = float(tt.item())
-        ff = torch.tensor([e_flops], dtype=torch.float64, device=dev)
-        dist.all_reduce(ff)
-        e_flops = float(ff.item())
+    e_s, e_flops = aggregate(e_s, e_flops, world, dev)
     e2e = {"value": e_flops / e_s / 1e12, "unit": UNIT,
            "h2d_bytes_per_step": int(pin_pos.numel() * 8 + pin_mass.numel() * 8),
            "d2h_bytes_per_step": int(pin_acc.numel() * 4 + pin_pot.numel() * 4),
