@@ -42,10 +42,15 @@ struct __align__(16) WarpLists {
     int cid[RING];    // node index of the cell
 };
 
-// targets of one group for the adjoint policy
+// Targets of one group for the adjoint policy, two per record (targets 2p
+// and 2p+1 in record p), so that one 16-byte shared load yields two packed
+// operands.  Slots beyond the group copy target 0 with zero cotangents.
 struct __align__(16) WarpTargets {
-    float4 pos[NCRIT];  // {dx, dy, dz, sorted index as bits}
-    float4 lam[NCRIT];  // {lambda_x, lambda_y, lambda_z, mu}
+    float4 nxy[NCRIT / 2];  // {-x, -x', -y, -y'}: minus the group-relative position
+    float4 nzi[NCRIT / 2];  // {-z, -z', sorted index (bits), sorted index' (bits)}
+    float4 lxy[NCRIT / 2];  // {lambda_x, lambda_x', lambda_y, lambda_y'}
+    float4 lzm[NCRIT / 2];  // {lambda_z, lambda_z', mu, mu'}
+    float4 mus[NCRIT / 2];  // {-mu, -mu', mu/2, mu'/2}
 };
 
 struct WalkArgs {
@@ -294,7 +299,48 @@ struct ForwardPolicy : Fp32Rings {
 // Adjoint evaluation
 // ---------------------------------------------------------------------------
 
-// Gradient of lambda.a + mu phi for one cell on one target (without G),
+// Two FP32 values in one 64-bit register pair, operated on by the packed
+// FP32 instructions of sm_100 and later (add/mul/fma.rn.f32x2): one issue
+// slot performs two IEEE round-to-nearest operations, each bit-identical to
+// its scalar counterpart.  The adjoint evaluates two targets per operation.
+typedef unsigned long long f32x2;
+
+__device__ __forceinline__ f32x2 p2(float lo, float hi) {
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void u2(f32x2 v, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
+    f32x2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f32x2 dup2(float v) { return p2(v, v); }
+__device__ __forceinline__ ulonglong2 lds2(const float4 &v) {
+    return *reinterpret_cast<const ulonglong2 *>(&v);
+}
+
+// One list entry (in both halves) and two targets.
+struct TargetPair {
+    f32x2 nx, ny, nz;  // minus the target positions
+    f32x2 lx, ly, lz, mu, nmu, hmu;  // lambda, mu, -mu, mu/2
+    int2 id;           // sorted indices
+};
+
+// Gradient of lambda.a + mu phi for one cell on two targets (without G),
 // with respect to r = com - x_i (g_r), the cell mass (gM) and the symmetric
 // quadrupole Q.  With u = 1/s, w = u^2, Q' = -3Q (as stored), rq = r.Q'r,
 // lq = lambda.Q'r, lr = lambda.r:
@@ -305,70 +351,89 @@ struct ForwardPolicy : Fp32Rings {
 //   gM    = lr u^3 - mu u
 //   gQ    = P0 I + (r v^T + v r^T),  P0 = mu u^3/2 - 3/2 u^5 lr,
 //           v = (15/4 u^7 lr - 3/4 mu u^5) r - 3/2 u^5 lambda.
-// Returns P0 and v2 = 2v; the caller accumulates gQ from them.
-// Per-cell constants of pc_vjp, computed once per flush: M3 = -3M, cw5 = -5 c.w.
-__device__ __forceinline__ void pc_vjp(const float4 a, const float4 b, const float4 c, float M3,
-                                       float cw5, float4 tp, float4 tl, float eps2, float &gx,
-                                       float &gy, float &gz, float &gM, float &P0, float &vx,
-                                       float &vy, float &vz, float &rx, float &ry, float &rz) {
-    rx = a.x - tp.x;
-    ry = a.y - tp.y;
-    rz = a.z - tp.z;
-    float s2 = fmaf(rx, rx, eps2);
-    s2 = fmaf(ry, ry, s2);
-    s2 = fmaf(rz, rz, s2);
-    const float u = rsqrtf(s2);
-    const float w = u * u;
-    const float u3 = u * w, u5 = u3 * w, u7 = u5 * w;
-    const float qx = fmaf(b.x, rx, fmaf(b.w, ry, c.x * rz));  // Q'r
-    const float qy = fmaf(b.w, rx, fmaf(b.y, ry, c.y * rz));
-    const float qz = fmaf(c.x, rx, fmaf(c.y, ry, b.z * rz));
-    const float px = fmaf(b.x, tl.x, fmaf(b.w, tl.y, c.x * tl.z));  // Q'lambda
-    const float py = fmaf(b.w, tl.x, fmaf(b.y, tl.y, c.y * tl.z));
-    const float pz = fmaf(c.x, tl.x, fmaf(c.y, tl.y, b.z * tl.z));
-    const float rq = fmaf(rx, qx, fmaf(ry, qy, rz * qz));
-    const float lq = fmaf(tl.x, qx, fmaf(tl.y, qy, tl.z * qz));
-    const float lr = fmaf(tl.x, rx, fmaf(tl.y, ry, tl.z * rz));
-    const float mu = tl.w;
+// Returns P0 and v2 = 2v; the caller accumulates gQ from them.  The cell
+// record (both halves equal): a = {com, M}, b, c as stored, M3 = -3M,
+// cw5 = -5 c.w.
+struct CellDup {
+    f32x2 x, y, z, M, bx, by, bz, bw, cx, cy, cw, M3, cw5;
+};
+
+__device__ __forceinline__ void pc_vjp2(const CellDup &C, const TargetPair &T, f32x2 eps2,
+                                        f32x2 &gx, f32x2 &gy, f32x2 &gz, f32x2 &gM, f32x2 &P0,
+                                        f32x2 &vx, f32x2 &vy, f32x2 &vz, f32x2 &rx, f32x2 &ry,
+                                        f32x2 &rz) {
+    const f32x2 k_m25 = dup2(-2.5f), k_175 = dup2(17.5f), k_m5 = dup2(-5.0f), k_m15 = dup2(-1.5f);
+    rx = add2(C.x, T.nx);
+    ry = add2(C.y, T.ny);
+    rz = add2(C.z, T.nz);
+    f32x2 s2 = fma2(rx, rx, eps2);
+    s2 = fma2(ry, ry, s2);
+    s2 = fma2(rz, rz, s2);
+    float s0, s1;
+    u2(s2, s0, s1);
+    const f32x2 u = p2(rsqrtf(s0), rsqrtf(s1));
+    const f32x2 w = mul2(u, u);
+    const f32x2 u3 = mul2(u, w), u5 = mul2(u3, w), u7 = mul2(u5, w);
+    const f32x2 qx = fma2(C.bx, rx, fma2(C.bw, ry, mul2(C.cx, rz)));  // Q'r
+    const f32x2 qy = fma2(C.bw, rx, fma2(C.by, ry, mul2(C.cy, rz)));
+    const f32x2 qz = fma2(C.cx, rx, fma2(C.cy, ry, mul2(C.bz, rz)));
+    const f32x2 px = fma2(C.bx, T.lx, fma2(C.bw, T.ly, mul2(C.cx, T.lz)));  // Q'lambda
+    const f32x2 py = fma2(C.bw, T.lx, fma2(C.by, T.ly, mul2(C.cy, T.lz)));
+    const f32x2 pz = fma2(C.cx, T.lx, fma2(C.cy, T.ly, mul2(C.bz, T.lz)));
+    const f32x2 rq = fma2(rx, qx, fma2(ry, qy, mul2(rz, qz)));
+    const f32x2 lq = fma2(T.lx, qx, fma2(T.ly, qy, mul2(T.lz, qz)));
+    const f32x2 lr = fma2(T.lx, rx, fma2(T.ly, ry, mul2(T.lz, rz)));
     // alpha = u^3 (M + w (c.w - 5/2 rq w))
-    const float alpha = u3 * fmaf(w, fmaf(-2.5f * rq, w, c.w), a.w);
+    const f32x2 alpha = mul2(u3, fma2(w, fma2(mul2(k_m25, rq), w, C.cw), C.M));
     // beta = lr u^5 (-3M + w (-5 c.w + 35/2 rq w)) + mu alpha - 5 u^7 lq
-    const float m5u7 = -5.0f * u7;
-    const float K = u5 * fmaf(w, fmaf(17.5f * rq, w, cw5), M3);
-    const float beta = fmaf(lr, K, fmaf(mu, alpha, m5u7 * lq));
-    const float gam = fmaf(mu, u5, m5u7 * lr);
-    gx = fmaf(alpha, tl.x, fmaf(beta, rx, fmaf(gam, qx, u5 * px)));
-    gy = fmaf(alpha, tl.y, fmaf(beta, ry, fmaf(gam, qy, u5 * py)));
-    gz = fmaf(alpha, tl.z, fmaf(beta, rz, fmaf(gam, qz, u5 * pz)));
-    gM = fmaf(lr, u3, -mu * u);
-    const float m15u5 = -1.5f * u5;
-    P0 = fmaf(0.5f * mu, u3, m15u5 * lr);
-    const float p1 = fmaf(7.5f * u7, lr, m15u5 * mu);  // v2 = p1 r - 3 u^5 lambda
-    const float m3u5 = 2.0f * m15u5;
-    vx = fmaf(p1, rx, m3u5 * tl.x);
-    vy = fmaf(p1, ry, m3u5 * tl.y);
-    vz = fmaf(p1, rz, m3u5 * tl.z);
+    const f32x2 m5u7 = mul2(k_m5, u7);
+    const f32x2 K = mul2(u5, fma2(w, fma2(mul2(k_175, rq), w, C.cw5), C.M3));
+    const f32x2 beta = fma2(lr, K, fma2(T.mu, alpha, mul2(m5u7, lq)));
+    const f32x2 gam = fma2(T.mu, u5, mul2(m5u7, lr));
+    gx = fma2(alpha, T.lx, fma2(beta, rx, fma2(gam, qx, mul2(u5, px))));
+    gy = fma2(alpha, T.ly, fma2(beta, ry, fma2(gam, qy, mul2(u5, py))));
+    gz = fma2(alpha, T.lz, fma2(beta, rz, fma2(gam, qz, mul2(u5, pz))));
+    gM = fma2(lr, u3, mul2(T.nmu, u));
+    const f32x2 m15u5 = mul2(k_m15, u5);
+    P0 = fma2(T.hmu, u3, mul2(m15u5, lr));
+    const f32x2 p1 = fma2(mul2(k_m15, m5u7), lr, mul2(m15u5, T.mu));  // v2 = p1 r - 3 u^5 lambda
+    const f32x2 m3u5 = add2(m15u5, m15u5);
+    vx = fma2(p1, rx, mul2(m3u5, T.lx));
+    vy = fma2(p1, ry, mul2(m3u5, T.ly));
+    vz = fma2(p1, rz, mul2(m3u5, T.lz));
 }
 
-// Gradient of lambda.a + mu phi for one p-p source (without G):
+// Gradient of lambda.a + mu phi for one p-p source on two targets (without G):
 //   g_r = m u^3 (lambda + (mu - 3 w lr) r),  gm = lr u^3 - mu u;
 // zero for the self pair (u is set to 0, which also avoids r = 0 at eps = 0).
-__device__ __forceinline__ void pp_vjp(const float4 s, bool self, float4 tp, float4 tl, float eps2,
-                                       float &gx, float &gy, float &gz, float &gm) {
-    const float rx = s.x - tp.x, ry = s.y - tp.y, rz = s.z - tp.z;
-    float s2 = fmaf(rx, rx, eps2);
-    s2 = fmaf(ry, ry, s2);
-    s2 = fmaf(rz, rz, s2);
-    const float u = self ? 0.0f : rsqrtf(s2);
-    const float w = u * u;
-    const float u3 = u * w;
-    const float lr = fmaf(tl.x, rx, fmaf(tl.y, ry, tl.z * rz));
-    const float co = fmaf(-3.0f * w, lr, tl.w);
-    const float k = s.w * u3;
-    gx = k * fmaf(co, rx, tl.x);
-    gy = k * fmaf(co, ry, tl.y);
-    gz = k * fmaf(co, rz, tl.z);
-    gm = fmaf(lr, u3, -tl.w * u);
+__device__ __forceinline__ void pp_vjp2(f32x2 sx, f32x2 sy, f32x2 sz, f32x2 sm, int sid,
+                                        const TargetPair &T, f32x2 eps2, f32x2 &gx, f32x2 &gy,
+                                        f32x2 &gz, f32x2 &gm) {
+    const f32x2 rx = add2(sx, T.nx), ry = add2(sy, T.ny), rz = add2(sz, T.nz);
+    f32x2 s2 = fma2(rx, rx, eps2);
+    s2 = fma2(ry, ry, s2);
+    s2 = fma2(rz, rz, s2);
+    float s0, s1;
+    u2(s2, s0, s1);
+    const f32x2 u = p2(sid == T.id.x ? 0.0f : rsqrtf(s0), sid == T.id.y ? 0.0f : rsqrtf(s1));
+    const f32x2 w = mul2(u, u);
+    const f32x2 u3 = mul2(u, w);
+    const f32x2 lr = fma2(T.lx, rx, fma2(T.ly, ry, mul2(T.lz, rz)));
+    const f32x2 co = fma2(mul2(dup2(-3.0f), w), lr, T.mu);
+    const f32x2 k = mul2(sm, u3);
+    gx = mul2(k, fma2(co, rx, T.lx));
+    gy = mul2(k, fma2(co, ry, T.ly));
+    gz = mul2(k, fma2(co, rz, T.lz));
+    gm = fma2(lr, u3, mul2(T.nmu, u));
+}
+
+__device__ __forceinline__ TargetPair load_targets(const WarpTargets *T, int p) {
+    const ulonglong2 a = lds2(T->nxy[p]), b = lds2(T->nzi[p]), c = lds2(T->lxy[p]);
+    const ulonglong2 d = lds2(T->lzm[p]), e = lds2(T->mus[p]);
+    float i0, i1;
+    u2(b.y, i0, i1);
+    return TargetPair{a.x, a.y, b.x, c.x, c.y, d.x, d.y, e.x, e.y,
+                      make_int2(__float_as_int(i0), __float_as_int(i1))};
 }
 
 // Per-warp scratch of the adjoint: a 32 x 24 transpose buffer for the target
@@ -381,8 +446,9 @@ struct __align__(16) WarpAdjoint {
 };
 
 // The adjoint evaluates each ring flush with one list entry per lane and a
-// loop over the group's targets (broadcast from shared memory).  The cell or
-// source adjoint stays in the lane's registers.  The 3-vector target
+// loop over the group's targets (broadcast from shared memory), two targets
+// per packed FP32 operation.  The cell or source adjoint stays in the lane's
+// registers (packed: one half per target parity, added at the end).  The 3-vector target
 // gradients of 8 targets at a time are transposed through shared memory and
 // each column summed by one lane (24 lanes, 32 rows), which costs far fewer
 // instructions than a shuffle reduction per target.  Every lane is busy
@@ -406,15 +472,27 @@ struct AdjointPolicy : Fp32Rings {
         G = A.G;
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
+            // slots beyond the group: target 0's position and index, zero
+            // cotangents, so that every term they produce is exactly zero
             const int li = lane + 32 * k;
-            if (li < gc) {
-                const int64_t i = gf + li;
-                const float4 h = A.body_hi[i], l = A.body_lo[i];
-                T->pos[li] = make_float4((h.x - box.x) + (l.x - clo.x), (h.y - box.y) + (l.y - clo.y),
-                                         (h.z - box.z) + (l.z - clo.z), __int_as_float((int)i));
-                T->lam[li] = make_float4(A.lam[i], A.lam[A.n + i], A.lam[2 * A.n + i],
-                                         A.mu ? A.mu[i] : 0.0f);
-            }
+            const bool v = li < gc;
+            const int64_t i = gf + (v ? li : 0);
+            const float4 h = A.body_hi[i], l = A.body_lo[i];
+            const float lx = v ? A.lam[i] : 0.0f, ly = v ? A.lam[A.n + i] : 0.0f;
+            const float lz = v ? A.lam[2 * A.n + i] : 0.0f;
+            const float mu = (v && A.mu) ? A.mu[i] : 0.0f;
+            float *rec = reinterpret_cast<float *>(T) + (li >> 1) * 4 + (li & 1);
+            constexpr int K = 4 * (NCRIT / 2);  // floats per array
+            rec[0] = -((h.x - box.x) + (l.x - clo.x));
+            rec[2] = -((h.y - box.y) + (l.y - clo.y));
+            rec[K] = -((h.z - box.z) + (l.z - clo.z));
+            rec[K + 2] = __int_as_float((int)i);
+            rec[2 * K] = lx;
+            rec[2 * K + 2] = ly;
+            rec[3 * K] = lz;
+            rec[3 * K + 2] = mu;
+            rec[4 * K] = -mu;
+            rec[4 * K + 2] = 0.5f * mu;
         }
         for (int k = lane; k < NCRIT * 3; k += 32) W->tacc[k] = 0.0f;
         __syncwarp();
@@ -441,53 +519,59 @@ struct AdjointPolicy : Fp32Rings {
     __device__ __forceinline__ void flush_pc(const WarpLists &L, int hb, int cnt, int lane) {
         const bool v = FULL || lane < cnt;
         const int j = hb + (v ? lane : 0);
-        const float4 a = L.ca[j], b = L.cb[j];
-        float4 c = L.cc[j];
-        float4 am = a;
+        const float4 a = L.ca[j];
+        float4 b = L.cb[j], c = L.cc[j];
+        float M = a.w;
         if (!FULL && !v) {  // an empty lane: a massless, quadrupole-free cell
-            am.w = 0.0f;
-            c = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            M = 0.0f;
+            b = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            c = b;
         }
-        const float4 bm = (!FULL && !v) ? make_float4(0.0f, 0.0f, 0.0f, 0.0f) : b;
-        const float M3 = -3.0f * am.w, cw5 = -5.0f * c.w;
-        float ax = 0, ay = 0, az = 0, aM = 0, aP = 0;
-        float dxx = 0, dyy = 0, dzz = 0, oxy = 0, oxz = 0, oyz = 0;
+        const CellDup C{dup2(a.x), dup2(a.y), dup2(a.z), dup2(M), dup2(b.x), dup2(b.y),
+                        dup2(b.z), dup2(b.w), dup2(c.x), dup2(c.y), dup2(c.w),
+                        dup2(-3.0f * M), dup2(-5.0f * c.w)};
+        const f32x2 e2 = dup2(eps2);
+        f32x2 ax = 0ull, ay = 0ull, az = 0ull, aM = 0ull, aP = 0ull;
+        f32x2 dxx = 0ull, dyy = 0ull, dzz = 0ull, oxy = 0ull, oxz = 0ull, oyz = 0ull;
         for (int t0 = 0; t0 < gc; t0 += ADJ_CHUNK) {
             float part[3 * ADJ_CHUNK];
 #pragma unroll
-            for (int tt = 0; tt < ADJ_CHUNK; ++tt) {
-                const int t = t0 + tt;
-                float gx = 0.0f, gy = 0.0f, gz = 0.0f;
-                if (t < gc) {
-                    const float4 tp = T->pos[t], tl = T->lam[t];
-                    float gM, P0, vx, vy, vz, rx, ry, rz;
-                    pc_vjp(am, bm, c, M3, cw5, tp, tl, eps2, gx, gy, gz, gM, P0, vx, vy, vz, rx, ry,
-                           rz);
-                    if (!FULL && !v) gx = gy = gz = gM = P0 = vx = vy = vz = 0.0f;
-                    ax += gx;
-                    ay += gy;
-                    az += gz;
-                    aM += gM;
-                    aP += P0;
-                    dxx = fmaf(rx, vx, dxx);
-                    dyy = fmaf(ry, vy, dyy);
-                    dzz = fmaf(rz, vz, dzz);
-                    oxy = fmaf(rx, vy, fmaf(ry, vx, oxy));
-                    oxz = fmaf(rx, vz, fmaf(rz, vx, oxz));
-                    oyz = fmaf(ry, vz, fmaf(rz, vy, oyz));
-                }
-                part[3 * tt] = gx;
-                part[3 * tt + 1] = gy;
-                part[3 * tt + 2] = gz;
+            for (int tp = 0; tp < ADJ_CHUNK / 2; ++tp) {
+                const TargetPair T2 = load_targets(T, (t0 >> 1) + tp);
+                f32x2 gx, gy, gz, gM, P0, vx, vy, vz, rx, ry, rz;
+                pc_vjp2(C, T2, e2, gx, gy, gz, gM, P0, vx, vy, vz, rx, ry, rz);
+                ax = add2(ax, gx);
+                ay = add2(ay, gy);
+                az = add2(az, gz);
+                aM = add2(aM, gM);
+                aP = add2(aP, P0);
+                dxx = fma2(rx, vx, dxx);
+                dyy = fma2(ry, vy, dyy);
+                dzz = fma2(rz, vz, dzz);
+                oxy = fma2(rx, vy, fma2(ry, vx, oxy));
+                oxz = fma2(rx, vz, fma2(rz, vx, oxz));
+                oyz = fma2(ry, vz, fma2(rz, vy, oyz));
+                u2(gx, part[6 * tp], part[6 * tp + 3]);
+                u2(gy, part[6 * tp + 1], part[6 * tp + 4]);
+                u2(gz, part[6 * tp + 2], part[6 * tp + 5]);
             }
             reduce_chunk(part, t0, lane);
         }
         if (v) {
             // gQ = P0 I + (r v^T + v r^T) with v2 = 2v accumulated:
             // diagonal P0 + r_a v2_a, off-diagonal (r_a v2_b + r_b v2_a) / 2
-            const float aQ[6] = {aP + dxx, aP + dyy, aP + dzz, 0.5f * oxy, 0.5f * oxz, 0.5f * oyz};
-            cell_add(L.cid[j], ax, ay, az, aM, aQ);
+            const float P = fold(aP);
+            const float aQ[6] = {P + fold(dxx), P + fold(dyy), P + fold(dzz),
+                                 0.5f * fold(oxy), 0.5f * fold(oxz), 0.5f * fold(oyz)};
+            cell_add(L.cid[j], fold(ax), fold(ay), fold(az), fold(aM), aQ);
         }
+    }
+
+    // the sum of the two halves
+    __device__ __forceinline__ static float fold(f32x2 v) {
+        float a, b;
+        u2(v, a, b);
+        return a + b;
     }
 
     __device__ __forceinline__ void cell_add(int node, float ax, float ay, float az, float aM,
@@ -504,30 +588,28 @@ struct AdjointPolicy : Fp32Rings {
         float4 s = L.pp[j];
         if (!FULL && !v) s.w = 0.0f;  // an empty lane: a massless source
         const int sid = L.pid[j];
-        float ax = 0, ay = 0, az = 0, am = 0;
+        const f32x2 sx = dup2(s.x), sy = dup2(s.y), sz = dup2(s.z), sm = dup2(s.w);
+        const f32x2 e2 = dup2(eps2);
+        f32x2 ax = 0ull, ay = 0ull, az = 0ull, am = 0ull;
         for (int t0 = 0; t0 < gc; t0 += ADJ_CHUNK) {
             float part[3 * ADJ_CHUNK];
 #pragma unroll
-            for (int tt = 0; tt < ADJ_CHUNK; ++tt) {
-                const int t = t0 + tt;
-                float gx = 0.0f, gy = 0.0f, gz = 0.0f;
-                if (t < gc) {
-                    const float4 tp = T->pos[t], tl = T->lam[t];
-                    float gm;
-                    pp_vjp(s, sid == __float_as_int(tp.w), tp, tl, eps2, gx, gy, gz, gm);
-                    if (!FULL && !v) gx = gy = gz = gm = 0.0f;
-                    ax += gx;
-                    ay += gy;
-                    az += gz;
-                    am += gm;
-                }
-                part[3 * tt] = gx;
-                part[3 * tt + 1] = gy;
-                part[3 * tt + 2] = gz;
+            for (int tp = 0; tp < ADJ_CHUNK / 2; ++tp) {
+                const TargetPair T2 = load_targets(T, (t0 >> 1) + tp);
+                f32x2 gx, gy, gz, gm;
+                pp_vjp2(sx, sy, sz, sm, sid, T2, e2, gx, gy, gz, gm);
+                ax = add2(ax, gx);
+                ay = add2(ay, gy);
+                az = add2(az, gz);
+                am = add2(am, gm);
+                u2(gx, part[6 * tp], part[6 * tp + 3]);
+                u2(gy, part[6 * tp + 1], part[6 * tp + 4]);
+                u2(gz, part[6 * tp + 2], part[6 * tp + 5]);
             }
             reduce_chunk(part, t0, lane);
         }
-        if (v) atomicAdd(&part_adj[sid], make_float4(G * ax, G * ay, G * az, G * am));
+        if (v) atomicAdd(&part_adj[sid], make_float4(G * fold(ax), G * fold(ay), G * fold(az),
+                                                     G * fold(am)));
     }
 
     __device__ __forceinline__ void finish(const WalkArgs &A, uint32_t gf, uint32_t gcount, int lane) {
@@ -846,7 +928,7 @@ __global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(const WalkArgs A) {
     }
 }
 
-__global__ void __launch_bounds__(WALK_WARPS * 32, 5) k_walk_adjoint(const WalkArgs A) {
+__global__ void __launch_bounds__(WALK_WARPS * 32, 4) k_walk_adjoint(const WalkArgs A) {
     __shared__ WarpLists lists[WALK_WARPS];
     __shared__ WarpTargets targets[WALK_WARPS];
     __shared__ WarpAdjoint scratch[WALK_WARPS];
