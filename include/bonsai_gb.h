@@ -156,6 +156,23 @@ int tree_get_forces(bonsai_ctx *ctx, float *acc, float *pot);
  * Errors: ESTATE (no forces yet), ECUDA. */
 int bonsai_diagnostics(bonsai_ctx *ctx, double out[10]);
 
+/* tree_direct_forces -- direct summation, the O(N^2) sum that the tree
+ * approximates (Sec. I; the direct N-body kernel of Fig. 1), over all n
+ * particles of the last tree_build for nt targets:
+ *   a_i = G sum_{j != i} m_j r_ij / (|r_ij|^2 + eps^2)^{3/2},
+ *   phi_i = -G sum_{j != i} m_j / (|r_ij|^2 + eps^2)^{1/2},  r_ij = x_j - x_i.
+ * Pair terms in FP32 on coordinates split into an FP32 head and remainder
+ * (differences accurate to FP32 relative to the separation), summed in FP32
+ * within tiles of 256 sources and in FP64 across tiles, in a fixed order
+ * (deterministic).  targets: device int64 [nt] caller indices, or NULL for
+ * all particles (then nt must equal n).  acc: device float64 [3][nt], pot:
+ * device float64 [nt], in the order of targets; either may be NULL.
+ * Errors: EINVAL (null ctx, nt < 1, eps < 0, NULL targets with nt != n, an
+ * index outside [0, n), found on the device), ESTATE (no tree), ENOMEM,
+ * ECUDA. */
+int tree_direct_forces(bonsai_ctx *ctx, const int64_t *targets, int64_t nt, float eps,
+                       double *acc, double *pot);
+
 /* ---- adjoint (vector-Jacobian products) ------------------------------- */
 /* The paper has no adjoint.  These give the exact derivative of the forward
  * map with the tree and interaction lists of the forward evaluation held

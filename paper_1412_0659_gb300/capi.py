@@ -32,7 +32,7 @@ EXPORTED = (
     "bonsai_diagnostics", "tree_get_stats", "tree_solve_host", "tree_debug_cube",
     "tree_debug_keys", "tree_debug_nodes", "tree_debug_multipoles", "tree_debug_groups",
     "bonsai_strerror", "bonsai_sfc_order_noalloc", "tree_forces_vjp", "tree_run", "tree_run_vjp",
-    "tree_debug_set_frontier_capacity", "tree_forces_fp64",
+    "tree_debug_set_frontier_capacity", "tree_forces_fp64", "tree_direct_forces",
 )
 
 BONSAI_NOALLOC_MAX_N = 1 << 20
@@ -98,6 +98,7 @@ def load(path: str | None = None):
             "tree_run": (i32, [P, i32, f64, i32]),
             "tree_run_vjp": (i32, [P, P, P, P, P, P, P]),
             "tree_debug_set_frontier_capacity": (i32, [P, i32]),
+            "tree_direct_forces": (i32, [P, P, i64, f32, P, P]),
             "tree_forces_fp64": (i32, [P, f32, f32, P, P]),
         }
         for name, (res, args) in sig.items():
@@ -194,6 +195,13 @@ def tree_forces_fp64(ctx, theta: float, eps: float, acc=None, pot=None) -> None:
     import torch
     _check(load().tree_forces_fp64(ctx, float(theta), float(eps), _ptr(acc, torch.float64, None, "acc"),
                                    _ptr(pot, torch.float64, None, "pot")), "tree_forces_fp64")
+
+
+def tree_direct_forces(ctx, targets, nt: int, eps: float, acc=None, pot=None) -> None:
+    import torch
+    _check(load().tree_direct_forces(ctx, _ptr(targets, torch.int64, nt, "targets"), int(nt), float(eps),
+                                     _ptr(acc, torch.float64, 3 * nt, "acc"),
+                                     _ptr(pot, torch.float64, nt, "pot")), "tree_direct_forces")
 
 
 def tree_set_velocities(ctx, vel) -> None:

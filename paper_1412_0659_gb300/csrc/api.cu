@@ -202,6 +202,7 @@ void bonsai_destroy(bonsai_ctx *c) {
     release(c->acc); release(c->pot); release(c->key); release(c->key2);
     release(c->val); release(c->val2); release(c->hist); release(c->scan_tmp);
     release(c->box_part); release(c->body_hi); release(c->body_lo);
+    release(c->inv_id); release(c->dir_part);
     release(c->nd_first); release(c->nd_count); release(c->nd_child); release(c->nd_nchild);
     release(c->nd_level); release(c->nd_parent); release(c->nd_scan);
     release(c->nd_M); release(c->nd_com); release(c->nd_Q);
@@ -243,6 +244,19 @@ int tree_build(bonsai_ctx *c, const double *pos, const double *mass, int64_t n) 
 int tree_forces(bonsai_ctx *c, float theta, float eps, float *acc, float *pot) {
     if (!c) return BONSAI_EINVAL;
     return forces_internal(c, theta, eps, acc, pot);
+}
+
+int tree_direct_forces(bonsai_ctx *c, const int64_t *targets, int64_t nt, float eps, double *acc,
+                       double *pot) {
+    if (!c || nt < 1 || !(eps >= 0.0f) || !isfinite(eps)) return BONSAI_EINVAL;
+    if (!c->have_tree) return BONSAI_ESTATE;
+    if (!targets && nt != c->n) return BONSAI_EINVAL;
+    BGB_CUDA(cudaMemsetAsync(&c->dsc->status, 0, sizeof(int32_t), c->stream));
+    int rc = direct_forces(c, targets, nt, eps, acc, pot);
+    if (rc) return rc;
+    if ((rc = read_scalars(c))) return rc;
+    if (c->hsc->status & ST_BAD_INPUT) return BONSAI_EINVAL;
+    return BONSAI_OK;
 }
 
 int tree_forces_fp64(bonsai_ctx *c, float theta, float eps, double *acc, double *pot) {

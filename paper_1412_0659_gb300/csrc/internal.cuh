@@ -136,6 +136,10 @@ struct bonsai_ctx {
     bgb::DBuf<double> ckpt;        // [nck][6n]
     bgb::DBuf<double> seg_pos;     // [ckpt_every + 1][3n]
 
+    // direct summation scratch
+    bgb::DBuf<uint32_t> inv_id;    // [n] caller index -> key-order slot
+    bgb::DBuf<double> dir_part;    // [chunks][4][nt] partial sums
+
     // timing events
     cudaEvent_t ev[10];
     bonsai_stats stats;
@@ -169,6 +173,9 @@ void launch_cell_pack(bonsai_ctx *c, float theta);
 // walk.cu
 int walk_force(bonsai_ctx *c, float theta, float eps, float *acc_caller, float *pot_caller);
 int walk_force_fp64(bonsai_ctx *c, float eps, double *acc, double *pot);
+// direct.cu
+int direct_forces(bonsai_ctx *c, const int64_t *targets, int64_t nt, float eps, double *acc,
+                  double *pot);
 // integrate.cu
 void launch_kick(bonsai_ctx *c, double h);
 void launch_drift(bonsai_ctx *c, double dt);

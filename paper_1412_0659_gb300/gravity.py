@@ -69,6 +69,19 @@ class TreeGravity:
         capi.tree_forces_fp64(self.ctx, theta, eps, acc, pot)
         return acc, pot
 
+    def direct_forces(self, targets: torch.Tensor | None = None, eps: float | None = None):
+        """Direct summation over all particles of the current tree for the
+        given caller indices (all if None); (3, nt) / (nt,) float64."""
+        eps = self.eps if eps is None else eps
+        dev = torch.device("cuda", torch.cuda.current_device())
+        nt = self.n if targets is None else int(targets.numel())
+        if targets is not None:
+            targets = targets.to(device=dev, dtype=torch.int64).contiguous()
+        acc = torch.empty((3, nt), dtype=torch.float64, device=dev)
+        pot = torch.empty(nt, dtype=torch.float64, device=dev)
+        capi.tree_direct_forces(self.ctx, targets, nt, eps, acc, pot)
+        return acc, pot
+
     def set_velocities(self, vel: torch.Tensor):
         capi.tree_set_velocities(self.ctx, vel)
 

@@ -120,6 +120,52 @@ def _jeans_sigma2(rgrid, rho, menc_tot, G):
     return s2
 
 
+def _exp_disk(rng, n_d, M_disk, R_d, z0, R_max, Q_toomre, G, menc_other):
+    """Exponential disk: R from Gamma(2, R_d) truncated at R_max, z = z0
+    atanh(U) (sech^2), Toomre-Q radial dispersion, epicyclic azimuthal
+    dispersion, vertical dispersion from the isothermal sheet, and the
+    asymmetric-drift corrected mean rotation in the potential of the disk
+    (Freeman's thin-disk circular speed) plus the spherical mass
+    menc_other(R) of the other components."""
+    from scipy import special
+
+    R = np.empty(n_d)
+    k = 0
+    while k < n_d:
+        rr = rng.gamma(2.0, R_d, 2 * (n_d - k) + 16)
+        rr = rr[rr <= R_max][: n_d - k]
+        R[k:k + rr.size] = rr
+        k += rr.size
+    phi = rng.uniform(0.0, 2.0 * math.pi, n_d)
+    u = rng.uniform(-1.0, 1.0, n_d)
+    u = np.clip(u, -1.0 + 1e-15, 1.0 - 1e-15)
+    z = z0 * np.arctanh(u)
+
+    Rg = np.linspace(0.01, R_max * 1.2, 4000)
+    sigma0 = M_disk / (2.0 * math.pi * R_d * R_d)
+    y = Rg / (2.0 * R_d)
+    vdisk2 = 4.0 * math.pi * G * sigma0 * R_d * y * y * (
+        special.i0(y) * special.k0(y) - special.i1(y) * special.k1(y))
+    vc2 = G * menc_other(Rg) / Rg + vdisk2
+    om2 = vc2 / (Rg * Rg)
+    kap2 = Rg * np.gradient(om2, Rg) + 4.0 * om2
+    kap = np.sqrt(np.maximum(kap2, 1e-30))
+    Sig = sigma0 * np.exp(-Rg / R_d)
+    sR = Q_toomre * 3.36 * G * Sig / kap
+    sphi = sR * kap / (2.0 * np.sqrt(om2))
+    sz = np.sqrt(math.pi * G * Sig * z0)
+    # asymmetric drift: vphi^2 = vc^2 + sR^2 (1 - sphi^2/sR^2 + dln(Sig sR^2)/dlnR)
+    dln = np.gradient(np.log(Sig * sR * sR), np.log(Rg))
+    vphi2 = np.maximum(vc2 + sR * sR * (1.0 - (sphi * sphi) / (sR * sR) + dln), 0.0)
+    vbar = np.sqrt(vphi2)
+
+    vR = rng.standard_normal(n_d) * np.interp(R, Rg, sR)
+    vphi = np.interp(R, Rg, vbar) + rng.standard_normal(n_d) * np.interp(R, Rg, sphi)
+    vz = rng.standard_normal(n_d) * np.interp(R, Rg, sz)
+    c, s = np.cos(phi), np.sin(phi)
+    return np.stack([R * c, R * s, z]), np.stack([vR * c - vphi * s, vR * s + vphi * c, vz])
+
+
 def milky_way(n: int, seed: int = 1002, eps: float = 0.01, theta: float = 0.4, dt: float = 0.1,
               ratio=(5.0, 1.0, 0.2), M_halo=1.0e12, a_halo=30.0, rcut=200.0, M_bulge=1.0e10,
               a_bulge=0.5, M_disk=5.0e10, R_d=2.5, z0=0.3, R_max=30.0, Q_toomre=1.5,
@@ -134,8 +180,6 @@ def milky_way(n: int, seed: int = 1002, eps: float = 0.01, theta: float = 0.4, d
     is exponential in R (Gamma(2, R_d), truncated at R_max) and sech^2 in z,
     with Toomre-Q epicyclic velocity dispersions and an asymmetric-drift
     corrected mean rotation."""
-    from scipy import special
-
     rng = np.random.default_rng(seed)
     tot = sum(ratio)
     n_d = int(math.floor(n * ratio[1] / tot))
@@ -161,44 +205,9 @@ def milky_way(n: int, seed: int = 1002, eps: float = 0.01, theta: float = 0.4, d
     hp, hv = spheroid(n_h, M_halo, a_halo)
     bp, bv = spheroid(n_b, M_bulge, a_bulge)
 
-    # disk
-    R = np.empty(n_d)
-    k = 0
-    while k < n_d:
-        rr = rng.gamma(2.0, R_d, 2 * (n_d - k) + 16)
-        rr = rr[rr <= R_max][: n_d - k]
-        R[k:k + rr.size] = rr
-        k += rr.size
-    phi = rng.uniform(0.0, 2.0 * math.pi, n_d)
-    u = rng.uniform(-1.0, 1.0, n_d)
-    u = np.clip(u, -1.0 + 1e-15, 1.0 - 1e-15)
-    z = z0 * np.arctanh(u)
-
-    Rg = np.linspace(0.01, R_max * 1.2, 4000)
-    sigma0 = M_disk / (2.0 * math.pi * R_d * R_d)
-    y = Rg / (2.0 * R_d)
-    vdisk2 = 4.0 * math.pi * G * sigma0 * R_d * y * y * (
-        special.i0(y) * special.k0(y) - special.i1(y) * special.k1(y))
-    mh = _hernquist_menc(Rg, M_halo, a_halo, rcut) + _hernquist_menc(Rg, M_bulge, a_bulge, rcut)
-    vc2 = G * mh / Rg + vdisk2
-    om2 = vc2 / (Rg * Rg)
-    kap2 = Rg * np.gradient(om2, Rg) + 4.0 * om2
-    kap = np.sqrt(np.maximum(kap2, 1e-30))
-    Sig = sigma0 * np.exp(-Rg / R_d)
-    sR = Q_toomre * 3.36 * G * Sig / kap
-    sphi = sR * kap / (2.0 * np.sqrt(om2))
-    sz = np.sqrt(math.pi * G * Sig * z0)
-    # asymmetric drift: vphi^2 = vc^2 + sR^2 (1 - sphi^2/sR^2 + dln(Sig sR^2)/dlnR)
-    dln = np.gradient(np.log(Sig * sR * sR), np.log(Rg))
-    vphi2 = np.maximum(vc2 + sR * sR * (1.0 - (sphi * sphi) / (sR * sR) + dln), 0.0)
-    vbar = np.sqrt(vphi2)
-
-    vR = rng.standard_normal(n_d) * np.interp(R, Rg, sR)
-    vphi = np.interp(R, Rg, vbar) + rng.standard_normal(n_d) * np.interp(R, Rg, sphi)
-    vz = rng.standard_normal(n_d) * np.interp(R, Rg, sz)
-    c, s = np.cos(phi), np.sin(phi)
-    dp = np.stack([R * c, R * s, z])
-    dv = np.stack([vR * c - vphi * s, vR * s + vphi * c, vz])
+    dp, dv = _exp_disk(rng, n_d, M_disk, R_d, z0, R_max, Q_toomre, G,
+                       lambda R: _hernquist_menc(R, M_halo, a_halo, rcut)
+                       + _hernquist_menc(R, M_bulge, a_bulge, rcut))
 
     pos = np.concatenate([hp, dp, bp], axis=1)
     vel = np.concatenate([hv, dv, bv], axis=1)
@@ -210,6 +219,32 @@ def milky_way(n: int, seed: int = 1002, eps: float = 0.01, theta: float = 0.4, d
     comps = {"halo": (0, n_h), "disk": (n_h, n_d), "bulge": (n_h + n_d, n_b)}
     return Model(np.ascontiguousarray(pos), np.ascontiguousarray(vel), mass, G, eps, theta, dt,
                  name or f"milky-way-{n}", comps)
+
+
+def halo_disk(n_halo: int, n_disk: int, seed: int = 1004, eps: float = 0.02, theta: float = 0.4,
+              dt: float = 0.1, M_halo=1.0e11, a_halo=10.0, rmax_halo=300.0, M_disk=5.0e10, R_d=2.5,
+              z0=0.3, R_max=30.0, Q_toomre=1.5, G: float = G_KPC_MSUN_MYR) -> Model:
+    """Plummer halo plus exponential disk in kpc / Msun / Myr (the model of
+    the differentiable run): the halo is sampled from its own isotropic
+    distribution function (radii beyond rmax_halo redrawn), the disk as in
+    the Milky-Way-like model with its rotation in the potential of the disk
+    plus the Plummer halo.  Equal masses within each component; centre of
+    mass and mean velocity at rest."""
+    rng = np.random.default_rng(seed)
+    h = plummer(n_halo, seed=int(rng.integers(1 << 31)), rmax=rmax_halo / a_halo, G=G, M=M_halo,
+                a=a_halo)
+
+    def menc_plummer(R):
+        return M_halo * R ** 3 / (R * R + a_halo * a_halo) ** 1.5
+
+    dp, dv = _exp_disk(rng, n_disk, M_disk, R_d, z0, R_max, Q_toomre, G, menc_plummer)
+    pos = np.concatenate([h.pos, dp], axis=1)
+    vel = np.concatenate([h.vel, dv], axis=1)
+    mass = np.concatenate([h.mass, np.full(n_disk, M_disk / max(n_disk, 1))])
+    pos -= (pos * mass).sum(axis=1, keepdims=True) / mass.sum()
+    vel -= (vel * mass).sum(axis=1, keepdims=True) / mass.sum()
+    return Model(np.ascontiguousarray(pos), np.ascontiguousarray(vel), mass, G, eps, theta, dt,
+                 f"halo-disk-{n_halo}+{n_disk}", {"halo": (0, n_halo), "disk": (n_halo, n_disk)})
 
 
 def config_model(index: int, n: int | None = None) -> Model:
