@@ -32,6 +32,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
+# DRAM bytes (read + written) of one walk/force launch, from a one-pass ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum) of the benchmark
+# command, valid only for the walk source it was taken on (checked by hash).
+WALK_TRAFFIC = {"walk_cu_sha256": "461cc5599d412fcfc07e62b904694bfc35580991d946751c257a70b74d0e2f28",
+                "bytes": {"milky-way-2^23": 708.41e6 + 277.75e6}}
+
 METRIC = "tree-force Tflop/s (23 flops/p-p + 65 flops/p-c, Sec. VI.A) per full KDK step, theta=0.4"
 UNIT = "Tflop/s"
 FP32_LANES_PER_SM = 128
@@ -120,6 +126,18 @@ def aggregate(t_ms: float, work: float, world: int, device=None):
     ww = torch.tensor([work], dtype=torch.float64, device=device)
     dist.all_reduce(ww)
     return float(tt.item()), float(ww.item())
+
+
+def walk_traffic(workload: str):
+    """The captured DRAM bytes per walk launch for this workload, or None
+    when there is no capture of the current walk source."""
+    import hashlib
+    path = os.path.join(ROOT, "paper_1412_0659_gb300", "csrc", "walk.cu")
+    with open(path, "rb") as f:
+        digest = hashlib.sha256(f.read()).hexdigest()
+    if digest != WALK_TRAFFIC["walk_cu_sha256"]:
+        return None
+    return WALK_TRAFFIC["bytes"].get(workload)
 
 
 def _workload(name: str, rank: int):
@@ -256,11 +274,33 @@ def run_ours(args):
     walk_avg = sum(walk_ms) / len(walk_ms)
     flops_launch = flops / args.steps
     achieved = flops_launch / (walk_avg * 1e-3) / 1e12
+    traffic = args.traffic if args.traffic is not None else walk_traffic(args.workload)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": args.traffic,
+                "frac": achieved / peak, "traffic": traffic,
                 "kernel": "k_walk (fused walk + p-p/p-c evaluation)",
                 "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flops x {max_mhz:.0f} MHz",
                 "convention_cap": "23/26 of peak for p-p and 65/76 for p-c at one FP32 instruction per issue slot"}
+
+    # --- direct summation on the same particles (the paper's Fig. 1 compares
+    # tree and direct N-body performance): 2^16 targets over all sources ---
+    direct = None
+    if not args.no_direct:
+        nt = min(n, 1 << 16)
+        tgt = torch.from_numpy(np.random.default_rng(5).choice(n, nt, replace=False)).to(dev)
+        g.direct_forces(tgt)
+        d0 = torch.cuda.Event(enable_timing=True)
+        d1 = torch.cuda.Event(enable_timing=True)
+        d0.record(stream)
+        g.direct_forces(tgt)
+        d1.record(stream)
+        torch.cuda.synchronize()
+        d_s = d0.elapsed_time(d1) * 1e-3
+        pairs = float(nt) * n
+        direct = {"targets": nt, "sources": n, "ms": d_s * 1e3, "pairs_per_s": pairs / d_s,
+                  "tflops_23_per_pair": 23.0 * pairs / d_s / 1e12,
+                  "tree_speedup_per_particle": (n / (walk_avg * 1e-3)) / (nt / d_s),
+                  "what": "tree_direct_forces: FP32 pair terms, FP64 tile sums; tree_speedup_per_particle = "
+                          "particles/s of the tree walk / particles/s of direct summation"}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -283,7 +323,7 @@ def run_ours(args):
             "phase_ms": {"keys_sort": statistics.mean(keys_ms), "tree_groups_multipoles": statistics.mean(tree_ms),
                          "force": statistics.mean(force_ms), "walk_kernel": walk_avg},
             "energy": {"E_tot": diag["E_tot"] if diag else None},
-            "adjoint": adjoint,
+            "adjoint": adjoint, "direct": direct,
             "clocks": clk, "gpu_launches": int(launches), "roofline": roofline, "e2e": e2e,
             "cpu_baseline": cpu,
         }
@@ -359,6 +399,7 @@ def main():
                     help="groups walked by the CPU oracle sample (about 10 s of CPU work at 2^23)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward timing")
+    ap.add_argument("--no-direct", action="store_true", help="skip the direct-summation comparison")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per walk launch from an ncu capture (null when not captured)")
     args = ap.parse_args()
