@@ -33,24 +33,31 @@ __global__ void k_root(uint32_t *first, uint32_t *count, uint32_t *level, uint32
     parent[0] = 0;
 }
 
-__device__ inline uint32_t lower_bound_key(const uint64_t *__restrict__ key, uint32_t lo,
-                                           uint32_t hi, uint64_t v) {
-    while (lo < hi) {
-        uint32_t mid = lo + ((hi - lo) >> 1);
-        if (key[mid] < v) lo = mid + 1; else hi = mid;
-    }
-    return lo;
-}
-
-// Child boundaries of a node at level l: b[d] = first slot whose digit l+1 is >= d.
+// Child boundaries of a node at level l: b[d] = first slot of [f, f + c)
+// whose digit l+1 is >= d.  The seven lower bounds share the range, so they
+// run in lockstep (branch-free halving; the trip count depends on c only):
+// log2(c) rounds of seven independent loads instead of seven chained
+// searches.
 __device__ inline void child_bounds(const uint64_t *__restrict__ key, uint32_t f, uint32_t c,
                                     int l, uint32_t b[9]) {
     const int shift = 3 * (MAX_LEVEL - 1 - l);
     const uint64_t base = key[f] & ~((8ull << shift) - 1ull);
+    uint32_t lo[7];
+#pragma unroll
+    for (int d = 0; d < 7; ++d) lo[d] = f;
+    uint32_t len = c;
+    while (len > 1) {
+        const uint32_t half = len >> 1;
+#pragma unroll
+        for (int d = 0; d < 7; ++d)
+            lo[d] = key[lo[d] + half] < (base | ((uint64_t)(d + 1) << shift)) ? lo[d] + half : lo[d];
+        len -= half;
+    }
     b[0] = f;
     b[8] = f + c;
 #pragma unroll
-    for (int d = 1; d < 8; ++d) b[d] = lower_bound_key(key, b[d - 1], f + c, base | ((uint64_t)d << shift));
+    for (int d = 0; d < 7; ++d)
+        b[d + 1] = lo[d] + (key[lo[d]] < (base | ((uint64_t)(d + 1) << shift)) ? 1u : 0u);
 }
 
 __global__ void __launch_bounds__(256) k_split_count(const uint64_t *__restrict__ key,
@@ -220,8 +227,23 @@ __global__ void __launch_bounds__(256) k_group_write(const uint32_t *__restrict_
     if (flag[i]) gfirst[gid[i]] = (uint32_t)i;
 }
 
-// One warp per group: FP64 box of the members, its FP32 centre (nearest),
-// the centre's FP32 remainder, and the half-size rounded up to FP32.
+// Order-preserving integer image of a double: for finite values (the input
+// check rejects the others) a < b exactly when key(a) < key(b), with -0 just
+// below +0.  Minima and maxima taken on the keys are therefore exact, and
+// run on the integer pipes instead of the FP64 one.
+__device__ __forceinline__ long long order_key(double v) {
+    const long long b = __double_as_longlong(v);
+    return b ^ ((b >> 63) & 0x7fffffffffffffffll);
+}
+__device__ __forceinline__ double from_order_key(long long k) {
+    return __longlong_as_double(k ^ ((k >> 63) & 0x7fffffffffffffffll));
+}
+
+// Per group: the FP64 box of the members, its FP32 centre (nearest), the
+// centre's FP32 remainder, and the half-size rounded up to FP32.  A warp
+// takes 32 consecutive groups: for each, all lanes load its members and
+// reduce their minima and maxima; lane k keeps those of group k, and the
+// FP64 epilogue then runs once per lane for the 32 groups at a time.
 __global__ void __launch_bounds__(256) k_group_box(const double *__restrict__ pos, int64_t n,
                                                    const uint32_t *__restrict__ gfirst,
                                                    uint32_t *__restrict__ gcount, int64_t ng,
@@ -229,38 +251,51 @@ __global__ void __launch_bounds__(256) k_group_box(const double *__restrict__ po
                                                    float4 *__restrict__ gbox,
                                                    float4 *__restrict__ ghalf,
                                                    float4 *__restrict__ glo) {
-    int64_t g = (blockIdx.x * 256ll + threadIdx.x) >> 5;
-    int lane = threadIdx.x & 31;
-    if (g >= ng) return;
-    uint32_t f = gfirst[g];
-    uint32_t e = (g + 1 < ng) ? gfirst[g + 1] : (uint32_t)n;
-    uint32_t c = e - f;
-    if (lane == 0) gcount[g] = c;
+    const int64_t g0 = ((blockIdx.x * 256ll + threadIdx.x) >> 5) * 32;
+    const int lane = threadIdx.x & 31;
+    if (g0 >= ng) return;
+    long long myn[3] = {0, 0, 0}, myx[3] = {0, 0, 0};
+    const int kend = (int)min((int64_t)32, ng - g0);
+    for (int k = 0; k < kend; ++k) {
+        const int64_t g = g0 + k;
+        const uint32_t f = gfirst[g];
+        const uint32_t e = (g + 1 < ng) ? gfirst[g + 1] : (uint32_t)n;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            long long kn = 0x7fffffffffffffffll, kx = -0x7fffffffffffffffll - 1;
+            for (uint32_t j = f + lane; j < e; j += 32) {
+                const long long key = order_key(pos[d * n + j]);
+                kn = min(kn, key);
+                kx = max(kx, key);
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                kn = min(kn, __shfl_xor_sync(0xffffffffu, kn, o));
+                kx = max(kx, __shfl_xor_sync(0xffffffffu, kx, o));
+            }
+            if (lane == k) {
+                myn[d] = kn;
+                myx[d] = kx;
+            }
+        }
+    }
+    const int64_t g = g0 + lane;
+    if (lane >= kend) return;
+    const uint32_t f = gfirst[g];
+    gcount[g] = ((g + 1 < ng) ? gfirst[g + 1] : (uint32_t)n) - f;
     float cf[3], hf[3], cl[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-        double mn = INFINITY, mx = -INFINITY;
-        for (uint32_t j = f + lane; j < e; j += 32) {
-            double v = pos[d * n + j];
-            mn = fmin(mn, v);
-            mx = fmax(mx, v);
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-            mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        }
-        double ctr = __dmul_rn(__dadd_rn(mn, mx), 0.5);
-        double half = __dmul_rn(__dsub_rn(mx, mn), 0.5);
+        const double mn = from_order_key(myn[d]), mx = from_order_key(myx[d]);
+        const double ctr = __dmul_rn(__dadd_rn(mn, mx), 0.5);
+        const double half = __dmul_rn(__dsub_rn(mx, mn), 0.5);
         cf[d] = __double2float_rn(ctr);
         cl[d] = __double2float_rn(__dsub_rn(ctr, (double)cf[d]));
         hf[d] = __double2float_ru(half);
-        if (lane == 0) gcentre[d * ng + g] = ctr;
+        gcentre[d * ng + g] = ctr;
     }
-    if (lane == 0) {
-        gbox[g] = make_float4(cf[0], cf[1], cf[2], 0.0f);
-        ghalf[g] = make_float4(hf[0], hf[1], hf[2], 0.0f);
-        glo[g] = make_float4(cl[0], cl[1], cl[2], 0.0f);
-    }
+    gbox[g] = make_float4(cf[0], cf[1], cf[2], 0.0f);
+    ghalf[g] = make_float4(hf[0], hf[1], hf[2], 0.0f);
+    glo[g] = make_float4(cl[0], cl[1], cl[2], 0.0f);
 }
 
 // Particle records for the walk: FP32 head and remainder of each coordinate.
@@ -430,7 +465,7 @@ int build_groups(bonsai_ctx *c) {
         ensure(c->grp_npp, ng) || ensure(c->grp_npc, ng))
         return BONSAI_ENOMEM;
     k_group_write<<<grid_for(n, 256), 256, 0, c->stream>>>(c->grp_flag.p, gid, n, c->grp_first.p);
-    k_group_box<<<grid_for(ng * 32, 256), 256, 0, c->stream>>>(
+    k_group_box<<<grid_for((ng + 31) / 32 * 32, 256), 256, 0, c->stream>>>(
         c->pos.p, n, c->grp_first.p, c->grp_count.p, ng, c->grp_centre.p, c->grp_box.p,
         c->grp_half.p, c->grp_lo.p);
     c->launches += 2;
