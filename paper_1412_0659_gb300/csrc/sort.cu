@@ -5,7 +5,7 @@
 // The sort is 8 passes of 8 bits.  Each pass is a per-tile histogram, an
 // exclusive scan of the digit-major histogram table (which yields every
 // tile's output offset per digit), and a stable scatter that ranks the
-// tile's keys with warp match/popc.  Stability plus the index payload
+// tile's keys with warp match/popc and writes them digit by digit.  Stability plus the index payload
 // starting at 0..n-1 makes the order identical to sorting by (key, index).
 #include <utility>
 
@@ -47,6 +47,13 @@ __global__ void __launch_bounds__(SORT_BLOCK) k_hist(const uint64_t *__restrict_
     hist[(int64_t)threadIdx.x * nb + blockIdx.x] = cnt[threadIdx.x];
 }
 
+// Stable scatter of one tile, in two halves of 2048 pairs.  Each warp owns
+// a contiguous run of 256 pairs of the half and ranks them by digit with
+// match_any against warp-private digit counts; a scan over the digits then
+// gives every pair its place in a digit-sorted copy of the half in shared
+// memory, from which the pairs of each digit are written to global memory
+// as one contiguous run (instead of one scattered store per pair).  Warps
+// own consecutive positions, so the order within a digit is the input order.
 __global__ void __launch_bounds__(SORT_BLOCK) k_scatter(const uint64_t *__restrict__ kin,
                                                         const uint32_t *__restrict__ vin,
                                                         uint64_t *__restrict__ kout,
@@ -54,42 +61,81 @@ __global__ void __launch_bounds__(SORT_BLOCK) k_scatter(const uint64_t *__restri
                                                         int shift,
                                                         const uint32_t *__restrict__ offs,
                                                         int nb) {
-    __shared__ uint32_t base[256];
-    __shared__ uint32_t wcnt[SORT_WARPS][256];
-    const int tid = threadIdx.x, warp = tid >> 5;
-    base[tid] = offs[(int64_t)tid * nb + blockIdx.x];
-    const int64_t tile = (int64_t)blockIdx.x * SORT_TILE;
+    constexpr int HALF = SORT_TILE / 2;
+    constexpr int PER_WARP = HALF / SORT_WARPS;
+    constexpr int ROUNDS = PER_WARP / 32;
+    __shared__ uint64_t sk[HALF];
+    __shared__ uint32_t sv[HALF];
+    __shared__ uint32_t wh[SORT_WARPS][256];
+    __shared__ uint32_t gbase[256], lstart[256], wsum[SORT_WARPS];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t lt = lanemask_lt();
-    for (int r = 0; r < SORT_IPT; ++r) {
-        int64_t i = tile + r * SORT_BLOCK + tid;
-        bool valid = i < n;
-        uint64_t k = valid ? kin[i] : 0ull;
-        uint32_t v = valid ? vin[i] : 0u;
-        uint32_t d = valid ? (uint32_t)(k >> shift) & 255u : 256u;
+    gbase[tid] = offs[(int64_t)tid * nb + blockIdx.x];
+    for (int h = 0; h < 2; ++h) {
+        const int64_t h0 = (int64_t)blockIdx.x * SORT_TILE + (int64_t)h * HALF;
 #pragma unroll
-        for (int w = 0; w < SORT_WARPS; ++w) wcnt[w][tid] = 0u;
+        for (int w = 0; w < SORT_WARPS; ++w) wh[w][tid] = 0u;
         __syncthreads();
-        uint32_t peers = __match_any_sync(0xffffffffu, d);
-        uint32_t rank = __popc(peers & lt);
-        if (valid && rank == 0u) wcnt[warp][d] = __popc(peers);
-        __syncthreads();
-        {
-            uint32_t run = base[tid];
+        uint64_t key[ROUNDS];
+        uint32_t val[ROUNDS], dg[ROUNDS], rk[ROUNDS];
 #pragma unroll
-            for (int w = 0; w < SORT_WARPS; ++w) {
-                uint32_t c = wcnt[w][tid];
-                wcnt[w][tid] = run;
-                run += c;
+        for (int r = 0; r < ROUNDS; ++r) {
+            const int64_t i = h0 + warp * PER_WARP + r * 32 + lane;
+            const bool valid = i < n;
+            key[r] = valid ? kin[i] : 0ull;
+            val[r] = valid ? vin[i] : 0u;
+            const uint32_t d = valid ? (uint32_t)(key[r] >> shift) & 255u : 256u;
+            dg[r] = d;
+            const uint32_t peers = __match_any_sync(0xffffffffu, d);
+            const uint32_t prev = d < 256u ? wh[warp][d] : 0u;
+            rk[r] = prev + __popc(peers & lt);
+            __syncwarp();
+            if (d < 256u && (peers & lt) == 0u) wh[warp][d] = prev + __popc(peers);
+            __syncwarp();
+        }
+        __syncthreads();
+        // digit tid: offsets of the warps' runs, and the half's count
+        uint32_t cnt = 0;
+#pragma unroll
+        for (int w = 0; w < SORT_WARPS; ++w) {
+            const uint32_t c = wh[w][tid];
+            wh[w][tid] = cnt;
+            cnt += c;
+        }
+        // exclusive scan of the counts over the 256 digits
+        uint32_t inc = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += t;
+        }
+        if (lane == 31) wsum[warp] = inc;
+        __syncthreads();
+        uint32_t add = 0;
+        for (int w = 0; w < warp; ++w) add += wsum[w];
+        lstart[tid] = add + inc - cnt;
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < ROUNDS; ++r) {
+            const uint32_t d = dg[r];
+            if (d < 256u) {
+                const uint32_t p = lstart[d] + wh[warp][d] + rk[r];
+                sk[p] = key[r];
+                sv[p] = val[r];
             }
-            base[tid] = run;
         }
         __syncthreads();
-        if (valid) {
-            uint32_t dst = wcnt[warp][d] + rank;
+        const int64_t left = n - h0;
+        const int nh = left <= 0 ? 0 : (left < HALF ? (int)left : HALF);
+        for (int p = tid; p < nh; p += SORT_BLOCK) {
+            const uint64_t k = sk[p];
+            const uint32_t d = (uint32_t)(k >> shift) & 255u;
+            const uint32_t dst = gbase[d] + ((uint32_t)p - lstart[d]);
             kout[dst] = k;
-            vout[dst] = v;
+            vout[dst] = sv[p];
         }
         __syncthreads();
+        gbase[tid] += cnt;
     }
 }
 
