@@ -302,6 +302,42 @@ def run_ours(args):
                   "what": "tree_direct_forces: FP32 pair terms, FP64 tile sums; tree_speedup_per_particle = "
                           "particles/s of the tree walk / particles/s of direct summation"}
 
+    # --- snapshot I/O and the on-the-fly face-on surface density (disk and
+    # bulge, 1024 x 1024 pixels over 30 x 30 kpc) ---
+    io = None
+    if not args.no_io:
+        import tempfile
+        with tempfile.TemporaryDirectory() as td:
+            path = os.path.join(td, f"snapshot{rank}.bin")
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            g.save(path, 0.0)
+            t1 = time.perf_counter()
+            gl = TreeGravity(G=m.G, theta=m.theta, eps=m.eps)
+            gl.load(path)
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            gl.close()
+            nbytes = os.path.getsize(path)
+        comp = [v for k, v in m.components.items() if k != "halo"]
+        first = min(c[0] for c in comp) if comp else 0
+        count = sum(c[1] for c in comp) if comp else n
+        window = (-15.0, 15.0, -15.0, 15.0)
+        g.surface_density(first, count, window, 1024, 1024)
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        g.surface_density(first, count, window, 1024, 1024)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        map_ms = s0.elapsed_time(s1)
+        io = {"snapshot_bytes": nbytes, "save_gb_per_s": nbytes / (t1 - t0) / 1e9,
+              "load_and_build_gb_per_s": nbytes / (t2 - t1) / 1e9,
+              "surface_density_ms": map_ms, "surface_density_particles": count,
+              "what": "tree_save_snapshot / tree_load_snapshot (includes the tree build) of the FP64 "
+                      "state to a local temporary file; tree_surface_density of disk + bulge, "
+                      "1024^2 pixels, CUDA events (includes the map clear and a stream sync)"}
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(m, args.cpu_groups)
@@ -323,7 +359,7 @@ def run_ours(args):
             "phase_ms": {"keys_sort": statistics.mean(keys_ms), "tree_groups_multipoles": statistics.mean(tree_ms),
                          "force": statistics.mean(force_ms), "walk_kernel": walk_avg},
             "energy": {"E_tot": diag["E_tot"] if diag else None},
-            "adjoint": adjoint, "direct": direct,
+            "adjoint": adjoint, "direct": direct, "io": io,
             "clocks": clk, "gpu_launches": int(launches), "roofline": roofline, "e2e": e2e,
             "cpu_baseline": cpu,
         }
@@ -400,6 +436,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward timing")
     ap.add_argument("--no-direct", action="store_true", help="skip the direct-summation comparison")
+    ap.add_argument("--no-io", action="store_true", help="skip the snapshot and surface-density timing")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per walk launch from an ncu capture (null when not captured)")
     args = ap.parse_args()

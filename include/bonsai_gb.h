@@ -45,6 +45,8 @@ extern "C" {
 #define BONSAI_EOVERFLOW (-3) /* a bounded walk buffer overflowed (device status word) */
 #define BONSAI_ECUDA (-4)     /* a CUDA runtime call failed */
 #define BONSAI_ESTATE (-5)    /* call out of order, e.g. forces before a tree was built */
+#define BONSAI_EIO (-6)       /* a snapshot file could not be opened, read or written, or
+                                 is not a snapshot of this format (size, magic, version) */
 
 typedef struct bonsai_ctx bonsai_ctx;
 
@@ -172,6 +174,40 @@ int bonsai_diagnostics(bonsai_ctx *ctx, double out[10]);
  * ECUDA. */
 int tree_direct_forces(bonsai_ctx *ctx, const int64_t *targets, int64_t nt, float eps,
                        double *acc, double *pot);
+
+/* ---- snapshots and on-the-fly analysis (Sec. VI.C, Sec. IV Fig. 4) ---- */
+
+/* tree_save_snapshot -- write the FP64 state of the context, in caller
+ * order, to the file at path (Sec. VI.C: snapshots serve restarting and
+ * analysis).  Format (little-endian): a 64-byte header {char magic[8] =
+ * "BONSAIGB", uint32 version = 1, uint32 flags = 0, int64 n, double time,
+ * double G, float theta, float eps, uint64 reserved[2]}, then pos [3][n],
+ * vel [3][n], mass [n] as float64.  time is the caller's simulation time,
+ * stored as given.  Streams through two 64 MB pinned staging buffers owned
+ * by the context.  Errors: EINVAL (null ctx or path), ESTATE (no tree),
+ * ENOMEM (staging), EIO, ECUDA. */
+int tree_save_snapshot(bonsai_ctx *ctx, const char *path, double time);
+
+/* tree_load_snapshot -- read a snapshot written by tree_save_snapshot into
+ * the context: builds the tree of its positions and sets its velocities
+ * (as tree_build followed by tree_set_velocities); *time (if non-NULL)
+ * receives the stored time.  The context's creation parameters are kept.
+ * Errors: EINVAL (null ctx or path, non-finite position or mass <= 0 in
+ * the file), EIO (missing, short or foreign file), ENOMEM, ECUDA. */
+int tree_load_snapshot(bonsai_ctx *ctx, const char *path, double *time);
+
+/* tree_surface_density -- face-on (x-y) surface density of the particles
+ * whose caller index is in [first, first + count) (for instance the disk
+ * and bulge of Fig. 4), on an nx x ny grid over window = {xmin, xmax,
+ * ymin, ymax}: each particle deposits m / (hx hy) onto the four pixel
+ * centres nearest to it with bilinear (cloud-in-cell) weights, hx = (xmax -
+ * xmin)/nx, hy = (ymax - ymin)/ny; deposits outside the grid are dropped.
+ * FP64 with atomic additions (the order of the additions varies).  map:
+ * device float64 [ny][nx], overwritten.  window: host double[4].
+ * Errors: EINVAL (null pointer, nx or ny < 1, an empty or non-finite
+ * window, a range outside [0, n)), ESTATE (no tree), ECUDA. */
+int tree_surface_density(bonsai_ctx *ctx, int64_t first, int64_t count, const double window[4],
+                         int nx, int ny, double *map);
 
 /* ---- adjoint (vector-Jacobian products) ------------------------------- */
 /* The paper has no adjoint.  These give the exact derivative of the forward

@@ -80,6 +80,7 @@ def _load():
             "orc_forces": (i32, [i64, P, P, i32, i32, f32, f64, f64, i32, P, P, P]),
             "orc_kdk": (i32, [i64, P, P, P, i32, f64, i32, i32, f32, f64, f64, i32, P, P, i32]),
             "orc_diagnostics": (None, [i64, P, P, P, P, P]),
+            "orc_surface_density": (None, [i64, P, P, i64, i64, P, ctypes.c_int, ctypes.c_int, P]),
             "orc_num_threads": (i32, []),
             "orc_eval_source": (None, [P, f64, P, f64, f64, P, P]),
             "orc_group_lists": (i32, [P, f32, i64, P, P, i64, P]),
@@ -421,6 +422,19 @@ def kdk(pos, vel, mass, nsteps: int, dt: float, theta: float, eps: float, G: flo
     if rc:
         raise MemoryError("oracle kdk failed")
     return pos, vel, acc, pot
+
+
+def surface_density(pos, mass, first: int, count: int, window, nx: int, ny: int):
+    """Face-on cloud-in-cell surface density of particles [first, first +
+    count) over window = (xmin, xmax, ymin, ymax); returns (ny, nx)."""
+    pos = _f64(pos)
+    n = pos.shape[1]
+    mass = _f64(mass, (n,))
+    w = np.ascontiguousarray(window, dtype=np.float64)
+    out = np.zeros((ny, nx))
+    _load().orc_surface_density(n, _p(pos), _p(mass), int(first), int(count), _p(w), int(nx), int(ny),
+                                _p(out))
+    return out
 
 
 def diagnostics(pos, vel, mass, pot):

@@ -815,6 +815,34 @@ void orc_diagnostics(int64_t n, const double *pos, const double *vel, const doub
     out[9] = Mt;
 }
 
+/* Face-on surface density (Sec. IV, Fig. 4: the disk and bulge seen from
+ * above), by cloud-in-cell deposition: particle i in [first, first+count)
+ * contributes m_i / (hx hy) times the bilinear weights of the four pixel
+ * centres around it, pixel (px, py) having its centre at
+ * (xmin + (px + 1/2) hx, ymin + (py + 1/2) hy); parts that fall outside the
+ * nx x ny grid are dropped.  window = {xmin, xmax, ymin, ymax};
+ * map[py * nx + px], zeroed here; particles in index order.              */
+void orc_surface_density(int64_t n, const double *pos, const double *mass, int64_t first,
+                         int64_t count, const double window[4], int nx, int ny, double *map) {
+    const double hx = (window[1] - window[0]) / nx, hy = (window[3] - window[2]) / ny;
+    for (int64_t k = 0; k < (int64_t)nx * ny; ++k) map[k] = 0.0;
+    for (int64_t i = first; i < first + count && i < n; ++i) {
+        double fx = (pos[i] - window[0]) / hx - 0.5;
+        double fy = (pos[n + i] - window[2]) / hy - 0.5;
+        if (!(fx > -1.0 && fx < (double)nx && fy > -1.0 && fy < (double)ny)) continue;
+        double ix = floor(fx), iy = floor(fy);
+        double tx = fx - ix, ty = fy - iy;
+        double w = mass[i] / (hx * hy);
+        for (int dy = 0; dy < 2; ++dy)
+            for (int dx = 0; dx < 2; ++dx) {
+                int px = (int)ix + dx, py = (int)iy + dy;
+                if (px < 0 || px >= nx || py < 0 || py >= ny) continue;
+                double wx = dx ? tx : 1.0 - tx, wy = dy ? ty : 1.0 - ty;
+                map[(int64_t)py * nx + px] += w * wx * wy;
+            }
+    }
+}
+
 int orc_num_threads(void) {
 #ifdef _OPENMP
     return omp_get_max_threads();

@@ -24,6 +24,7 @@ BONSAI_ENOMEM = -2
 BONSAI_EOVERFLOW = -3
 BONSAI_ECUDA = -4
 BONSAI_ESTATE = -5
+BONSAI_EIO = -6
 
 # every symbol include/bonsai_gb.h declares
 EXPORTED = (
@@ -33,6 +34,7 @@ EXPORTED = (
     "tree_debug_keys", "tree_debug_nodes", "tree_debug_multipoles", "tree_debug_groups",
     "bonsai_strerror", "bonsai_sfc_order_noalloc", "tree_forces_vjp", "tree_run", "tree_run_vjp",
     "tree_debug_set_frontier_capacity", "tree_forces_fp64", "tree_direct_forces",
+    "tree_save_snapshot", "tree_load_snapshot", "tree_surface_density",
 )
 
 BONSAI_NOALLOC_MAX_N = 1 << 20
@@ -99,6 +101,9 @@ def load(path: str | None = None):
             "tree_run_vjp": (i32, [P, P, P, P, P, P, P]),
             "tree_debug_set_frontier_capacity": (i32, [P, i32]),
             "tree_direct_forces": (i32, [P, P, i64, f32, P, P]),
+            "tree_save_snapshot": (i32, [P, ctypes.c_char_p, f64]),
+            "tree_load_snapshot": (i32, [P, ctypes.c_char_p, ctypes.POINTER(f64)]),
+            "tree_surface_density": (i32, [P, i64, i64, ctypes.POINTER(f64), i32, i32, P]),
             "tree_forces_fp64": (i32, [P, f32, f32, P, P]),
         }
         for name, (res, args) in sig.items():
@@ -202,6 +207,23 @@ def tree_direct_forces(ctx, targets, nt: int, eps: float, acc=None, pot=None) ->
     _check(load().tree_direct_forces(ctx, _ptr(targets, torch.int64, nt, "targets"), int(nt), float(eps),
                                      _ptr(acc, torch.float64, 3 * nt, "acc"),
                                      _ptr(pot, torch.float64, nt, "pot")), "tree_direct_forces")
+
+
+def tree_save_snapshot(ctx, path: str, time: float = 0.0) -> None:
+    _check(load().tree_save_snapshot(ctx, os.fsencode(path), float(time)), "tree_save_snapshot")
+
+
+def tree_load_snapshot(ctx, path: str) -> float:
+    t = ctypes.c_double()
+    _check(load().tree_load_snapshot(ctx, os.fsencode(path), ctypes.byref(t)), "tree_load_snapshot")
+    return t.value
+
+
+def tree_surface_density(ctx, first: int, count: int, window, nx: int, ny: int, out) -> None:
+    import torch
+    w = (ctypes.c_double * 4)(*[float(x) for x in window])
+    _check(load().tree_surface_density(ctx, int(first), int(count), w, int(nx), int(ny),
+                                       _ptr(out, torch.float64, nx * ny, "map")), "tree_surface_density")
 
 
 def tree_set_velocities(ctx, vel) -> None:

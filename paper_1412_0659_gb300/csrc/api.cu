@@ -47,7 +47,7 @@ template int ensure<BoxPartial>(DBuf<BoxPartial> &, size_t);
 
 using namespace bgb;
 
-namespace {
+namespace bgb {
 
 int particle_buffers(bonsai_ctx *c, int64_t n) {
     const size_t n3 = 3 * (size_t)n;
@@ -89,7 +89,12 @@ int rebuild(bonsai_ctx *c, const double *pos, const double *mass, bool from_call
     const double *p = from_caller ? pos : c->pos.p;
     const double *m = from_caller ? mass : c->mass.p;
     launch_bbox(c, p, m, n);
-    launch_keys(c, p, n);
+    if (from_caller) {
+        launch_keys(c, p, n);
+    } else {
+        if (ensure(c->inv_id, (size_t)n)) return BONSAI_ENOMEM;
+        launch_keys(c, p, n, c->id.p, c->inv_id.p);
+    }
     radix_sort_pairs(c, n);
     if (from_caller) launch_gather_build(c, pos, mass, n); else launch_gather_step(c, n);
     BGB_CUDA(cudaEventRecord(c->ev[1], c->stream));
@@ -162,7 +167,7 @@ int reverse_force_step(bonsai_ctx *c, double *xbar, double *mbar) {
     return BONSAI_OK;
 }
 
-}  // namespace
+}  // namespace bgb
 
 extern "C" {
 
@@ -203,6 +208,8 @@ void bonsai_destroy(bonsai_ctx *c) {
     release(c->val); release(c->val2); release(c->hist); release(c->scan_tmp);
     release(c->box_part); release(c->body_hi); release(c->body_lo);
     release(c->inv_id); release(c->dir_part);
+    for (int k = 0; k < 2; ++k)
+        if (c->stage[k]) cudaFreeHost(c->stage[k]);
     release(c->nd_first); release(c->nd_count); release(c->nd_child); release(c->nd_nchild);
     release(c->nd_level); release(c->nd_parent); release(c->nd_scan);
     release(c->nd_M); release(c->nd_com); release(c->nd_Q);
@@ -558,6 +565,7 @@ const char *bonsai_strerror(int code) {
         case BONSAI_EOVERFLOW: return "walk buffer overflow";
         case BONSAI_ECUDA: return "CUDA runtime error";
         case BONSAI_ESTATE: return "call out of order";
+        case BONSAI_EIO: return "snapshot file could not be opened, read or written, or has the wrong format";
         default: return "unknown status";
     }
 }

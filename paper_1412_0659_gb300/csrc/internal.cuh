@@ -140,6 +140,9 @@ struct bonsai_ctx {
     bgb::DBuf<uint32_t> inv_id;    // [n] caller index -> key-order slot
     bgb::DBuf<double> dir_part;    // [chunks][4][nt] partial sums
 
+    // pinned staging halves of the snapshot transfers (allocated on first use)
+    void *stage[2] = {nullptr, nullptr};
+
     // timing events
     cudaEvent_t ev[10];
     bonsai_stats stats;
@@ -154,10 +157,19 @@ int ensure(DBuf<T> &b, size_t n);
 template <typename T>
 void release(DBuf<T> &b);
 
+// ---- context steps (api.cu) ----
+int particle_buffers(bonsai_ctx *c, int64_t n);
+// keys, sort, gather, octree, groups, multipoles, particle records;
+// from_caller: pos/mass are caller-order arrays, else the context's state
+int rebuild(bonsai_ctx *c, const double *pos, const double *mass, bool from_caller);
+
 // ---- launchers (one per kernel family) ----
 // keys.cu
 void launch_bbox(bonsai_ctx *c, const double *pos, const double *mass, int64_t n);
-void launch_keys(bonsai_ctx *c, const double *pos, int64_t n);
+// id non-null: pos is the key-ordered state with caller indices id; the
+// keys are written in caller order and inv receives the inverse of id
+void launch_keys(bonsai_ctx *c, const double *pos, int64_t n, const uint32_t *id = nullptr,
+                 uint32_t *inv = nullptr);
 // sort.cu
 void radix_sort_pairs(bonsai_ctx *c, int64_t n);  // sorts key/val in place (ping-pong inside)
 void exclusive_scan_u32(bonsai_ctx *c, const uint32_t *in, uint32_t *out, int64_t n,

@@ -177,17 +177,25 @@ __device__ __forceinline__ uint64_t ph_key(uint32_t x0, uint32_t x1, uint32_t x2
 
 namespace {
 
+// Keys of the particles at pos.  With id (the caller index of each slot of
+// a key-ordered state), key and payload go to the caller index, so that the
+// stable sort breaks ties by caller index as the order rule asks, and
+// inv[caller index] = slot records where each particle was.
 __global__ void __launch_bounds__(256) k_keys(const double *__restrict__ pos, int64_t n,
                                               const DevScalars *__restrict__ sc,
                                               uint64_t *__restrict__ key,
-                                              uint32_t *__restrict__ val) {
+                                              uint32_t *__restrict__ val,
+                                              const uint32_t *__restrict__ id,
+                                              uint32_t *__restrict__ inv) {
     const double lo0 = sc->lo[0], lo1 = sc->lo[1], lo2 = sc->lo[2], s = sc->scale;
     for (int64_t i = blockIdx.x * 256ll + threadIdx.x; i < n; i += (int64_t)gridDim.x * 256) {
         uint32_t q0 = quantise(pos[i], lo0, s);
         uint32_t q1 = quantise(pos[n + i], lo1, s);
         uint32_t q2 = quantise(pos[2 * n + i], lo2, s);
-        key[i] = ph_key(q0, q1, q2);
-        val[i] = (uint32_t)i;
+        const uint32_t o = id ? id[i] : (uint32_t)i;
+        key[o] = ph_key(q0, q1, q2);
+        val[o] = o;
+        if (id) inv[o] = (uint32_t)i;
     }
 }
 
@@ -209,13 +217,13 @@ int launch_cube_keys_into(cudaStream_t s, int sm_count, const double *pos, const
     const int nb = grid_for(n, BOX_BLOCK * 4, cap);
     k_box_partial<<<nb, BOX_BLOCK, 0, s>>>(pos, mass, n, part);
     k_box_final<<<1, BOX_BLOCK, 0, s>>>(part, nb, dsc);
-    k_keys<<<grid_for(n, 256, sm_count * 16), 256, 0, s>>>(pos, n, dsc, key, val);
+    k_keys<<<grid_for(n, 256, sm_count * 16), 256, 0, s>>>(pos, n, dsc, key, val, nullptr, nullptr);
     return 3;
 }
 
-void launch_keys(bonsai_ctx *c, const double *pos, int64_t n) {
+void launch_keys(bonsai_ctx *c, const double *pos, int64_t n, const uint32_t *id, uint32_t *inv) {
     k_keys<<<grid_for(n, 256, c->sm_count * 16), 256, 0, c->stream>>>(pos, n, c->dsc, c->key.p,
-                                                                       c->val.p);
+                                                                       c->val.p, id, inv);
     c->launches += 1;
 }
 

@@ -226,20 +226,23 @@ __global__ void __launch_bounds__(256) k_gather_build(const double *__restrict__
     }
 }
 
+// Re-sort of the context's state: perm holds the caller index of each new
+// slot, inv the old slot of each caller index.
 __global__ void __launch_bounds__(256) k_gather_step(
     const double *__restrict__ pos_o, const double *__restrict__ vel_o,
-    const double *__restrict__ mass_o, const uint32_t *__restrict__ id_o,
+    const double *__restrict__ mass_o, const uint32_t *__restrict__ inv,
     const uint32_t *__restrict__ perm, int64_t n, double *__restrict__ pos,
     double *__restrict__ vel, double *__restrict__ mass, uint32_t *__restrict__ id) {
     for (int64_t i = blockIdx.x * 256ll + threadIdx.x; i < n; i += (int64_t)gridDim.x * 256) {
-        uint32_t j = perm[i];
+        const uint32_t c = perm[i];
+        const uint32_t j = inv[c];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             pos[d * n + i] = pos_o[d * n + j];
             vel[d * n + i] = vel_o[d * n + j];
         }
         mass[i] = mass_o[j];
-        id[i] = id_o[j];
+        id[i] = c;
     }
 }
 
@@ -308,7 +311,7 @@ void launch_gather_build(bonsai_ctx *c, const double *pos, const double *mass, i
 
 void launch_gather_step(bonsai_ctx *c, int64_t n) {
     k_gather_step<<<grid_for(n, 256, c->sm_count * 16), 256, 0, c->stream>>>(
-        c->pos.p, c->vel.p, c->mass.p, c->id.p, c->val.p, n, c->pos2.p, c->vel2.p, c->mass2.p,
+        c->pos.p, c->vel.p, c->mass.p, c->inv_id.p, c->val.p, n, c->pos2.p, c->vel2.p, c->mass2.p,
         c->id2.p);
     c->launches += 1;
     std::swap(c->pos, c->pos2);

@@ -82,6 +82,26 @@ class TreeGravity:
         capi.tree_direct_forces(self.ctx, targets, nt, eps, acc, pot)
         return acc, pot
 
+    def save(self, path: str, time: float = 0.0):
+        """Write the FP64 state (caller order) to a snapshot file."""
+        capi.tree_save_snapshot(self.ctx, path, time)
+
+    def load(self, path: str) -> float:
+        """Read a snapshot into this context (tree built, velocities set);
+        returns its stored time."""
+        t = capi.tree_load_snapshot(self.ctx, path)
+        self.n = self.stats()["n"]
+        return t
+
+    def surface_density(self, first: int, count: int, window, nx: int, ny: int) -> torch.Tensor:
+        """Face-on cloud-in-cell surface density of caller indices
+        [first, first + count) over window = (xmin, xmax, ymin, ymax);
+        (ny, nx) float64."""
+        dev = torch.device("cuda", torch.cuda.current_device())
+        out = torch.empty((ny, nx), dtype=torch.float64, device=dev)
+        capi.tree_surface_density(self.ctx, first, count, window, nx, ny, out)
+        return out
+
     def set_velocities(self, vel: torch.Tensor):
         capi.tree_set_velocities(self.ctx, vel)
 
