@@ -63,6 +63,9 @@ def _load():
             "orc_hilbert_key": (ctypes.c_uint64, [ctypes.c_uint32] * 3 + [i32]),
             "orc_bounding_cube": (None, [i64, P, P, P, P, P]),
             "orc_tree_build": (P, [i64, P, P, i32, i32]),
+            "orc_tree_build_cube": (P, [i64, P, P, i32, i32, P, f64]),
+            "orc_let_mark": (i32, [P, P, f32, P, P]),
+            "orc_cross_forces": (i32, [P, P, f32, f64, f64, P, P, P, P, P]),
             "orc_tree_free": (None, [P]),
             "orc_tree_num_nodes": (i64, [P]),
             "orc_tree_num_groups": (i64, [P]),
@@ -135,13 +138,21 @@ class Tree:
     """Steps 1-6 of the tree method (keys, sort, octree, groups, multipoles)
     built from caller-order positions ``(3, N)`` and masses ``(N,)``."""
 
-    def __init__(self, pos: np.ndarray, mass: np.ndarray, nleaf: int = NLEAF, ncrit: int = NCRIT):
+    def __init__(self, pos: np.ndarray, mass: np.ndarray, nleaf: int = NLEAF, ncrit: int = NCRIT,
+                 cube=None):
+        """cube = (lo (3,), L): build in that cube (a branch of a global
+        octree) instead of the particles' own bounding cube."""
         self._lib = _load()
         self.pos = _f64(pos)
         self.n = self.pos.shape[1]
         self.mass = _f64(mass, (self.n,))
         self.nleaf, self.ncrit = nleaf, ncrit
-        h = self._lib.orc_tree_build(self.n, _p(self.pos), _p(self.mass), nleaf, ncrit)
+        if cube is None:
+            h = self._lib.orc_tree_build(self.n, _p(self.pos), _p(self.mass), nleaf, ncrit)
+        else:
+            lo = np.ascontiguousarray(cube[0], dtype=np.float64)
+            h = self._lib.orc_tree_build_cube(self.n, _p(self.pos), _p(self.mass), nleaf, ncrit, _p(lo),
+                                              float(cube[1]))
         if not h:
             raise MemoryError("oracle tree build failed")
         self._h = ctypes.c_void_p(h)
@@ -153,6 +164,29 @@ class Tree:
         if h is not None and self._lib is not None:
             self._lib.orc_tree_free(h)
             self._h = None
+
+    def let_mark(self, dst: "Tree", theta: float):
+        """(visited, opened) flags of this tree's cells for the walks of
+        dst's groups (the local essential tree this tree sends to dst)."""
+        v = np.zeros(self.nnodes, np.uint8)
+        o = np.zeros(self.nnodes, np.uint8)
+        if self._lib.orc_let_mark(self._h, dst._h, float(theta), _p(v), _p(o)):
+            raise MemoryError("let mark failed")
+        return v.astype(bool), o.astype(bool)
+
+    def cross_forces(self, dst: "Tree", theta: float, eps: float, G: float = 1.0):
+        """Forces of this tree's particles on dst's particles through dst's
+        group walks over this tree: (acc (3, n_dst), pot (n_dst,)) in dst's
+        caller order, per-group (n_pp, n_pc) of dst's groups, total counts."""
+        acc = np.zeros((3, dst.n))
+        pot = np.zeros(dst.n)
+        g_npp = np.zeros(dst.ngroups, np.int64)
+        g_npc = np.zeros(dst.ngroups, np.int64)
+        counts = np.zeros(2, np.uint64)
+        if self._lib.orc_cross_forces(self._h, dst._h, float(theta), float(eps), float(G), _p(acc), _p(pot),
+                                      _p(g_npp), _p(g_npc), _p(counts)):
+            raise MemoryError("cross forces failed")
+        return dst.to_caller(acc), dst.to_caller(pot), g_npp, g_npc, (int(counts[0]), int(counts[1]))
 
     def cube(self):
         lo = np.zeros(3)

@@ -367,15 +367,24 @@ void orc_tree_free(orc_tree *t) {
 
 /* Steps 1-6: bounding cube, keys, sort, octree, groups, multipoles.
  * Positions are caller-order SoA [3][n]; nothing is kept from the caller. */
-orc_tree *orc_tree_build(int64_t n, const double *pos, const double *mass, int nleaf,
-                         int ncrit) {
+/* Steps 1-6 with the cube given (lo, L), or the bounding cube if lo is
+ * NULL.  A given cube makes the trees of several particle subsets branches
+ * of one global octree (Sec. III.B.1: the global bounding box maps every
+ * process's coordinates to global PH keys).                               */
+static orc_tree *orc_tree_build_in(int64_t n, const double *pos, const double *mass, int nleaf,
+                                   int ncrit, const double *lo, double L) {
     if (n <= 0 || nleaf < 1 || ncrit < 1) return NULL;
     orc_tree *t = (orc_tree *)calloc(1, sizeof(orc_tree));
     if (!t) return NULL;
     t->n = n;
     t->nleaf = nleaf;
     t->ncrit = ncrit;
-    orc_bounding_cube(n, pos, pos + n, pos + 2 * n, t->lo, &t->L);
+    if (lo) {
+        for (int d = 0; d < 3; ++d) t->lo[d] = lo[d];
+        t->L = L;
+    } else {
+        orc_bounding_cube(n, pos, pos + n, pos + 2 * n, t->lo, &t->L);
+    }
     t->scale = 0x1p21 / t->L;
     orc_pair *pairs = (orc_pair *)malloc((size_t)n * sizeof(orc_pair));
     uint32_t *qc = (uint32_t *)malloc((size_t)n * 3 * sizeof(uint32_t));
@@ -418,6 +427,17 @@ orc_tree *orc_tree_build(int64_t n, const double *pos, const double *mass, int n
     if (!t->M || !t->com || !t->Q || !t->centre || !t->side) { orc_tree_free(t); return NULL; }
     orc_multipoles(t);
     return t;
+}
+
+orc_tree *orc_tree_build(int64_t n, const double *pos, const double *mass, int nleaf,
+                         int ncrit) {
+    return orc_tree_build_in(n, pos, mass, nleaf, ncrit, NULL, 0.0);
+}
+
+orc_tree *orc_tree_build_cube(int64_t n, const double *pos, const double *mass, int nleaf,
+                              int ncrit, const double lo[3], double L) {
+    if (!(L > 0.0)) return NULL;
+    return orc_tree_build_in(n, pos, mass, nleaf, ncrit, lo, L);
 }
 
 /* ---- accessors (copy out) ---------------------------------------------- */
@@ -676,6 +696,116 @@ int orc_tree_forces_list(const orc_tree *t, float theta, double eps, double G, i
                 }
                 pot[i] = G * phi;
                 for (int d = 0; d < 3; ++d) acc[(size_t)d * n + i] = G * a[d];
+            }
+        }
+        free(L.pc);
+        free(L.pp);
+    }
+    if (counts) {
+        counts[0] = npp_tot;
+        counts[1] = npc_tot;
+    }
+    free(com_f); free(ropen2_f); free(gcf); free(ghf);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Local essential trees (Sec. III.B.2): the part of a process's tree that
+ * a remote process needs is what the remote groups' walks visit in it.   */
+/* ------------------------------------------------------------------------ */
+
+/* Marks, for every group of dst, the walk of src's tree with that group's
+ * box: visited[c] = 1 for every cell the walk reaches, opened[c] = 1 for
+ * every cell it opens (an internal cell's children are visited, a leaf's
+ * particles become p-p sources).  Visited cells that no group opens are
+ * used whole.                                                              */
+int orc_let_mark(const orc_tree *src, const orc_tree *dst, float theta, uint8_t *visited,
+                 uint8_t *opened) {
+    int64_t nn = src->nnodes, ng = dst->ngroups;
+    float *com_f = (float *)malloc((size_t)nn * 3 * sizeof(float));
+    float *ropen2_f = (float *)malloc((size_t)nn * sizeof(float));
+    float *gcf = (float *)malloc((size_t)ng * 3 * sizeof(float));
+    float *ghf = (float *)malloc((size_t)ng * 3 * sizeof(float));
+    uint32_t *stack = (uint32_t *)malloc(((size_t)ORC_MAX_LEVEL * 8 + 16) * sizeof(uint32_t));
+    if (!com_f || !ropen2_f || !gcf || !ghf || !stack) {
+        free(com_f); free(ropen2_f); free(gcf); free(ghf); free(stack);
+        return -1;
+    }
+    orc_cell_mac(src, theta, com_f, ropen2_f);
+    orc_group_box_f32(dst, gcf, ghf);
+    memset(visited, 0, (size_t)nn);
+    memset(opened, 0, (size_t)nn);
+    for (int64_t g = 0; g < ng; ++g) {
+        float gc[3] = {gcf[g], gcf[(size_t)ng + g], gcf[2 * (size_t)ng + g]};
+        float gh[3] = {ghf[g], ghf[(size_t)ng + g], ghf[2 * (size_t)ng + g]};
+        int sp = 0;
+        stack[sp++] = 0;
+        while (sp > 0) {
+            uint32_t c = stack[--sp];
+            visited[c] = 1;
+            float cf[3] = {com_f[c], com_f[(size_t)nn + c], com_f[2 * (size_t)nn + c]};
+            if (!orc_mac_open(cf, ropen2_f[c], gc, gh)) continue;
+            opened[c] = 1;
+            for (int k = (int)src->nchild[c] - 1; k >= 0; --k) stack[sp++] = src->child[c] + (uint32_t)k;
+        }
+    }
+    free(com_f); free(ropen2_f); free(gcf); free(ghf); free(stack);
+    return 0;
+}
+
+/* The force of src's particles on dst's particles through the walks of
+ * dst's groups over src's tree (Eq. 1-2, FP64, without self pairs: the two
+ * particle sets are disjoint).  acc [3][dst n], pot [dst n] in dst's sorted
+ * order (overwritten); per-group list lengths; counts as for the tree.   */
+int orc_cross_forces(const orc_tree *src, const orc_tree *dst, float theta, double eps, double G,
+                     double *acc, double *pot, int64_t *g_npp, int64_t *g_npc, uint64_t counts[2]) {
+    int64_t ns = src->n, nd = dst->n, nn = src->nnodes, ng = dst->ngroups;
+    float *com_f = (float *)malloc((size_t)nn * 3 * sizeof(float));
+    float *ropen2_f = (float *)malloc((size_t)nn * sizeof(float));
+    float *gcf = (float *)malloc((size_t)ng * 3 * sizeof(float));
+    float *ghf = (float *)malloc((size_t)ng * 3 * sizeof(float));
+    if (!com_f || !ropen2_f || !gcf || !ghf) {
+        free(com_f); free(ropen2_f); free(gcf); free(ghf);
+        return -1;
+    }
+    orc_cell_mac(src, theta, com_f, ropen2_f);
+    orc_group_box_f32(dst, gcf, ghf);
+    double eps2 = eps * eps;
+    uint64_t npp_tot = 0, npc_tot = 0;
+#pragma omp parallel reduction(+ : npp_tot, npc_tot)
+    {
+        orc_lists L;
+        memset(&L, 0, sizeof(L));
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t g = 0; g < ng; ++g) {
+            float gc[3] = {gcf[g], gcf[(size_t)ng + g], gcf[2 * (size_t)ng + g]};
+            float gh[3] = {ghf[g], ghf[(size_t)ng + g], ghf[2 * (size_t)ng + g]};
+            orc_walk_group(src, com_f, ropen2_f, gc, gh, &L);
+            uint32_t f = dst->gfirst[g], c = dst->gcount[g];
+            if (g_npp) g_npp[g] = L.npp;
+            if (g_npc) g_npc[g] = L.npc;
+            npp_tot += (uint64_t)c * (uint64_t)L.npp;
+            npc_tot += (uint64_t)c * (uint64_t)L.npc;
+            for (uint32_t i = f; i < f + c; ++i) {
+                double xi[3] = {dst->x[i], dst->x[(size_t)nd + i], dst->x[2 * (size_t)nd + i]};
+                double phi = 0.0, a[3] = {0.0, 0.0, 0.0};
+                for (int64_t k = 0; k < L.npc; ++k) {
+                    uint32_t cc = L.pc[k];
+                    double r[3], Qc[6];
+                    for (int d = 0; d < 3; ++d) r[d] = src->com[(size_t)d * nn + cc] - xi[d];
+                    for (int q = 0; q < 6; ++q) Qc[q] = src->Q[(size_t)q * nn + cc];
+                    orc_eq12(r, src->M[cc], Qc, eps2, &phi, a);
+                }
+                for (int64_t k = 0; k < L.npp_leaves; ++k) {
+                    uint32_t lf = L.pp[k];
+                    for (uint32_t j = src->first[lf]; j < src->first[lf] + src->count[lf]; ++j) {
+                        double r[3];
+                        for (int d = 0; d < 3; ++d) r[d] = src->x[(size_t)d * ns + j] - xi[d];
+                        orc_eq12(r, src->m[j], NULL, eps2, &phi, a);
+                    }
+                }
+                pot[i] = G * phi;
+                for (int d = 0; d < 3; ++d) acc[(size_t)d * nd + i] = G * a[d];
             }
         }
         free(L.pc);
