@@ -49,6 +49,7 @@ extern "C" {
                                  is not a snapshot of this format (size, magic, version) */
 
 typedef struct bonsai_ctx bonsai_ctx;
+typedef struct bonsai_let bonsai_let;
 
 /* Parameters fixed at creation.  nleaf and ncrit must be 16 and 64: the
  * leaf size of Sec. I.A and the walk-group size; other values are EINVAL. */
@@ -174,6 +175,66 @@ int bonsai_diagnostics(bonsai_ctx *ctx, double out[10]);
  * ECUDA. */
 int tree_direct_forces(bonsai_ctx *ctx, const int64_t *targets, int64_t nt, float eps,
                        double *acc, double *pot);
+
+/* ---- domains and local essential trees (Sec. III.B), on one GPU ------- */
+/* The paper's processes each hold a piece of the global Peano-Hilbert
+ * order, build their tree as a branch of the global octree, and send each
+ * remote process the local essential tree (LET) it needs.  Here one context
+ * stands for one process; the exchange is a device copy. */
+
+/* tree_build_cube -- tree_build with the keys taken in the given cube
+ * (cube = {lo_x, lo_y, lo_z, L}, host) instead of the particles' own
+ * bounding cube, so that the trees of several domains are branches of one
+ * global octree (Sec. III.B.1: the global bounding box maps every
+ * process's coordinates to global PH keys).  Later tree_step calls keep the
+ * cube.  Positions outside the cube are clamped to its edge cells.
+ * Errors: as tree_build, and EINVAL for a non-finite cube or L <= 0. */
+int tree_build_cube(bonsai_ctx *ctx, const double *pos, const double *mass, int64_t n,
+                    const double cube[4]);
+
+/* tree_domain_state -- copy the particles in key-order slots [first,
+ * first + count) of the context's state out: pos, vel device float64
+ * [3][count], mass [count], caller_id device uint32 [count] (the caller
+ * index of each); any may be NULL.  With first = r n / R this is domain r of
+ * R equal pieces of the Peano-Hilbert order (Sec. III.B.1).
+ * Errors: EINVAL (bad range), ESTATE (no tree), ECUDA. */
+int tree_domain_state(bonsai_ctx *ctx, int64_t first, int64_t count, double *pos, double *vel,
+                      double *mass, uint32_t *caller_id);
+
+/* A local essential tree: created empty, filled by let_build, read by
+ * let_forces; owns its device arrays (the data a process sends).  stream:
+ * a cudaStream_t for its kernels.  Errors: EINVAL, ENOMEM, ECUDA. */
+int let_create(bonsai_let **out, void *stream);
+void let_destroy(bonsai_let *let);
+
+/* let_build -- the part of src's tree that dst's groups need (Sec. III.B.2):
+ * src's tree is walked with the box of every group of dst (the opening test
+ * of tree_forces at this theta); every cell reached is kept, an opened cell
+ * with all its children, an opened leaf with its particles, a cell no group
+ * opens as a leaf without particles.  Walking the LET with dst's groups
+ * gives exactly the interaction lists of walking all of src's tree.  src
+ * and dst must have been built with tree_build_cube in the same cube.
+ * Errors: EINVAL (null, theta <= 0, different cubes), ESTATE (no tree),
+ * EOVERFLOW (a marking walk's frontier overflowed), ENOMEM, ECUDA. */
+int let_build(bonsai_let *let, bonsai_ctx *src, const bonsai_ctx *dst, float theta);
+
+/* LET size: out = {cells, particles, bytes of its records, cells of the
+ * source tree}.  Errors: EINVAL. */
+int let_get_info(const bonsai_let *let, int64_t out[4]);
+
+/* For tests: the source cell of each LET cell and its kind (0 used whole,
+ * 1 opened cell, 2 opened leaf), device uint32 [cells] each; either may be
+ * NULL.  Errors: EINVAL, ESTATE (empty LET), ECUDA. */
+int let_debug_cells(const bonsai_let *let, uint32_t *src_node, uint32_t *kind);
+
+/* let_forces -- add the force of the LET's sources on dst's particles to
+ * dst's current forces (those of its last tree_forces; read the sum with
+ * tree_get_forces): dst's groups walk the LET like a local tree (Sec.
+ * III.B.2: imported structures are processed separately as they arrive),
+ * FP32 as tree_forces, no self pairs.  The per-group list lengths and the
+ * counts of tree_get_stats become this walk's.
+ * Errors: EINVAL, ESTATE (dst has no forces, empty LET), EOVERFLOW, ECUDA. */
+int let_forces(bonsai_ctx *dst, const bonsai_let *let, float eps);
 
 /* ---- snapshots and on-the-fly analysis (Sec. VI.C, Sec. IV Fig. 4) ---- */
 

@@ -35,6 +35,8 @@ EXPORTED = (
     "bonsai_strerror", "bonsai_sfc_order_noalloc", "tree_forces_vjp", "tree_run", "tree_run_vjp",
     "tree_debug_set_frontier_capacity", "tree_forces_fp64", "tree_direct_forces",
     "tree_save_snapshot", "tree_load_snapshot", "tree_surface_density",
+    "tree_build_cube", "tree_domain_state", "let_create", "let_destroy", "let_build", "let_get_info",
+    "let_debug_cells", "let_forces",
 )
 
 BONSAI_NOALLOC_MAX_N = 1 << 20
@@ -102,6 +104,14 @@ def load(path: str | None = None):
             "tree_debug_set_frontier_capacity": (i32, [P, i32]),
             "tree_direct_forces": (i32, [P, P, i64, f32, P, P]),
             "tree_save_snapshot": (i32, [P, ctypes.c_char_p, f64]),
+            "tree_build_cube": (i32, [P, P, P, i64, ctypes.POINTER(f64)]),
+            "tree_domain_state": (i32, [P, i64, i64, P, P, P, P]),
+            "let_create": (i32, [ctypes.POINTER(P), P]),
+            "let_destroy": (None, [P]),
+            "let_build": (i32, [P, P, P, f32]),
+            "let_get_info": (i32, [P, ctypes.POINTER(i64)]),
+            "let_debug_cells": (i32, [P, P, P]),
+            "let_forces": (i32, [P, P, f32]),
             "tree_load_snapshot": (i32, [P, ctypes.c_char_p, ctypes.POINTER(f64)]),
             "tree_surface_density": (i32, [P, i64, i64, ctypes.POINTER(f64), i32, i32, P]),
             "tree_forces_fp64": (i32, [P, f32, f32, P, P]),
@@ -207,6 +217,53 @@ def tree_direct_forces(ctx, targets, nt: int, eps: float, acc=None, pot=None) ->
     _check(load().tree_direct_forces(ctx, _ptr(targets, torch.int64, nt, "targets"), int(nt), float(eps),
                                      _ptr(acc, torch.float64, 3 * nt, "acc"),
                                      _ptr(pot, torch.float64, nt, "pot")), "tree_direct_forces")
+
+
+def tree_build_cube(ctx, pos, mass, cube) -> None:
+    import torch
+    n = int(mass.numel())
+    c = (ctypes.c_double * 4)(*[float(x) for x in cube])
+    _check(load().tree_build_cube(ctx, _ptr(pos, torch.float64, 3 * n, "pos"), _ptr(mass, torch.float64, n, "mass"),
+                                  n, c), "tree_build_cube")
+
+
+def tree_domain_state(ctx, first: int, count: int, pos=None, vel=None, mass=None, caller_id=None) -> None:
+    import torch
+    _check(load().tree_domain_state(ctx, int(first), int(count), _ptr(pos, torch.float64, 3 * count, "pos"),
+                                    _ptr(vel, torch.float64, 3 * count, "vel"),
+                                    _ptr(mass, torch.float64, count, "mass"),
+                                    _ptr(caller_id, torch.int32, count, "caller_id")), "tree_domain_state")
+
+
+def let_create(stream=None):
+    h = ctypes.c_void_p()
+    s = None if stream is None else ctypes.c_void_p(int(stream))
+    _check(load().let_create(ctypes.byref(h), s), "let_create")
+    return h
+
+
+def let_destroy(let) -> None:
+    load().let_destroy(let)
+
+
+def let_build(let, src, dst, theta: float) -> None:
+    _check(load().let_build(let, src, dst, float(theta)), "let_build")
+
+
+def let_get_info(let) -> dict:
+    out = (ctypes.c_int64 * 4)()
+    _check(load().let_get_info(let, out), "let_get_info")
+    return {"cells": out[0], "particles": out[1], "bytes": out[2], "source_cells": out[3]}
+
+
+def let_debug_cells(let, src_node=None, kind=None) -> None:
+    import torch
+    _check(load().let_debug_cells(let, _ptr(src_node, torch.int32, None, "src_node"),
+                                  _ptr(kind, torch.int32, None, "kind")), "let_debug_cells")
+
+
+def let_forces(dst, let, eps: float) -> None:
+    _check(load().let_forces(dst, let, float(eps)), "let_forces")
 
 
 def tree_save_snapshot(ctx, path: str, time: float = 0.0) -> None:

@@ -42,6 +42,10 @@ template int ensure<uint64_t>(DBuf<uint64_t> &, size_t);
 template int ensure<float4>(DBuf<float4> &, size_t);
 template int ensure<uint2>(DBuf<uint2> &, size_t);
 template int ensure<BoxPartial>(DBuf<BoxPartial> &, size_t);
+template void release<float4>(DBuf<float4> &);
+template void release<uint2>(DBuf<uint2> &);
+template void release<uint32_t>(DBuf<uint32_t> &);
+template void release<int32_t>(DBuf<int32_t> &);
 
 }  // namespace bgb
 
@@ -88,7 +92,8 @@ int rebuild(bonsai_ctx *c, const double *pos, const double *mass, bool from_call
     BGB_CUDA(cudaEventRecord(c->ev[0], c->stream));
     const double *p = from_caller ? pos : c->pos.p;
     const double *m = from_caller ? mass : c->mass.p;
-    launch_bbox(c, p, m, n);
+    launch_bbox(c, p, m, n);  // also checks the input
+    if (c->fixed_cube) launch_set_cube(c);
     if (from_caller) {
         launch_keys(c, p, n);
     } else {
@@ -111,6 +116,10 @@ int rebuild(bonsai_ctx *c, const double *pos, const double *mass, bool from_call
     if (c->hsc->status & ST_BAD_INPUT) {
         c->have_tree = false;
         return BONSAI_EINVAL;
+    }
+    if (!c->fixed_cube) {
+        for (int d = 0; d < 3; ++d) c->cube[d] = c->hsc->lo[d];
+        c->cube[3] = c->hsc->L;
     }
     cudaEventElapsedTime(&c->stats.ms_keys, c->ev[0], c->ev[1]);
     cudaEventElapsedTime(&c->stats.ms_tree, c->ev[1], c->ev[2]);
@@ -233,8 +242,26 @@ int bonsai_set_stream(bonsai_ctx *c, void *stream) {
     return BONSAI_OK;
 }
 
+static int build_common(bonsai_ctx *c, const double *pos, const double *mass, int64_t n);
+
 int tree_build(bonsai_ctx *c, const double *pos, const double *mass, int64_t n) {
     if (!c || !pos || !mass || n < 1 || n > 0x7fffffffll) return BONSAI_EINVAL;
+    c->fixed_cube = false;
+    return build_common(c, pos, mass, n);
+}
+
+int tree_build_cube(bonsai_ctx *c, const double *pos, const double *mass, int64_t n,
+                    const double cube[4]) {
+    if (!c || !pos || !mass || !cube || n < 1 || n > 0x7fffffffll) return BONSAI_EINVAL;
+    for (int k = 0; k < 4; ++k)
+        if (!isfinite(cube[k])) return BONSAI_EINVAL;
+    if (!(cube[3] > 0.0)) return BONSAI_EINVAL;
+    for (int k = 0; k < 4; ++k) c->cube[k] = cube[k];
+    c->fixed_cube = true;
+    return build_common(c, pos, mass, n);
+}
+
+static int build_common(bonsai_ctx *c, const double *pos, const double *mass, int64_t n) {
     c->have_tree = c->have_forces = c->have_vel = false;
     c->n = n;
     int rc = particle_buffers(c, n);

@@ -65,6 +65,8 @@ struct bonsai_ctx {
     bool have_tree = false;
     bool have_forces = false;  // acc/pot in sorted order are valid
     bool have_vel = false;
+    bool fixed_cube = false;         // keys in a given cube (a branch of a global octree)
+    double cube[4] = {0, 0, 0, 0};   // lo[3], L of the current tree
     float packed_theta = -1.0f;  // theta of the current cell pack
 
     // particle state in key-sorted order (double buffers for the re-sort)
@@ -166,6 +168,8 @@ int rebuild(bonsai_ctx *c, const double *pos, const double *mass, bool from_call
 // ---- launchers (one per kernel family) ----
 // keys.cu
 void launch_bbox(bonsai_ctx *c, const double *pos, const double *mass, int64_t n);
+// let.cu: overwrite the bounding cube with c->cube (keys in a given cube)
+void launch_set_cube(bonsai_ctx *c);
 // id non-null: pos is the key-ordered state with caller indices id; the
 // keys are written in caller order and inv receives the inverse of id
 void launch_keys(bonsai_ctx *c, const double *pos, int64_t n, const uint32_t *id = nullptr,
@@ -183,7 +187,16 @@ void launch_multipoles(bonsai_ctx *c);
 void launch_body_pack(bonsai_ctx *c);
 void launch_cell_pack(bonsai_ctx *c, float theta);
 // walk.cu
+// A tree given by its walk records (a local essential tree, let.cu).
+struct LetTree {
+    const float4 *mac;
+    const uint2 *topo;
+    const float4 *ca, *cb, *cc;
+    const float4 *hi, *lo;  // particle records of the opened leaves
+    int64_t nn;
+};
 int walk_force(bonsai_ctx *c, float theta, float eps, float *acc_caller, float *pot_caller);
+int walk_let(bonsai_ctx *dst, const LetTree &t, float eps);
 int walk_force_fp64(bonsai_ctx *c, float eps, double *acc, double *pot);
 // direct.cu
 int direct_forces(bonsai_ctx *c, const int64_t *targets, int64_t nt, float eps, double *acc,
@@ -213,6 +226,23 @@ int launch_cube_keys_into(cudaStream_t s, int sm_count, const double *pos, const
                           uint64_t *key, uint32_t *val);
 int radix_sort_pairs_into(cudaStream_t s, int64_t n, uint64_t *ka, uint64_t *kb, uint32_t *va,
                           uint32_t *vb, uint32_t *hist, uint32_t *tmp);
+
+// Exclusive scan on explicit buffers (in and out must not alias; tmp holds
+// scan_tmp_elems(n) entries); *total_dev receives the sum.  Returns the
+// number of kernels launched.
+int exclusive_scan_into(cudaStream_t s, const uint32_t *in, uint32_t *out, int64_t n,
+                        uint32_t *tmp, uint32_t *total_dev);
+
+// The opening test of Sec. I.A on FP32 records: m = {com_hi, r_open^2}, the
+// group box centre and (rounded-up) half-size; the squared distance from the
+// com to the box is formed with round-to-nearest in this fixed order.
+__device__ __forceinline__ bool mac_open(float4 m, float4 box, float4 half) {
+    const float dx = fmaxf(__fsub_rn(fabsf(__fsub_rn(m.x, box.x)), half.x), 0.0f);
+    const float dy = fmaxf(__fsub_rn(fabsf(__fsub_rn(m.y, box.y)), half.y), 0.0f);
+    const float dz = fmaxf(__fsub_rn(fabsf(__fsub_rn(m.z, box.z)), half.z), 0.0f);
+    const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+    return d2 < m.w;
+}
 
 inline int grid_for(int64_t n, int block, int max_blocks = 1 << 30) {
     int64_t g = (n + block - 1) / block;

@@ -257,6 +257,16 @@ void exclusive_scan_u32(bonsai_ctx *c, const uint32_t *in, uint32_t *out, int64_
     }
 }
 
+int exclusive_scan_into(cudaStream_t s, const uint32_t *in, uint32_t *out, int64_t n,
+                        uint32_t *tmp, uint32_t *total_dev) {
+    int launches = n > 0 ? scan_rec(s, in, out, n, tmp) : 0;
+    if (total_dev) {
+        k_scan_total<<<1, 1, 0, s>>>(in, out, n, total_dev);
+        launches += 1;
+    }
+    return launches;
+}
+
 size_t scan_tmp_elems(int64_t n) {
     size_t t = 0;
     int64_t m = n;

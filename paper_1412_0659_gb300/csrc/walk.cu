@@ -57,7 +57,8 @@ struct WalkArgs {
     const float4 *mac;
     const uint2 *topo;
     const float4 *ca, *cb, *cc;
-    const float4 *body_hi, *body_lo;
+    const float4 *body_hi, *body_lo;  // targets (the groups' particles)
+    const float4 *src_hi, *src_lo;    // p-p sources (the tree's particles)
     const uint32_t *gfirst, *gcount;
     const float4 *gbox, *ghalf, *glo;
     int64_t ngroups;
@@ -69,6 +70,7 @@ struct WalkArgs {
     float *pot;    // sorted [n]
     float *acc_c;  // caller order [3][n] or null
     float *pot_c;  // caller order [n] or null
+    int accumulate;  // add to acc/pot instead of writing them
     const uint32_t *id;
     int32_t *gnpp, *gnpc;
     // adjoint inputs / outputs (sorted order)
@@ -182,12 +184,15 @@ __device__ __forceinline__ float sum_copies(float v, int lane, int T2, int S) {
     return r;
 }
 
-// MASK: skip the self pair inside the p-p loop (needed when eps = 0, or when
-// theta >= 1/sqrt(3) so that a target's own leaf may be accepted as a cell).
-// Otherwise every target meets itself exactly once in its p-p list: for
-// theta < 1/sqrt(3) a cell containing the group is always opened (the
-// distance from its com to the group box is at most sqrt(3) l < l/theta),
-// and the self term is removed after the loop.
+// Self pairs.  SELF_MASK: skip the self pair inside the p-p loop (needed when
+// eps = 0, or when theta >= 1/sqrt(3) so that a target's own leaf may be
+// accepted as a cell).  SELF_SUB: every target meets itself exactly once in
+// its p-p list: for theta < 1/sqrt(3) a cell containing the group is always
+// opened (the distance from its com to the group box is at most
+// sqrt(3) l < l/theta), and the self term is removed after the loop.
+// SELF_NONE: targets and sources are disjoint sets (a remote domain's
+// local essential tree).
+constexpr int SELF_SUB = 0, SELF_MASK = 1, SELF_NONE = 2;
 // Ring appends of the FP32 policies: a cell's com relative to the group
 // centre is (com_hi - c_hi) + (com_lo - c_lo), each difference rounded once,
 // so the FP32 record is accurate relative to the separation.
@@ -204,14 +209,14 @@ struct Fp32Rings {
     }
     __device__ __forceinline__ void append_particle(const WalkArgs &A, WarpLists &L, uint32_t s,
                                                     uint32_t j, float4 box, float4 clo, uint32_t) {
-        const float4 h = A.body_hi[j], l = A.body_lo[j];
+        const float4 h = A.src_hi[j], l = A.src_lo[j];
         L.pp[s] = make_float4((h.x - box.x) + (l.x - clo.x), (h.y - box.y) + (l.y - clo.y),
                               (h.z - box.z) + (l.z - clo.z), h.w);
         L.pid[s] = (int)j;
     }
 };
 
-template <bool MASK>
+template <int SELF>
 struct ForwardPolicy : Fp32Rings {
     int T2, S, cp, tl, j0;
     Targets t;
@@ -262,8 +267,8 @@ struct ForwardPolicy : Fp32Rings {
             const int sid = L.pid[j];
 #pragma unroll
             for (int k = 0; k < 2; ++k)
-                pp_one<MASK>(p, sid, t.id[k], t.x[k], t.y[k], t.z[k], eps2, t.ax[k], t.ay[k],
-                             t.az[k], t.ph[k]);
+                pp_one<SELF == SELF_MASK>(p, sid, t.id[k], t.x[k], t.y[k], t.z[k], eps2, t.ax[k],
+                                          t.ay[k], t.az[k], t.ph[k]);
         }
     }
 
@@ -274,11 +279,18 @@ struct ForwardPolicy : Fp32Rings {
             const float ay = A.G * sum_copies(t.ay[k], lane, T2, S);
             const float az = A.G * sum_copies(t.az[k], lane, T2, S);
             float phs = sum_copies(t.ph[k], lane, T2, S);
-            if (!MASK) phs = phs + self[k] * rsqrtf(eps2);  // remove the self pair
+            if (SELF == SELF_SUB) phs = phs + self[k] * rsqrtf(eps2);  // remove the self pair
             const float ph = A.G * phs;
             const uint32_t li = (uint32_t)(tl + k * T2);
             if (cp == 0 && li < gc) {
                 const int64_t i = gf + li;
+                if (A.accumulate) {
+                    A.acc[i] += ax;
+                    A.acc[A.n + i] += ay;
+                    A.acc[2 * A.n + i] += az;
+                    A.pot[i] += ph;
+                    continue;
+                }
                 A.acc[i] = ax;
                 A.acc[A.n + i] = ay;
                 A.acc[2 * A.n + i] = az;
@@ -629,8 +641,8 @@ struct AdjointPolicy : Fp32Rings {
 // Forward and adjoint policies take the lane for their flushes differently.
 template <class P>
 __device__ __forceinline__ void do_flush_pc(P &pol, const WarpLists &L, int hb, int cnt, int lane);
-template <bool MASK>
-__device__ __forceinline__ void do_flush_pc(ForwardPolicy<MASK> &pol, const WarpLists &L, int hb,
+template <int SELF>
+__device__ __forceinline__ void do_flush_pc(ForwardPolicy<SELF> &pol, const WarpLists &L, int hb,
                                             int cnt, int) {
     pol.flush_pc(L, hb, cnt);
 }
@@ -639,8 +651,8 @@ __device__ __forceinline__ void do_flush_pc(AdjointPolicy &pol, const WarpLists 
     if (cnt >= 32) pol.flush_pc<true>(L, hb, 32, lane);
     else if (cnt > 0) pol.flush_pc<false>(L, hb, cnt, lane);
 }
-template <bool MASK>
-__device__ __forceinline__ void do_flush_pp(ForwardPolicy<MASK> &pol, const WarpLists &L, int hb,
+template <int SELF>
+__device__ __forceinline__ void do_flush_pp(ForwardPolicy<SELF> &pol, const WarpLists &L, int hb,
                                             int cnt, int) {
     pol.flush_pp(L, hb, cnt);
 }
@@ -810,13 +822,7 @@ __device__ __forceinline__ void walk_group(const WalkArgs &A, LT &L, WarpTargets
             const uint32_t node = valid ? cur[idx] : 0u;
             const float4 m = A.mac[node];
             const uint2 tp = A.topo[node];
-            // opening test: squared distance from com to the group box
-            float dx = fmaxf(__fsub_rn(fabsf(__fsub_rn(m.x, box.x)), half.x), 0.0f);
-            float dy = fmaxf(__fsub_rn(fabsf(__fsub_rn(m.y, box.y)), half.y), 0.0f);
-            float dz = fmaxf(__fsub_rn(fabsf(__fsub_rn(m.z, box.z)), half.z), 0.0f);
-            const float d2 =
-                __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-            const bool open = d2 < m.w;
+            const bool open = mac_open(m, box, half);  // Sec. I.A opening test
             const bool leaf = (tp.y & LEAF_FLAG) != 0u;
             const bool accept = valid && !open;
 
@@ -909,7 +915,7 @@ __device__ __forceinline__ void walk_group(const WalkArgs &A, LT &L, WarpTargets
     __syncwarp();
 }
 
-template <bool MASK>
+template <int SELF>
 __global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(const WalkArgs A) {
     __shared__ WarpLists lists[WALK_WARPS];
     const int lane = threadIdx.x & 31;
@@ -923,7 +929,7 @@ __global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(const WalkArgs A) {
         if (lane == 0) g = atomicAdd(&A.sc->group_counter, 1u);
         g = __shfl_sync(0xffffffffu, g, 0);
         if (g >= A.ngroups) break;
-        ForwardPolicy<MASK> pol;
+        ForwardPolicy<SELF> pol;
         walk_group(A, lists[wib], nullptr, pol, g, fa, fb, lane, lt);
     }
 }
@@ -978,6 +984,9 @@ void fill_args(bonsai_ctx *c, float eps, WalkArgs &a) {
     a.cc = c->cell_c.p;
     a.body_hi = c->body_hi.p;
     a.body_lo = c->body_lo.p;
+    a.src_hi = c->body_hi.p;
+    a.src_lo = c->body_lo.p;
+    a.accumulate = 0;
     a.gfirst = c->grp_first.p;
     a.gcount = c->grp_count.p;
     a.gbox = c->grp_box.p;
@@ -1018,10 +1027,10 @@ void fill_args(bonsai_ctx *c, float eps, WalkArgs &a) {
 
 int walk_resident_warps(bonsai_ctx *c) {
     int a = 0, b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_walk<true>, WALK_WARPS * 32, 0) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_walk<SELF_MASK>, WALK_WARPS * 32, 0) !=
             cudaSuccess || a < 1)
         a = 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_walk<false>, WALK_WARPS * 32, 0) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_walk<SELF_SUB>, WALK_WARPS * 32, 0) !=
             cudaSuccess || b < 1)
         b = 1;
     int d = 0;
@@ -1052,11 +1061,35 @@ int walk_force(bonsai_ctx *c, float theta, float eps, float *acc_c, float *pot_c
     a.pot_c = pot_c;
     cudaEventRecord(c->ev[8], c->stream);
     if (mask_self)
-        k_walk<true><<<launch_blocks((const void *)k_walk<true>, c), WALK_WARPS * 32, 0, c->stream>>>(a);
+        k_walk<SELF_MASK><<<launch_blocks((const void *)k_walk<SELF_MASK>, c), WALK_WARPS * 32, 0,
+                            c->stream>>>(a);
     else
-        k_walk<false><<<launch_blocks((const void *)k_walk<false>, c), WALK_WARPS * 32, 0, c->stream>>>(a);
+        k_walk<SELF_SUB><<<launch_blocks((const void *)k_walk<SELF_SUB>, c), WALK_WARPS * 32, 0,
+                           c->stream>>>(a);
     cudaEventRecord(c->ev[9], c->stream);
     c->launches += 1;
+    return cudaPeekAtLastError() == cudaSuccess ? BONSAI_OK : BONSAI_ECUDA;
+}
+
+// The walk of dst's groups over a local essential tree (cell records, leaf
+// particle records); the forces are added to dst's key-order acc / pot.
+int walk_let(bonsai_ctx *dst, const LetTree &t, float eps) {
+    WalkArgs a;
+    fill_args(dst, eps, a);
+    a.mac = t.mac;
+    a.topo = t.topo;
+    a.ca = t.ca;
+    a.cb = t.cb;
+    a.cc = t.cc;
+    a.src_hi = t.hi;
+    a.src_lo = t.lo;
+    a.nn = t.nn;
+    a.accumulate = 1;
+    cudaEventRecord(dst->ev[8], dst->stream);
+    k_walk<SELF_NONE><<<launch_blocks((const void *)k_walk<SELF_NONE>, dst), WALK_WARPS * 32, 0,
+                        dst->stream>>>(a);
+    cudaEventRecord(dst->ev[9], dst->stream);
+    dst->launches += 1;
     return cudaPeekAtLastError() == cudaSuccess ? BONSAI_OK : BONSAI_ECUDA;
 }
 

@@ -48,6 +48,29 @@ class TreeGravity:
         self.n = int(mass.numel())
         return self
 
+    def build_cube(self, pos: torch.Tensor, mass: torch.Tensor, cube):
+        """Build with the keys taken in cube = (lo_x, lo_y, lo_z, L): the tree
+        is then a branch of the octree of that cube."""
+        capi.tree_build_cube(self.ctx, pos, mass, cube)
+        self.n = int(mass.numel())
+        return self
+
+    def cube(self):
+        """(lo_x, lo_y, lo_z, L) of the current tree."""
+        lo, L = capi.tree_debug_cube(self.ctx)
+        return (lo[0], lo[1], lo[2], L)
+
+    def domain_state(self, first: int, count: int):
+        """pos, vel (3, count), mass (count,) float64 and caller ids (count,)
+        int32 of key-order slots [first, first + count)."""
+        dev = torch.device("cuda", torch.cuda.current_device())
+        pos = torch.empty((3, count), dtype=torch.float64, device=dev)
+        vel = torch.empty((3, count), dtype=torch.float64, device=dev)
+        mass = torch.empty(count, dtype=torch.float64, device=dev)
+        ids = torch.empty(count, dtype=torch.int32, device=dev)
+        capi.tree_domain_state(self.ctx, first, count, pos, vel, mass, ids)
+        return pos, vel, mass, ids
+
     def forces(self, theta: float | None = None, eps: float | None = None, acc=None, pot=None):
         theta = self.theta if theta is None else theta
         eps = self.eps if eps is None else eps
