@@ -338,6 +338,47 @@ def run_ours(args):
                       "state to a local temporary file; tree_surface_density of disk + bulge, "
                       "1024^2 pixels, CUDA events (includes the map clear and a stream sync)"}
 
+    # --- domains and local essential trees (Sec. III.B) emulated on this GPU:
+    # the state split into R pieces of the key order, each domain's own walk
+    # plus the walks of the R - 1 LETs it receives ---
+    dom = None
+    if args.domains > 1:
+        from paper_1412_0659_gb300 import domains as dmod
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        doms = dmod.split(g, args.domains)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        let = dmod.Let()
+        own_ms, let_ms, let_build_s, dflops, nbytes = 0.0, 0.0, 0.0, 0.0, []
+        for i, (gi, _) in enumerate(doms):
+            gi.forces(m.theta, m.eps)
+            st = gi.stats()
+            own_ms += st["ms_walk"]
+            dflops += st["flops"]
+            for j, (gj, _) in enumerate(doms):
+                if j == i:
+                    continue
+                tb = time.perf_counter()
+                let.build(gj, gi, m.theta)
+                let_build_s += time.perf_counter() - tb
+                nbytes.append(let.info()["bytes"])
+                let.add_forces(gi, m.eps)
+                st = gi.stats()
+                let_ms += st["ms_walk"]
+                dflops += st["flops"]
+        let.close()
+        for gi, _ in doms:
+            gi.close()
+        dom = {"domains": args.domains, "split_and_build_s": t1 - t0, "own_walks_ms": own_ms,
+               "let_walks_ms": let_ms, "let_build_s": let_build_s, "let_bytes_total": int(sum(nbytes)),
+               "let_bytes_max_pair": int(max(nbytes)),
+               "walk_tflops": dflops / ((own_ms + let_ms) * 1e-3) / 1e12,
+               "flops_vs_single_tree": dflops / (flops / args.steps),
+               "what": "domains.split + tree_build_cube per domain; tree_forces (own walk) and, per "
+                       "source domain, let_build (host-timed, includes its syncs) and let_forces "
+                       "(CUDA events of the walk); flops in the 23/65 convention"}
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(m, args.cpu_groups)
@@ -359,7 +400,7 @@ def run_ours(args):
             "phase_ms": {"keys_sort": statistics.mean(keys_ms), "tree_groups_multipoles": statistics.mean(tree_ms),
                          "force": statistics.mean(force_ms), "walk_kernel": walk_avg},
             "energy": {"E_tot": diag["E_tot"] if diag else None},
-            "adjoint": adjoint, "direct": direct, "io": io,
+            "adjoint": adjoint, "direct": direct, "io": io, "domains": dom,
             "clocks": clk, "gpu_launches": int(launches), "roofline": roofline, "e2e": e2e,
             "cpu_baseline": cpu,
         }
@@ -437,6 +478,8 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward timing")
     ap.add_argument("--no-direct", action="store_true", help="skip the direct-summation comparison")
     ap.add_argument("--no-io", action="store_true", help="skip the snapshot and surface-density timing")
+    ap.add_argument("--domains", type=int, default=8,
+                    help="domains of the local-essential-tree emulation (0 or 1 to skip)")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per walk launch from an ncu capture (null when not captured)")
     args = ap.parse_args()
