@@ -35,8 +35,8 @@ if ROOT not in sys.path:
 # DRAM bytes (read + written) of one walk/force launch, from a one-pass ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum) of the benchmark
 # command, valid only for the walk source it was taken on (checked by hash).
-WALK_TRAFFIC = {"walk_cu_sha256": "461cc5599d412fcfc07e62b904694bfc35580991d946751c257a70b74d0e2f28",
-                "bytes": {"milky-way-2^23": 708.41e6 + 277.75e6}}
+WALK_TRAFFIC = {"walk_cu_sha256": "f8c8e6681dae7afc62ba27b659f83e600aa3f6300bf302a8af06ae249d8ecc24",
+                "bytes": {"milky-way-2^23": 708.41e6 + 276.85e6}}
 
 METRIC = "tree-force Tflop/s (23 flops/p-p + 65 flops/p-c, Sec. VI.A) per full KDK step, theta=0.4"
 UNIT = "Tflop/s"
