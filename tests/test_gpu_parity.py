@@ -122,6 +122,35 @@ def test_tiny_and_degenerate_inputs():
         gpu["g"].close()
 
 
+def test_all_particles_at_one_point():
+    """Degenerate input: 200 coincident particles (L = 1, equal keys, one
+    max-depth leaf cut into groups of 64): a = 0 exactly and
+    phi = -G (n - 1) m / eps, the oracle's closed form."""
+    from gpu_helpers import gpu_run
+    n, m, eps, G = 200, 0.5, 0.02, 2.0
+    pos = np.tile(np.array([[0.3], [-1.2], [4.0]]), (1, n))
+    gpu = gpu_run(pos, np.full(n, m), eps=eps, G=G)
+    assert gpu["L"] == 1.0
+    assert np.all(gpu["acc"] == 0.0)
+    assert np.allclose(gpu["pot"], -G * (n - 1) * m / eps, rtol=1e-6)
+    assert (gpu["stats"]["n_pp"], gpu["stats"]["n_pc"]) == (n * n, 0)
+    assert np.array_equal(gpu["group_count"], [64, 64, 64, 8])
+    gpu["g"].close()
+
+
+def test_empty_input_is_rejected():
+    import torch
+
+    from gpu_helpers import DEV
+    from paper_1412_0659_gb300 import TreeGravity, capi
+    g = TreeGravity()
+    with pytest.raises(capi.BonsaiError) as e:
+        g.build(torch.zeros((3, 0), dtype=torch.float64, device=DEV),
+                torch.zeros(0, dtype=torch.float64, device=DEV))
+    assert e.value.code == capi.BONSAI_EINVAL
+    g.close()
+
+
 def test_zero_softening_distinct_particles():
     from gpu_helpers import assert_force_tolerance, gpu_run, oracle_tree
     m = workloads.plummer(5000, seed=12)

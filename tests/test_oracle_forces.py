@@ -194,3 +194,17 @@ def test_interaction_counts_are_consistent(orc):
         for c in leaves:
             in_leaf[nd["first"][c]:nd["first"][c] + nd["count"][c]] = True
         assert in_leaf[own].all()
+
+
+def test_all_particles_at_one_point(orc):
+    """Degenerate input: n coincident particles.  The cube falls back to
+    L = 1, all keys are equal, the one max-depth leaf is cut into groups of
+    64; every pair has r = 0, so a = 0 exactly and phi = -G (n - 1) m / eps."""
+    n, m, eps, G = 200, 0.5, 0.02, 2.0
+    pos = np.tile(np.array([[0.3], [-1.2], [4.0]]), (1, n))
+    t = orc.Tree(pos, np.full(n, m))
+    assert t.cube()[1] == 1.0
+    acc, pot, (npp, npc) = t.forces(0.4, eps, G)
+    assert np.all(acc == 0.0)
+    assert np.allclose(pot, -G * (n - 1) * m / eps, rtol=1e-14)
+    assert (npp, npc) == (n * n, 0)
