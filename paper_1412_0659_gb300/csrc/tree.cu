@@ -10,9 +10,10 @@
 // pure function of the sorted keys.  The host reads one count per level to
 // size the next launch.
 //
-// The upward pass visits levels bottom-up.  Leaves sum their particles and
-// internal nodes combine their children by the parallel-axis rule, every
-// FP64 operation an explicit round-to-nearest intrinsic in a fixed order.
+// The upward pass computes every leaf in one launch (a leaf needs only its
+// particles), then visits the levels bottom-up, where internal nodes
+// combine their children by the parallel-axis rule; every FP64 operation is
+// an explicit round-to-nearest intrinsic in a fixed order.
 #include <math.h>
 
 #include <algorithm>
@@ -125,7 +126,11 @@ __global__ void k_mark_leaves(const uint32_t *__restrict__ first, const uint32_t
 }
 
 // ---- upward pass (FP64) ----
-// Q order: xx, yy, zz, xy, xz, yz.
+// Q order: xx, yy, zz, xy, xz, yz.  LEAVES: one launch over all nodes that
+// computes the leaves (they depend on nothing); otherwise one launch per
+// level, bottom-up, that combines the children of the level's internal
+// nodes.
+template <bool LEAVES>
 __global__ void __launch_bounds__(128) k_multipoles(
     const double *__restrict__ pos, const double *__restrict__ mass, int64_t n,
     const uint32_t *__restrict__ first, const uint32_t *__restrict__ count,
@@ -134,6 +139,7 @@ __global__ void __launch_bounds__(128) k_multipoles(
     int64_t t = blockIdx.x * 128ll + threadIdx.x;
     if (t >= m) return;
     int64_t i = s + t;
+    if ((nchild[i] == 0) != LEAVES) return;
     double Ms = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
     double q0 = 0.0, q1 = 0.0, q2 = 0.0, q3 = 0.0, q4 = 0.0, q5 = 0.0;
     double cx, cy, cz;
@@ -474,10 +480,14 @@ int build_groups(bonsai_ctx *c) {
 
 void launch_multipoles(bonsai_ctx *c) {
     const int64_t nn = c->n_nodes;
-    for (int l = c->depth; l >= 0; --l) {
+    k_multipoles<true><<<grid_for(nn, 128), 128, 0, c->stream>>>(
+        c->pos.p, c->mass.p, c->n, c->nd_first.p, c->nd_count.p, c->nd_child.p, c->nd_nchild.p,
+        c->nd_M.p, c->nd_com.p, c->nd_Q.p, nn, 0, nn);
+    c->launches += 1;
+    for (int l = c->depth - 1; l >= 0; --l) {  // the deepest level holds leaves only
         const int64_t s = c->level_start[l], m = c->level_start[l + 1] - s;
         if (m <= 0) continue;
-        k_multipoles<<<grid_for(m, 128), 128, 0, c->stream>>>(
+        k_multipoles<false><<<grid_for(m, 128), 128, 0, c->stream>>>(
             c->pos.p, c->mass.p, c->n, c->nd_first.p, c->nd_count.p, c->nd_child.p,
             c->nd_nchild.p, c->nd_M.p, c->nd_com.p, c->nd_Q.p, nn, s, m);
         c->launches += 1;
