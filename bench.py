@@ -150,6 +150,15 @@ def _workload(name: str, rank: int):
     elif name == "milky-way-2^20":
         m = workloads.milky_way(1 << 20, seed=1002 + 17 * rank, eps=0.01, theta=0.4, dt=0.1)
         desc = "Milky-Way-like N=2^20 (same profiles as the 2^23 model), theta=0.4, eps=10 pc, dt=0.1 Myr"
+    elif name == "milky-way-2^25":
+        m = workloads.milky_way(1 << 25, seed=1003 + 17 * rank, eps=0.01, theta=0.4, dt=0.1)
+        desc = "Milky-Way-like N=2^25 (the precision-study model), theta=0.4, eps=10 pc, dt=0.1 Myr"
+    elif name == "milky-way-2^28":
+        m = workloads.milky_way(1 << 28, seed=1005 + 17 * rank, eps=0.005, theta=0.4, dt=0.1)
+        desc = "Milky-Way-like N=2^28 (the largest single-GPU model), theta=0.4, eps=5 pc, dt=0.1 Myr"
+    elif name == "halo-disk-2^20":
+        m = workloads.halo_disk(1 << 19, 1 << 19, seed=1004 + 17 * rank, eps=0.02, dt=0.1)
+        desc = "Plummer halo 2^19 (1e11 Msun, a=10 kpc) + exponential disk 2^19, theta=0.4, eps=20 pc"
     elif name == "plummer-2^14":
         m = workloads.plummer(1 << 14, seed=1001 + 17 * rank)
         desc = "Plummer N=2^14, G=M=a=1, theta=0.4, eps=0.01, dt=1/64"
@@ -471,7 +480,9 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="milky-way-2^23", choices=["milky-way-2^23", "milky-way-2^20", "plummer-2^14"])
+    ap.add_argument("--workload", default="milky-way-2^23",
+                    choices=["milky-way-2^23", "milky-way-2^20", "milky-way-2^25", "milky-way-2^28",
+                             "halo-disk-2^20", "plummer-2^14"])
     ap.add_argument("--cpu-groups", type=int, default=24000,
                     help="groups walked by the CPU oracle sample (about 10 s of CPU work at 2^23)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
