@@ -449,9 +449,12 @@ __device__ __forceinline__ TargetPair load_targets(const WarpTargets *T, int p) 
 }
 
 // Per-warp scratch of the adjoint: a 32 x 24 transpose buffer for the target
-// gradients of a chunk of 8 targets, and the running target gradients.
+// gradients of a chunk of 8 targets, and the running target gradients.  A
+// lane's row holds, per target pair tp, {gx, gy, gz} as packed pairs
+// (x0 x1 y0 y1 z0 z1 at 6 tp); 26-float rows make the 8-byte row stores of a
+// half-warp and the column reads conflict-free.
 constexpr int ADJ_CHUNK = 8;
-constexpr int ADJ_ROW = 3 * ADJ_CHUNK + 4;  // 28 floats: row stores and column sums conflict-free
+constexpr int ADJ_ROW = 3 * ADJ_CHUNK + 2;
 struct __align__(16) WarpAdjoint {
     float red[32 * ADJ_ROW];
     float tacc[NCRIT * 3];
@@ -510,19 +513,24 @@ struct AdjointPolicy : Fp32Rings {
         __syncwarp();
     }
 
-    // add the 8 targets' gradients held in part (this lane's row) to tacc
-    __device__ __forceinline__ void reduce_chunk(const float part[3 * ADJ_CHUNK], int t0, int lane) {
-        float4 *row = reinterpret_cast<float4 *>(&W->red[lane * ADJ_ROW]);
-#pragma unroll
-        for (int k = 0; k < 3 * ADJ_CHUNK / 4; ++k)
-            row[k] = make_float4(part[4 * k], part[4 * k + 1], part[4 * k + 2], part[4 * k + 3]);
+    // this lane's gradients of target pair tp of the chunk into its row
+    __device__ __forceinline__ void put_pair(int tp, f32x2 gx, f32x2 gy, f32x2 gz, int lane) {
+        f32x2 *row = reinterpret_cast<f32x2 *>(&W->red[lane * ADJ_ROW + 6 * tp]);
+        row[0] = gx;
+        row[1] = gy;
+        row[2] = gz;
+    }
+
+    // add the chunk's target gradients (all rows) to tacc: column c is
+    // component (c % 6) / 2 of target t0 + 2 (c / 6) + (c & 1)
+    __device__ __forceinline__ void reduce_chunk(int t0, int lane) {
         __syncwarp();
         if (lane < 3 * ADJ_CHUNK) {
             float s = 0.0f;
 #pragma unroll 8
             for (int r = 0; r < 32; ++r) s += W->red[r * ADJ_ROW + lane];
-            const int t = t0 + lane / 3;
-            if (t < gc) W->tacc[3 * t0 + lane] += s;
+            const int t = t0 + 2 * (lane / 6) + (lane & 1);
+            if (t < gc) W->tacc[3 * t + (lane % 6) / 2] += s;
         }
         __syncwarp();
     }
@@ -546,7 +554,6 @@ struct AdjointPolicy : Fp32Rings {
         f32x2 ax = 0ull, ay = 0ull, az = 0ull, aM = 0ull, aP = 0ull;
         f32x2 dxx = 0ull, dyy = 0ull, dzz = 0ull, oxy = 0ull, oxz = 0ull, oyz = 0ull;
         for (int t0 = 0; t0 < gc; t0 += ADJ_CHUNK) {
-            float part[3 * ADJ_CHUNK];
 #pragma unroll
             for (int tp = 0; tp < ADJ_CHUNK / 2; ++tp) {
                 const TargetPair T2 = load_targets(T, (t0 >> 1) + tp);
@@ -563,11 +570,9 @@ struct AdjointPolicy : Fp32Rings {
                 oxy = fma2(rx, vy, fma2(ry, vx, oxy));
                 oxz = fma2(rx, vz, fma2(rz, vx, oxz));
                 oyz = fma2(ry, vz, fma2(rz, vy, oyz));
-                u2(gx, part[6 * tp], part[6 * tp + 3]);
-                u2(gy, part[6 * tp + 1], part[6 * tp + 4]);
-                u2(gz, part[6 * tp + 2], part[6 * tp + 5]);
+                put_pair(tp, gx, gy, gz, lane);
             }
-            reduce_chunk(part, t0, lane);
+            reduce_chunk(t0, lane);
         }
         if (v) {
             // gQ = P0 I + (r v^T + v r^T) with v2 = 2v accumulated:
@@ -604,7 +609,6 @@ struct AdjointPolicy : Fp32Rings {
         const f32x2 e2 = dup2(eps2);
         f32x2 ax = 0ull, ay = 0ull, az = 0ull, am = 0ull;
         for (int t0 = 0; t0 < gc; t0 += ADJ_CHUNK) {
-            float part[3 * ADJ_CHUNK];
 #pragma unroll
             for (int tp = 0; tp < ADJ_CHUNK / 2; ++tp) {
                 const TargetPair T2 = load_targets(T, (t0 >> 1) + tp);
@@ -614,11 +618,9 @@ struct AdjointPolicy : Fp32Rings {
                 ay = add2(ay, gy);
                 az = add2(az, gz);
                 am = add2(am, gm);
-                u2(gx, part[6 * tp], part[6 * tp + 3]);
-                u2(gy, part[6 * tp + 1], part[6 * tp + 4]);
-                u2(gz, part[6 * tp + 2], part[6 * tp + 5]);
+                put_pair(tp, gx, gy, gz, lane);
             }
-            reduce_chunk(part, t0, lane);
+            reduce_chunk(t0, lane);
         }
         if (v) atomicAdd(&part_adj[sid], make_float4(G * fold(ax), G * fold(ay), G * fold(az),
                                                      G * fold(am)));
