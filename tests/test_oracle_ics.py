@@ -1,0 +1,240 @@
+"""Pins of the oracle's on-the-fly galaxy initial conditions (Sec. IV: NFW
+halo, exponential disk, Hernquist bulge, generated on the fly).
+
+The generator's pieces are checked against what mathematics and published
+results fix, not against themselves: Philox4x32-10 against the known-answer
+vectors published with the generator (Salmon et al., SC11); Eddington's
+inversion against Hernquist's closed-form distribution function (Hernquist
+1990, Eq. 17); the distribution function against its own density (Eddington's
+defining integral) and against the isotropic Jeans equation; sampled radii,
+heights and speeds against their distributions; the virial theorem for a
+sampled halo (forces by direct summation); Freeman's disk rotation against
+its Keplerian limit and the position of its maximum."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import galaxy_ics as gi
+
+
+@pytest.mark.parametrize("ctr,key,want", [
+    ((0, 0, 0, 0), (0, 0), (0x6627E8D5, 0xE169C58D, 0xBC57AC4C, 0x9B00DBD8)),
+    ((0xFFFFFFFF,) * 4, (0xFFFFFFFF,) * 2, (0x408F276D, 0x41C83B0E, 0xA20BC7C6, 0x6D5451FD)),
+    ((0x243F6A88, 0x85A308D3, 0x13198A2E, 0x03707344), (0xA4093822, 0x299F31D0),
+     (0xD16CFE09, 0x94FDCCEB, 0x5001E420, 0x24126EA1)),
+])
+def test_philox_known_answers(ctr, key, want):
+    got = gi.philox4x32_10(*ctr, *key)
+    assert tuple(int(x) for x in got) == want
+
+
+def test_uniforms_are_exact_and_inside_the_unit_interval():
+    lo = gi.uniform52(0, 0)
+    hi = gi.uniform52(0xFFFFFFFF, 0xFFFFFFFF)
+    assert lo == 2.0 ** -53 and hi == 1.0 - 2.0 ** -53
+    u0, u1 = gi.draws(np.arange(100000, dtype=np.uint64), 0, 0, 12345)
+    for u in (u0, u1):
+        assert u.min() > 0.0 and u.max() < 1.0
+        assert abs(u.mean() - 0.5) < 5 * math.sqrt(1 / 12 / u.size)
+    assert abs(np.corrcoef(u0, u1)[0, 1]) < 0.02
+
+
+def test_counts_follow_the_paper_realisation():
+    assert gi.counts(sum(gi.PAPER_COUNTS)) == (gi.PAPER_COUNTS[2], gi.PAPER_COUNTS[1], gi.PAPER_COUNTS[0])
+    for n in (1 << 14, 1 << 23, 1 << 28):
+        h, d, b = gi.counts(n)
+        assert h + d + b == n and b < d < h
+
+
+def _hernquist_only(a=0.01):
+    return gi.Galaxy(0, 0, 1000, G=1.0, M_halo=0.0, M_disk=0.0, M_bulge=1.0, a_bulge=a,
+                     r_t=1e6, dr_t=1.0)
+
+
+def test_hernquist_potential_and_df_closed_forms():
+    """A lone Hernquist sphere (G = M = 1, a = 0.01; no taper on the grid):
+    Psi = GM/(r + a), and f(E) of Hernquist (1990) Eq. 17."""
+    a = 0.01
+    tb = gi.tables(_hernquist_only(a))
+    pr = tb["prof"]
+    r, Psi = pr["r"], pr["Psi"]
+    # the grid ends at 600: the sphere inside it carries all the mass (x 1.0000333)
+    assert np.max(np.abs(Psi * (r + a) - 1.0)) < 5e-5
+    q2 = Psi * a
+    q = np.sqrt(q2)
+    vg = math.sqrt(1.0 / a)
+    fcf = (1.0 / (8 * math.sqrt(2) * math.pi ** 3 * a ** 3 * vg ** 3) / (1 - q2) ** 2.5
+           * (3 * np.arcsin(q) + q * np.sqrt(1 - q2) * (1 - 2 * q2) * (8 * q2 * q2 - 8 * q2 - 3)))
+    f = tb["bulge"]["f"]
+    mid = (q2 > 0.02) & (q2 < 0.8)
+    assert np.max(np.abs(f[mid] / fcf[mid] - 1)) < 5e-4
+    deep = (q2 >= 0.8) & (q2 < 0.99)
+    assert np.max(np.abs(f[deep] / fcf[deep] - 1)) < 1.5e-2
+
+
+def test_nfw_enclosed_mass():
+    """An untapered NFW halo: M(<r) proportional to ln(1 + x) - x/(1 + x)."""
+    g = gi.Galaxy(1000, 0, 0, G=1.0, M_halo=1.0, a_halo=15.0, M_bulge=0.0, M_disk=0.0,
+                  r_t=1e6, dr_t=1.0)
+    pr = gi.profiles(g)
+    r = pr["r"]
+    x = r / 15.0
+    m = np.log1p(x) - x / (1 + x)
+    ref = np.searchsorted(r, 10.0)
+    got = pr["comp"]["halo"]["M"] / pr["comp"]["halo"]["M"][ref]
+    sel = r < 300
+    # trapezoid rule in ln r, step 0.0038: error of order step^2 / 12
+    assert np.max(np.abs(got[sel] / (m[sel] / m[ref]) - 1)) < 5e-6
+
+
+@pytest.fixture(scope="module")
+def sec4():
+    g = gi.milky_way_sec4(1 << 17)
+    return g, gi.tables(g)
+
+
+def test_df_gives_back_the_density(sec4):
+    """4 pi int v^2 f(Psi - v^2/2) dv = rho for both spheroids, inside the taper."""
+    _, tb = sec4
+    pr = tb["prof"]
+    r, Psi = pr["r"], pr["Psi"]
+    for name in ("halo", "bulge"):
+        rho = pr["comp"][name]["rho"]
+        rec = 4 * math.pi * (2 * (Psi - Psi[-1])) ** 1.5 * tb[name]["vnorm"]
+        sel = (r > 1e-3) & (r < 200)
+        assert np.max(np.abs(rec[sel] / rho[sel] - 1)) < 2e-4, name
+        assert np.all(tb[name]["f"] >= 0)
+
+
+def test_df_dispersion_solves_the_jeans_equation(sec4):
+    """<v^2>/3 of the distribution function equals the isotropic Jeans
+    dispersion (1/rho) int_r rho G M / r'^2 dr' of each spheroid."""
+    g, tb = sec4
+    pr = tb["prof"]
+    r, Psi, Mt = pr["r"], pr["Psi"], pr["Mt"]
+    q = np.linspace(0, 1, 4001)
+    for name in ("halo", "bulge"):
+        rho = pr["comp"][name]["rho"]
+        integrand = rho * g.G * Mt / r ** 2 * r  # d ln r
+        tail = np.concatenate([np.cumsum((0.5 * (integrand[1:] + integrand[:-1]) * pr["dl"])[::-1])[::-1], [0]])
+        s2_jeans = tail / rho
+        for k in np.searchsorted(r, [0.01, 0.1, 1.0, 10.0, 50.0, 150.0]):
+            w = Psi[k] - Psi[-1]
+            fv = gi.interp_desc(Psi[-1] + (1 - q * q) * w, Psi, tb[name]["f"])
+            m2 = np.trapezoid(q ** 2 * fv, q)
+            m4 = np.trapezoid(q ** 4 * fv, q)
+            s2_df = 2 * w * m4 / m2 / 3
+            assert abs(s2_df / s2_jeans[k] - 1) < 2e-3, (name, r[k], s2_df, s2_jeans[k])
+
+
+def test_sampled_spheroids_follow_the_tables(sec4):
+    g, tb = sec4
+    pos, vel, _ = gi.generate(g, tb)
+    pr = tb["prof"]
+    Psi = pr["Psi"]
+    for name, (s, n) in (("halo", (0, g.n_halo)), ("bulge", (g.n_halo + g.n_disk, g.n_bulge))):
+        # sampled before the centre-of-mass shift: redo the draw for the raw radii
+        comp_id = 0 if name == "halo" else 2
+        p, v = gi.sample_spheroid(g, tb, name, s, n, comp_id)
+        r = np.sqrt((p * p).sum(0))
+        sp = np.sqrt((v * v).sum(0))
+        rr = np.sort(r)
+        P = pr["comp"][name]["P"]
+        for x in np.quantile(r, [0.05, 0.25, 0.5, 0.75, 0.95]):
+            emp = np.searchsorted(rr, x) / n
+            assert abs(emp - np.interp(math.log(x), np.log(pr["r"]), P)) < 2.0 / math.sqrt(n)
+        vesc = np.sqrt(2 * (np.interp(np.log(r), np.log(pr["r"]), Psi) - Psi[-1]))
+        assert np.all(sp <= vesc * (1 + 1e-12))
+        # isotropy: each axis carries a third of <v^2>; directions uniform
+        m2 = (v * v).mean(1)
+        assert np.max(np.abs(m2 / m2.mean() - 1)) < 6 / math.sqrt(n)
+        assert np.max(np.abs(p.mean(1))) < 6 * r.std() / math.sqrt(n) + 1e-9
+
+
+def test_generate_centres_and_is_deterministic(sec4):
+    g, tb = sec4
+    pos, vel, mass = gi.generate(g, tb)
+    mt = mass.sum()
+    assert np.max(np.abs((pos * mass).sum(1) / mt)) < 1e-12 * np.abs(pos).max()
+    assert np.max(np.abs((vel * mass).sum(1) / mt)) < 1e-12 * np.abs(vel).max()
+    assert math.isclose(mt, g.M_halo + g.M_disk + g.M_bulge, rel_tol=1e-12)
+    p2, v2, _ = gi.generate(g, tb)
+    assert np.array_equal(pos, p2) and np.array_equal(vel, v2)
+    g3 = gi.milky_way_sec4(1 << 17, seed=g.seed + 1)
+    p3, _, _ = gi.generate(g3, tb)
+    assert not np.array_equal(pos, p3)
+
+
+def test_sampled_halo_is_virialised():
+    """A lone tapered NFW halo from its distribution function: 2K/|W| = 1
+    within the sampling noise (W by direct summation)."""
+    g = gi.Galaxy(6000, 0, 0, seed=7, M_bulge=0.0, M_disk=0.0)
+    pos, vel, mass = gi.generate(g)
+    _, pot = oracle.direct_forces(pos, mass, 0.05, g.G)
+    W = 0.5 * float((mass * pot).sum())
+    Kin = 0.5 * float((mass * (vel * vel).sum(0)).sum())
+    assert abs(2 * Kin / abs(W) - 1) < 0.05
+
+
+def test_disk_positions_follow_exponential_and_sech2(sec4):
+    g, tb = sec4
+    p, _ = gi.sample_disk(g, tb, g.n_halo, g.n_disk)
+    n = g.n_disk
+    R = np.sqrt(p[0] ** 2 + p[1] ** 2)
+    assert R.max() <= g.R_max * (1 + 1e-12)
+    norm = 1 - (1 + g.R_max / g.R_d) * math.exp(-g.R_max / g.R_d)
+    for x in (1.0, 2.5, 5.0, 10.0):
+        want = (1 - (1 + x / g.R_d) * math.exp(-x / g.R_d)) / norm
+        assert abs((R < x).mean() - want) < 2.5 / math.sqrt(n)
+    for x in (0.1, 0.3, 0.9):
+        assert abs((np.abs(p[2]) < x).mean() - math.tanh(x / g.z0)) < 2.5 / math.sqrt(n)
+
+
+def test_freeman_rotation_limits():
+    """Thin exponential disk: Keplerian far out; maximum near 2.15 R_d."""
+    G, M, Rd = 1.0, 1.0, 1.0
+    R = np.array([200.0])
+    assert abs(gi.freeman_vc2(R, G, M, Rd)[0] * R[0] / (G * M) - 1) < 2e-4
+    Rg = np.linspace(0.5, 5, 9001)
+    Rpk = Rg[np.argmax(gi.freeman_vc2(Rg, G, M, Rd))]
+    assert abs(Rpk - 2.15) < 0.01
+
+
+def test_disk_kinematic_tables(sec4):
+    """Toomre Q and the epicyclic ratio hold on the tables; the analytic
+    d ln(Sigma sigma_R^2)/d ln R used for the drift equals the numerical
+    slope of the tabulated Sigma sigma_R^2; the mean rotation lags v_c."""
+    g, tb = sec4
+    d = tb["disk"]
+    R = d["R"]
+    s0 = g.M_disk / (2 * math.pi * g.R_d ** 2)
+    Sig = s0 * np.exp(-R / g.R_d)
+    Q = d["sR"] * d["kappa"] / (3.36 * g.G * Sig)
+    assert np.allclose(Q, g.Q, rtol=1e-12)
+    y = np.log(Sig * d["sR"] ** 2)
+    num = np.gradient(y, np.log(R))
+    kap = d["kappa"]
+    h = d["h"]
+    dk = np.gradient(kap, h)
+    ana = -3 * R / g.R_d - 2 * R * dk / kap
+    sel = (R > 0.5) & (R < 25)
+    assert np.max(np.abs(num[sel] - ana[sel])) < 1e-3
+    # outside the inner disk (where a constant Q makes sigma_R grow inward
+    # as 1/kappa and the drift term changes sign) the mean rotation lags v_c
+    out = (R > 2.0) & (R < 25)
+    assert np.all(d["vphi"][out] ** 2 < d["vc2"][out])
+    # the sample's moments per radial bin follow the tables
+    p, v = gi.sample_disk(g, tb, g.n_halo, g.n_disk)
+    Rp = np.sqrt(p[0] ** 2 + p[1] ** 2)
+    c, s = p[0] / Rp, p[1] / Rp
+    vR = v[0] * c + v[1] * s
+    vp = -v[0] * s + v[1] * c
+    for lo, hi in ((2.0, 3.0), (4.0, 6.0)):
+        m = (Rp > lo) & (Rp < hi)
+        k = m.sum()
+        mid = np.interp(Rp[m], R, d["vphi"]).mean()
+        sRm = math.sqrt(np.mean(np.interp(Rp[m], R, d["sR"]) ** 2))
+        assert abs(vp[m].mean() - mid) < 4 * d["sphi"].max() / math.sqrt(k)
+        assert abs(vR[m].std() / sRm - 1) < 4 / math.sqrt(2 * k)
