@@ -199,11 +199,23 @@ def cumulative_mass_shape(r, dl, a, beta, shape, C0):
     return S
 
 
+def disk_fraction(x):
+    """1 - (1 + x) e^-x: the alternating series sum_{k>=2} (-1)^k (k-1) x^k / k!
+    (22 terms) below x = 1/2, where the closed form cancels; the closed form
+    above."""
+    x = np.asarray(x, dtype=np.float64)
+    s = np.zeros_like(x)
+    t = x * x / 2.0            # x^k / k! at k = 2
+    for k in range(2, 24):
+        s = s + (1.0 if k % 2 == 0 else -1.0) * (k - 1) * t
+        t = t * x / (k + 1)
+    return np.where(x < 0.5, s, 1.0 - (1.0 + x) * np.exp(-x))
+
+
 def disk_sph_mass(r, Md, Rd):
     """Mass of a thin exponential disk inside radius r, and its r-derivative."""
     x = r / Rd
-    e = np.exp(-x)
-    return Md * (1.0 - (1.0 + x) * e), Md * x * e / Rd
+    return Md * disk_fraction(x), Md * x * np.exp(-x) / Rd
 
 
 def profiles(g: Galaxy):
@@ -311,7 +323,7 @@ def disk_tables(g: Galaxy, pr):
     Rc = np.arange(KD) * h                    # cumulative-mass grid
     x = Rc / g.R_d
     xm = g.R_max / g.R_d
-    cdf = (1.0 - (1.0 + x) * np.exp(-x)) / (1.0 - (1.0 + xm) * math.exp(-xm))
+    cdf = disk_fraction(x) / disk_fraction(xm)
     cdf[-1] = 1.0
     R = (np.arange(KD) + 0.5) * h            # kinematic grid
     msph = sph_mass_at(pr, "halo", R) + sph_mass_at(pr, "bulge", R)

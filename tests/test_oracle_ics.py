@@ -192,6 +192,18 @@ def test_disk_positions_follow_exponential_and_sech2(sec4):
         assert abs((np.abs(p[2]) < x).mean() - math.tanh(x / g.z0)) < 2.5 / math.sqrt(n)
 
 
+def test_disk_fraction_series_and_closed_form_agree():
+    """1 - (1 + x) e^-x: the series branch against the closed form where the
+    latter is accurate, and against its first five Taylor terms for small x."""
+    x = np.linspace(0.3, 0.5, 51)
+    direct = 1.0 - (1.0 + x) * np.exp(-x)
+    below = x < 0.5
+    assert np.max(np.abs(gi.disk_fraction(x)[below] / direct[below] - 1)) < 1e-14
+    t = np.array([1e-8, 1e-5, 1e-3])
+    taylor = t * t / 2 - t ** 3 / 3 + t ** 4 / 8 - t ** 5 / 30 + t ** 6 / 144
+    assert np.max(np.abs(gi.disk_fraction(t) / taylor - 1)) < 1e-14
+
+
 def test_freeman_rotation_limits():
     """Thin exponential disk: Keplerian far out; maximum near 2.15 R_d."""
     G, M, Rd = 1.0, 1.0, 1.0
