@@ -26,11 +26,17 @@ module states, step by step in plain numpy, what the GPU generator computes:
    q = v / v_esc, p(q) ~ q^2 f(Psimin + (1 - q^2)(Psi - Psimin)), on V nodes.
 5. The disk: R from the truncated exponential surface density (cumulative
    in closed form on a linear grid), z = z0 atanh(2u - 1) (sech^2),
-   Gaussian velocities with Toomre-Q radial dispersion, the epicyclic
-   azimuthal dispersion, the isothermal-sheet vertical dispersion and an
-   asymmetric-drift corrected mean rotation in the potential of the
-   spheroids (their enclosed mass) plus the thin exponential disk
-   (Freeman's circular speed with modified Bessel functions).
+   Gaussian velocities: sigma_R^2 proportional to Sigma, scaled so that
+   Toomre's sigma_R kappa / (3.36 G Sigma) equals Q at R_Q = 2.43 R_d
+   (Hernquist 1993: Q set at the solar radius, 2.43 scale lengths); the
+   epicyclic sigma_phi = sigma_R kappa / (2 Omega); the isothermal-sheet
+   sigma_z^2 = pi G Sigma z0; and the mean rotation from the asymmetric
+   drift, v_phi^2 = v_c^2 + sigma_R^2 (1 - kappa^2 / (4 Omega^2) - 2 R /
+   R_d), held within [0, v_c^2] (the epicyclic closure fails where sigma_R
+   approaches v_c, near the centre, and would make the disk rotate faster
+   than circular), in the potential of the spheroids (their enclosed mass)
+   plus the thin exponential disk (Freeman's circular speed with modified
+   Bessel functions).
 6. Sampling: every particle draws its uniforms from Philox4x32-10 (Salmon,
    Moraes, Dror & Shaw, SC11) with counter (particle index, component,
    call, 0) and key (seed low, seed high); each uniform takes two 32-bit
@@ -81,6 +87,7 @@ class Galaxy:
     z0: float = 0.3
     R_max: float = 30.0
     Q: float = 1.5
+    R_Q: float = 6.075
 
     @property
     def n(self) -> int:
@@ -333,14 +340,17 @@ def disk_tables(g: Galaxy, pr):
     kap = np.sqrt(np.maximum(kap2, 1e-30))
     s0 = g.M_disk / (2.0 * math.pi * g.R_d * g.R_d)
     Sig = s0 * np.exp(-R / g.R_d)
-    sR = g.Q * 3.36 * g.G * Sig / kap
+    # kappa at R_Q: linear between the kinematic nodes, clamped
+    sq = min(max(g.R_Q / h - 0.5, 0.0), KD - 1.0)
+    iq = min(int(sq), KD - 2)
+    kq = (1.0 - (sq - iq)) * kap[iq] + (sq - iq) * kap[iq + 1]
+    sRq = g.Q * 3.36 * g.G * s0 * math.exp(-g.R_Q / g.R_d) / kq
+    sR = sRq * np.exp(-(R - g.R_Q) / (2.0 * g.R_d))
     sphi = sR * kap / (2.0 * np.sqrt(om2))
     sz = np.sqrt(math.pi * g.G * Sig * g.z0)
-    dlnk = R * central_diff(kap, h) / kap
-    dln = -3.0 * R / g.R_d - 2.0 * dlnk       # d ln(Sigma sigma_R^2) / d ln R
-    vphi = np.sqrt(np.maximum(vc2 + sR * sR * (1.0 - kap2 / (4.0 * om2) + dln), 0.0))
+    vphi = np.sqrt(np.clip(vc2 + sR * sR * (1.0 - kap2 / (4.0 * om2) - 2.0 * R / g.R_d), 0.0, vc2))
     return {"h": h, "cdf": cdf, "R": R, "vc2": vc2, "kappa": kap, "sR": sR, "sphi": sphi,
-            "sz": sz, "vphi": vphi}
+            "sz": sz, "vphi": vphi, "kappa_Q": kq}
 
 
 def tables(g: Galaxy):
