@@ -388,6 +388,81 @@ const char *bonsai_strerror(int code);
 int bonsai_sfc_order_noalloc(const double *pos, const double *mass, int64_t n, uint64_t *keys,
                              uint32_t *perm, double cube[4], void *stream);
 
+/* ---- on-the-fly galaxy initial conditions (Sec. IV) ------------------ */
+/* Sec. IV generates its Milky Way model on the fly instead of reading an
+ * initial-condition file: an NFW dark-matter halo, an exponential stellar
+ * disk and a Hernquist bulge.  These entry points build that model on the
+ * GPU.  The halo and the bulge are sampled from their isotropic distribution
+ * functions, obtained by Eddington's inversion in the spherically averaged
+ * potential of all three components; each carries the outer taper
+ * C(r) = erfc((r - r_t) / (sqrt(2) dr_t)) / 2.  The disk is exponential in
+ * R (truncated at R_max) and sech^2 in z, with Gaussian velocities:
+ * sigma_R^2 proportional to the surface density with Toomre's Q at R_Q,
+ * the epicyclic azimuthal dispersion, the isothermal-sheet vertical
+ * dispersion and the asymmetric-drift mean rotation held within [0, v_c]
+ * (the epicyclic approximation, not a disk distribution function).  The
+ * spheroids' distribution functions see the disk through its spherically
+ * averaged mass, so they are in equilibrium in that potential; where the
+ * flat disk dominates the inner mass the bulge adjusts.  Every particle draws its uniforms from Philox4x32-10 (Salmon
+ * et al., SC11) with counter (particle index, component, call, 0) and key
+ * (seed low word, seed high word), so the output depends on the seed and n
+ * only, not on the launch shape.  Units: kpc, Msun, Myr for the defaults. */
+
+#define BONSAI_ICS_K 4096        /* radial nodes of the spheroid tables (1e-4 .. 600, log) */
+#define BONSAI_ICS_V 256         /* speed-fraction nodes per velocity-table row */
+#define BONSAI_ICS_KD 4096       /* radial nodes of the disk tables */
+#define BONSAI_ICS_NRAD_OUT 15   /* rows of the radial table written by bonsai_galaxy_tables */
+#define BONSAI_ICS_NDISK_OUT 7   /* rows of the disk table written by bonsai_galaxy_tables */
+
+typedef struct {
+    int64_t n_halo, n_disk, n_bulge;  /* particles per component (>= 0, sum < 2^32) */
+    uint64_t seed;                    /* Philox key */
+    double G;                         /* gravitational constant */
+    double M_halo, a_halo;            /* NFW: total mass (with the taper), scale radius */
+    double M_bulge, a_bulge;          /* Hernquist: total mass (with the taper), scale radius */
+    double r_t, dr_t;                 /* outer taper of both spheroids */
+    double M_disk, R_d, z0, R_max;    /* disk mass, scale length, sech^2 height, edge */
+    double Q, R_Q;                    /* Toomre Q and the radius where it holds */
+} bonsai_galaxy;
+
+/* bonsai_galaxy_sec4 -- the Sec. IV model for n particles: component
+ * masses 6.0e11 (halo), 5.0e10 (disk), 4.6e9 (bulge) Msun; counts in the
+ * ratio of the paper's 51 G-particle realisation (bulge 994,689,024, disk
+ * 2,945,105,920, halo 47,260,172,288: bulge and disk rounded down, the halo
+ * takes the rest).  Scale lengths not given in the paper: a_halo = 15 kpc,
+ * a_bulge = 0.5 kpc, r_t = 200 kpc, dr_t = 20 kpc, R_d = 2.5 kpc, z0 =
+ * 0.3 kpc, R_max = 30 kpc, Q = 1.5 at R_Q = 2.43 R_d (Hernquist 1993);
+ * G in kpc^3 Msun^-1 Myr^-2.
+ * Errors: EINVAL (null, n < 1 or n >= 2^32). */
+int bonsai_galaxy_sec4(bonsai_galaxy *g, int64_t n, uint64_t seed);
+
+/* bonsai_galaxy_generate -- sample the model: pos, vel device float64
+ * [3][n] SoA and mass device float64 [n], n = n_halo + n_disk + n_bulge;
+ * halo first, then disk, then bulge; equal masses within a component; the
+ * centre of mass and the mean velocity moved to zero.  Device scratch of
+ * about 17 MB is allocated and freed stream-ordered (cudaMallocAsync).
+ * Twelve kernels run on stream (a cudaStream_t, NULL = legacy default); the
+ * call returns after they finish.  n = 0 does nothing.
+ * Errors: EINVAL (null pointer with n > 0, a negative count, n >= 2^32, a
+ * non-positive or non-finite length, G, Q or R_Q, a negative mass, zero mass
+ * for a component with particles), ENOMEM, ECUDA. */
+int bonsai_galaxy_generate(const bonsai_galaxy *g, double *pos, double *vel, double *mass,
+                           void *stream);
+
+/* bonsai_galaxy_tables -- the generator's tables, for checks.  radial:
+ * device float64 [BONSAI_ICS_NRAD_OUT][BONSAI_ICS_K], rows r, Psi (relative
+ * potential), M(<r) total, M_halo(<r), M_bulge(<r), halo and bulge
+ * cumulative mass fractions, halo and bulge d2rho/dPsi2, halo and bulge
+ * f(E) at E = Psi, halo and bulge int_0^1 q^2 f dq, halo and bulge density.
+ * vcdf: device float64 [2][K][V] (halo, bulge) normalised speed-fraction
+ * cumulative distributions, or NULL.  disk: device float64
+ * [BONSAI_ICS_NDISK_OUT][BONSAI_ICS_KD], rows: cumulative surface-mass
+ * fraction at R = j R_max / (KD - 1); and at R = (j + 1/2) R_max / (KD - 1):
+ * v_c^2, kappa, sigma_R, sigma_phi, sigma_z, mean v_phi.
+ * Errors: as bonsai_galaxy_generate (null radial or disk: EINVAL). */
+int bonsai_galaxy_tables(const bonsai_galaxy *g, double *radial, double *vcdf, double *disk,
+                         void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -36,10 +36,16 @@ EXPORTED = (
     "tree_debug_set_frontier_capacity", "tree_forces_fp64", "tree_direct_forces",
     "tree_save_snapshot", "tree_load_snapshot", "tree_surface_density",
     "tree_build_cube", "tree_domain_state", "let_create", "let_destroy", "let_build", "let_get_info",
-    "let_debug_cells", "let_forces",
+    "let_debug_cells", "let_forces", "bonsai_galaxy_sec4", "bonsai_galaxy_generate",
+    "bonsai_galaxy_tables",
 )
 
 BONSAI_NOALLOC_MAX_N = 1 << 20
+BONSAI_ICS_K = 4096
+BONSAI_ICS_V = 256
+BONSAI_ICS_KD = 4096
+BONSAI_ICS_NRAD_OUT = 15
+BONSAI_ICS_NDISK_OUT = 7
 
 
 class BonsaiError(RuntimeError):
@@ -61,6 +67,19 @@ class bonsai_stats(ctypes.Structure):
                 ("ms_keys", ctypes.c_float), ("ms_tree", ctypes.c_float),
                 ("ms_force", ctypes.c_float), ("ms_integrate", ctypes.c_float),
                 ("ms_walk", ctypes.c_float), ("launches", ctypes.c_uint64)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class bonsai_galaxy(ctypes.Structure):
+    _fields_ = [("n_halo", ctypes.c_int64), ("n_disk", ctypes.c_int64), ("n_bulge", ctypes.c_int64),
+                ("seed", ctypes.c_uint64), ("G", ctypes.c_double),
+                ("M_halo", ctypes.c_double), ("a_halo", ctypes.c_double),
+                ("M_bulge", ctypes.c_double), ("a_bulge", ctypes.c_double),
+                ("r_t", ctypes.c_double), ("dr_t", ctypes.c_double),
+                ("M_disk", ctypes.c_double), ("R_d", ctypes.c_double), ("z0", ctypes.c_double),
+                ("R_max", ctypes.c_double), ("Q", ctypes.c_double), ("R_Q", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -115,6 +134,9 @@ def load(path: str | None = None):
             "tree_load_snapshot": (i32, [P, ctypes.c_char_p, ctypes.POINTER(f64)]),
             "tree_surface_density": (i32, [P, i64, i64, ctypes.POINTER(f64), i32, i32, P]),
             "tree_forces_fp64": (i32, [P, f32, f32, P, P]),
+            "bonsai_galaxy_sec4": (i32, [ctypes.POINTER(bonsai_galaxy), i64, ctypes.c_uint64]),
+            "bonsai_galaxy_generate": (i32, [ctypes.POINTER(bonsai_galaxy), P, P, P, P]),
+            "bonsai_galaxy_tables": (i32, [ctypes.POINTER(bonsai_galaxy), P, P, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -392,3 +414,31 @@ def bonsai_sfc_order_noalloc(pos, mass, keys, perm, stream=None):
                                            _ptr(keys, None, n, "keys"), _ptr(perm, None, n, "perm"),
                                            cube, _stream_handle(stream)), "bonsai_sfc_order_noalloc")
     return list(cube)
+
+
+def bonsai_galaxy_sec4(n: int, seed: int) -> bonsai_galaxy:
+    """The Sec. IV Milky Way model for n particles (host struct)."""
+    g = bonsai_galaxy()
+    _check(load().bonsai_galaxy_sec4(ctypes.byref(g), int(n), int(seed)), "bonsai_galaxy_sec4")
+    return g
+
+
+def bonsai_galaxy_generate(g: bonsai_galaxy, pos, vel, mass, stream=None) -> None:
+    """Sample the model into pos, vel (float64 CUDA tensors, 3 x n) and mass (n)."""
+    import torch
+    n = int(g.n_halo + g.n_disk + g.n_bulge)
+    _check(load().bonsai_galaxy_generate(ctypes.byref(g), _ptr(pos, torch.float64, 3 * n, "pos"),
+                                         _ptr(vel, torch.float64, 3 * n, "vel"),
+                                         _ptr(mass, torch.float64, n, "mass"),
+                                         _stream_handle(stream)), "bonsai_galaxy_generate")
+
+
+def bonsai_galaxy_tables(g: bonsai_galaxy, radial, vcdf, disk, stream=None) -> None:
+    """The generator's tables into float64 CUDA tensors: radial (15 x K),
+    vcdf (2 x K x V or None), disk (7 x KD)."""
+    import torch
+    _check(load().bonsai_galaxy_tables(
+        ctypes.byref(g), _ptr(radial, torch.float64, BONSAI_ICS_NRAD_OUT * BONSAI_ICS_K, "radial"),
+        _ptr(vcdf, torch.float64, 2 * BONSAI_ICS_K * BONSAI_ICS_V, "vcdf"),
+        _ptr(disk, torch.float64, BONSAI_ICS_NDISK_OUT * BONSAI_ICS_KD, "disk"),
+        _stream_handle(stream)), "bonsai_galaxy_tables")
