@@ -35,8 +35,8 @@ if ROOT not in sys.path:
 # DRAM bytes (read + written) of one walk/force launch, from a one-pass ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum) of the benchmark
 # command, valid only for the walk source it was taken on (checked by hash).
-WALK_TRAFFIC = {"walk_cu_sha256": "f8c8e6681dae7afc62ba27b659f83e600aa3f6300bf302a8af06ae249d8ecc24",
-                "bytes": {"milky-way-2^23": 708.41e6 + 276.85e6}}
+WALK_TRAFFIC = {"walk_cu_sha256": "3d2cfdf63ddb187eec0968fe5da8fd1b30e957baee424d05e4450c08d7d7f3ae",
+                "bytes": {"milky-way-2^23": 706.85e6 + 276.77e6}}
 
 METRIC = "tree-force Tflop/s (23 flops/p-p + 65 flops/p-c, Sec. VI.A) per full KDK step, theta=0.4"
 UNIT = "Tflop/s"
@@ -347,6 +347,34 @@ def run_ours(args):
                       "state to a local temporary file; tree_surface_density of disk + bulge, "
                       "1024^2 pixels, CUDA events (includes the map clear and a stream sync)"}
 
+    # --- on-the-fly initial conditions (Sec. IV): the Milky Way model (NFW
+    # halo, exponential disk, Hernquist bulge) of the same size generated on
+    # the device, tables and sampling, CUDA events around the whole call ---
+    ics = None
+    if not args.no_ics:
+        from paper_1412_0659_gb300 import capi as _capi, galaxy
+        gal = galaxy.sec4(n, 1006 + rank)
+        ipos = torch.empty(3, n, dtype=torch.float64, device=dev)
+        ivel = torch.empty_like(ipos)
+        imass = torch.empty(n, dtype=torch.float64, device=dev)
+        cs = torch.cuda.current_stream()
+        _capi.bonsai_galaxy_generate(gal, ipos, ivel, imass, cs)
+        ts = []
+        for _ in range(3):
+            i0 = torch.cuda.Event(enable_timing=True)
+            i1 = torch.cuda.Event(enable_timing=True)
+            i0.record(cs)
+            _capi.bonsai_galaxy_generate(gal, ipos, ivel, imass, cs)
+            i1.record(cs)
+            torch.cuda.synchronize()
+            ts.append(i0.elapsed_time(i1))
+        ics = {"model": "Sec. IV Milky Way: NFW halo 6.0e11, exponential disk 5.0e10, Hernquist bulge "
+                        f"4.6e9 Msun; {int(gal.n_halo)} + {int(gal.n_disk)} + {int(gal.n_bulge)} particles",
+               "ms": min(ts), "particles_per_s": n / (min(ts) * 1e-3), "launches_per_call": 12,
+               "what": "bonsai_galaxy_generate: Eddington tables, speed and disk tables, Philox sampling, "
+                       "centre-of-mass shift; FP64 throughout"}
+        del ipos, ivel, imass
+
     # --- domains and local essential trees (Sec. III.B) emulated on this GPU:
     # the state split into R pieces of the key order, each domain's own walk
     # plus the walks of the R - 1 LETs it receives ---
@@ -409,7 +437,7 @@ def run_ours(args):
             "phase_ms": {"keys_sort": statistics.mean(keys_ms), "tree_groups_multipoles": statistics.mean(tree_ms),
                          "force": statistics.mean(force_ms), "walk_kernel": walk_avg},
             "energy": {"E_tot": diag["E_tot"] if diag else None},
-            "adjoint": adjoint, "direct": direct, "io": io, "domains": dom,
+            "adjoint": adjoint, "direct": direct, "io": io, "ics": ics, "domains": dom,
             "clocks": clk, "gpu_launches": int(launches), "roofline": roofline, "e2e": e2e,
             "cpu_baseline": cpu,
         }
@@ -489,6 +517,7 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward timing")
     ap.add_argument("--no-direct", action="store_true", help="skip the direct-summation comparison")
     ap.add_argument("--no-io", action="store_true", help="skip the snapshot and surface-density timing")
+    ap.add_argument("--no-ics", action="store_true", help="skip the on-the-fly initial-condition timing")
     ap.add_argument("--domains", type=int, default=8,
                     help="domains of the local-essential-tree emulation (0 or 1 to skip)")
     ap.add_argument("--traffic", type=float, default=None,
