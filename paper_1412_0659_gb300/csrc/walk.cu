@@ -522,10 +522,12 @@ struct AdjointPolicy : Fp32Rings {
     }
 
     // add the chunk's target gradients (all rows) to tacc: column c is
-    // component (c % 6) / 2 of target t0 + 2 (c / 6) + (c & 1)
+    // component (c % 6) / 2 of target t0 + 2 (c / 6) + (c & 1); a chunk of
+    // NP target pairs fills the first 6 NP columns
+    template <int NP>
     __device__ __forceinline__ void reduce_chunk(int t0, int lane) {
         __syncwarp();
-        if (lane < 3 * ADJ_CHUNK) {
+        if (lane < 6 * NP) {
             float s = 0.0f;
 #pragma unroll 8
             for (int r = 0; r < 32; ++r) s += W->red[r * ADJ_ROW + lane];
@@ -535,6 +537,35 @@ struct AdjointPolicy : Fp32Rings {
         __syncwarp();
     }
 
+    // Running cell adjoint of one lane (packed: one half per target parity).
+    struct PcAcc {
+        f32x2 ax = 0ull, ay = 0ull, az = 0ull, aM = 0ull, aP = 0ull;
+        f32x2 dxx = 0ull, dyy = 0ull, dzz = 0ull, oxy = 0ull, oxz = 0ull, oyz = 0ull;
+    };
+
+    // Target pair tp of the chunk at t0 into the cell adjoint and the row.
+    __device__ __forceinline__ void pc_pair(const CellDup &C, f32x2 e2, int t0, int tp, int lane,
+                                            PcAcc &S) {
+        const TargetPair T2 = load_targets(T, (t0 >> 1) + tp);
+        f32x2 gx, gy, gz, gM, P0, vx, vy, vz, rx, ry, rz;
+        pc_vjp2(C, T2, e2, gx, gy, gz, gM, P0, vx, vy, vz, rx, ry, rz);
+        S.ax = add2(S.ax, gx);
+        S.ay = add2(S.ay, gy);
+        S.az = add2(S.az, gz);
+        S.aM = add2(S.aM, gM);
+        S.aP = add2(S.aP, P0);
+        S.dxx = fma2(rx, vx, S.dxx);
+        S.dyy = fma2(ry, vy, S.dyy);
+        S.dzz = fma2(rz, vz, S.dzz);
+        S.oxy = fma2(rx, vy, fma2(ry, vx, S.oxy));
+        S.oxz = fma2(rx, vz, fma2(rz, vx, S.oxz));
+        S.oyz = fma2(ry, vz, fma2(rz, vy, S.oyz));
+        put_pair(tp, gx, gy, gz, lane);
+    }
+
+    // Full chunks of 8 targets, then a last chunk of as many target pairs as
+    // the group has left (slots past the group hold zero cotangents; columns
+    // of the transpose rows past it belong to targets >= gc and are skipped).
     template <bool FULL>
     __device__ __forceinline__ void flush_pc(const WarpLists &L, int hb, int cnt, int lane) {
         const bool v = FULL || lane < cnt;
@@ -551,36 +582,26 @@ struct AdjointPolicy : Fp32Rings {
                         dup2(b.z), dup2(b.w), dup2(c.x), dup2(c.y), dup2(c.w),
                         dup2(-3.0f * M), dup2(-5.0f * c.w)};
         const f32x2 e2 = dup2(eps2);
-        f32x2 ax = 0ull, ay = 0ull, az = 0ull, aM = 0ull, aP = 0ull;
-        f32x2 dxx = 0ull, dyy = 0ull, dzz = 0ull, oxy = 0ull, oxz = 0ull, oyz = 0ull;
-        for (int t0 = 0; t0 < gc; t0 += ADJ_CHUNK) {
+        PcAcc S;
+        int t0 = 0;
+        for (; t0 + ADJ_CHUNK <= gc; t0 += ADJ_CHUNK) {
 #pragma unroll
-            for (int tp = 0; tp < ADJ_CHUNK / 2; ++tp) {
-                const TargetPair T2 = load_targets(T, (t0 >> 1) + tp);
-                f32x2 gx, gy, gz, gM, P0, vx, vy, vz, rx, ry, rz;
-                pc_vjp2(C, T2, e2, gx, gy, gz, gM, P0, vx, vy, vz, rx, ry, rz);
-                ax = add2(ax, gx);
-                ay = add2(ay, gy);
-                az = add2(az, gz);
-                aM = add2(aM, gM);
-                aP = add2(aP, P0);
-                dxx = fma2(rx, vx, dxx);
-                dyy = fma2(ry, vy, dyy);
-                dzz = fma2(rz, vz, dzz);
-                oxy = fma2(rx, vy, fma2(ry, vx, oxy));
-                oxz = fma2(rx, vz, fma2(rz, vx, oxz));
-                oyz = fma2(ry, vz, fma2(rz, vy, oyz));
-                put_pair(tp, gx, gy, gz, lane);
-            }
-            reduce_chunk(t0, lane);
+            for (int tp = 0; tp < ADJ_CHUNK / 2; ++tp) pc_pair(C, e2, t0, tp, lane, S);
+            reduce_chunk<ADJ_CHUNK / 2>(t0, lane);
+        }
+        const int np = (gc - t0 + 1) >> 1;  // one code copy for the ragged tail
+        if (np > 0) {
+#pragma unroll 1
+            for (int tp = 0; tp < np; ++tp) pc_pair(C, e2, t0, tp, lane, S);
+            reduce_chunk<ADJ_CHUNK / 2>(t0, lane);
         }
         if (v) {
             // gQ = P0 I + (r v^T + v r^T) with v2 = 2v accumulated:
             // diagonal P0 + r_a v2_a, off-diagonal (r_a v2_b + r_b v2_a) / 2
-            const float P = fold(aP);
-            const float aQ[6] = {P + fold(dxx), P + fold(dyy), P + fold(dzz),
-                                 0.5f * fold(oxy), 0.5f * fold(oxz), 0.5f * fold(oyz)};
-            cell_add(L.cid[j], fold(ax), fold(ay), fold(az), fold(aM), aQ);
+            const float P = fold(S.aP);
+            const float aQ[6] = {P + fold(S.dxx), P + fold(S.dyy), P + fold(S.dzz),
+                                 0.5f * fold(S.oxy), 0.5f * fold(S.oxz), 0.5f * fold(S.oyz)};
+            cell_add(L.cid[j], fold(S.ax), fold(S.ay), fold(S.az), fold(S.aM), aQ);
         }
     }
 
@@ -598,6 +619,19 @@ struct AdjointPolicy : Fp32Rings {
         atomicAdd(&cell_adj[2 * nn + node], make_float4(G * aQ[4], G * aQ[5], 0.0f, 0.0f));
     }
 
+    __device__ __forceinline__ void pp_pair(f32x2 sx, f32x2 sy, f32x2 sz, f32x2 sm, int sid,
+                                            f32x2 e2, int t0, int tp, int lane, f32x2 &ax,
+                                            f32x2 &ay, f32x2 &az, f32x2 &am) {
+        const TargetPair T2 = load_targets(T, (t0 >> 1) + tp);
+        f32x2 gx, gy, gz, gm;
+        pp_vjp2(sx, sy, sz, sm, sid, T2, e2, gx, gy, gz, gm);
+        ax = add2(ax, gx);
+        ay = add2(ay, gy);
+        az = add2(az, gz);
+        am = add2(am, gm);
+        put_pair(tp, gx, gy, gz, lane);
+    }
+
     template <bool FULL>
     __device__ __forceinline__ void flush_pp(const WarpLists &L, int hb, int cnt, int lane) {
         const bool v = FULL || lane < cnt;
@@ -608,19 +642,19 @@ struct AdjointPolicy : Fp32Rings {
         const f32x2 sx = dup2(s.x), sy = dup2(s.y), sz = dup2(s.z), sm = dup2(s.w);
         const f32x2 e2 = dup2(eps2);
         f32x2 ax = 0ull, ay = 0ull, az = 0ull, am = 0ull;
-        for (int t0 = 0; t0 < gc; t0 += ADJ_CHUNK) {
+        int t0 = 0;
+        for (; t0 + ADJ_CHUNK <= gc; t0 += ADJ_CHUNK) {
 #pragma unroll
-            for (int tp = 0; tp < ADJ_CHUNK / 2; ++tp) {
-                const TargetPair T2 = load_targets(T, (t0 >> 1) + tp);
-                f32x2 gx, gy, gz, gm;
-                pp_vjp2(sx, sy, sz, sm, sid, T2, e2, gx, gy, gz, gm);
-                ax = add2(ax, gx);
-                ay = add2(ay, gy);
-                az = add2(az, gz);
-                am = add2(am, gm);
-                put_pair(tp, gx, gy, gz, lane);
-            }
-            reduce_chunk(t0, lane);
+            for (int tp = 0; tp < ADJ_CHUNK / 2; ++tp)
+                pp_pair(sx, sy, sz, sm, sid, e2, t0, tp, lane, ax, ay, az, am);
+            reduce_chunk<ADJ_CHUNK / 2>(t0, lane);
+        }
+        const int np = (gc - t0 + 1) >> 1;
+        if (np > 0) {
+#pragma unroll 1
+            for (int tp = 0; tp < np; ++tp)
+                pp_pair(sx, sy, sz, sm, sid, e2, t0, tp, lane, ax, ay, az, am);
+            reduce_chunk<ADJ_CHUNK / 2>(t0, lane);
         }
         if (v) atomicAdd(&part_adj[sid], make_float4(G * fold(ax), G * fold(ay), G * fold(az),
                                                      G * fold(am)));
