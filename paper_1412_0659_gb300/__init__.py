@@ -11,7 +11,7 @@ from .flops import FLOPS_PC, FLOPS_PP, fp32_peak_tflops, tree_force_flops  # noq
 
 def __getattr__(name):
     # the CUDA binding and the object wrapper load torch; import them on demand
-    if name in ("capi", "gravity"):
+    if name in ("capi", "gravity", "galaxy", "domains", "autograd"):
         import importlib
         return importlib.import_module(f".{name}", __name__)
     if name == "TreeGravity":
