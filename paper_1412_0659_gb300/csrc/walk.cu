@@ -50,7 +50,7 @@ struct __align__(16) WarpTargets {
     float4 nzi[NCRIT / 2];  // {-z, -z', sorted index (bits), sorted index' (bits)}
     float4 lxy[NCRIT / 2];  // {lambda_x, lambda_x', lambda_y, lambda_y'}
     float4 lzm[NCRIT / 2];  // {lambda_z, lambda_z', mu, mu'}
-    float4 mus[NCRIT / 2];  // {-mu, -mu', mu/2, mu'/2}
+    float2 nmu[NCRIT / 2];  // {-mu, -mu'}
 };
 
 struct WalkArgs {
@@ -348,33 +348,35 @@ __device__ __forceinline__ ulonglong2 lds2(const float4 &v) {
 // One list entry (in both halves) and two targets.
 struct TargetPair {
     f32x2 nx, ny, nz;  // minus the target positions
-    f32x2 lx, ly, lz, mu, nmu, hmu;  // lambda, mu, -mu, mu/2
+    f32x2 lx, ly, lz, mu, nmu;  // lambda, mu, -mu
     int2 id;           // sorted indices
 };
 
 // Gradient of lambda.a + mu phi for one cell on two targets (without G),
 // with respect to r = com - x_i (g_r), the cell mass (gM) and the symmetric
 // quadrupole Q.  With u = 1/s, w = u^2, Q' = -3Q (as stored), rq = r.Q'r,
-// lq = lambda.Q'r, lr = lambda.r:
-//   fQ    = c.w u^5 - 5/2 rq u^7                  (c.w = -3/2 trQ)
-//   alpha = M u^3 + fQ
-//   beta  = -3 M u^5 lr + mu alpha + lr (-5 c.w u^7 + 35/2 rq u^9) - 5 u^7 lq
-//   g_r   = alpha lambda + beta r + (mu u^5 - 5 u^7 lr) Q'r + u^5 Q'lambda
+// lq = lambda.Q'r, lr = lambda.r, z = w rq:
+//   alpha = u^3 (M + w (c.w - 5/2 z))            (c.w = -3/2 trQ)
+//   K     = u^5 (-3M + w (-5 c.w + 35/2 z))
+//   gam   = mu u^5 - 5 u^7 lr
+//   beta  = lr K + mu alpha - 5 u^7 lq
+//   g_r   = alpha lambda + beta r + gam Q'r + u^5 Q'lambda
 //   gM    = lr u^3 - mu u
-//   gQ    = P0 I + (r v^T + v r^T),  P0 = mu u^3/2 - 3/2 u^5 lr,
-//           v = (15/4 u^7 lr - 3/4 mu u^5) r - 3/2 u^5 lambda.
-// Returns P0 and v2 = 2v; the caller accumulates gQ from them.  The cell
-// record (both halves equal): a = {com, M}, b, c as stored, M3 = -3M,
-// cw5 = -5 c.w.
+//   gQ    = P0 I + (r v2^T + v2 r^T) / 2,  P0 = mu u^3 / 2 - 3/2 u^5 lr,
+//           v2 = (15/2 u^7 lr - 3/2 mu u^5) r - 3 u^5 lambda = -3/2 vq,
+//           vq = gam r + 2 u^5 lambda.
+// The caller accumulates mu u^3 and u^5 lr (for P0) and r vq^T (for gQ)
+// and applies the constant factors once per cell.  The cell record (both
+// halves equal): a = {com, M}, b, c as stored, M3 = -3M, cw5 = -5 c.w.
 struct CellDup {
     f32x2 x, y, z, M, bx, by, bz, bw, cx, cy, cw, M3, cw5;
 };
 
 __device__ __forceinline__ void pc_vjp2(const CellDup &C, const TargetPair &T, f32x2 eps2,
-                                        f32x2 &gx, f32x2 &gy, f32x2 &gz, f32x2 &gM, f32x2 &P0,
-                                        f32x2 &vx, f32x2 &vy, f32x2 &vz, f32x2 &rx, f32x2 &ry,
-                                        f32x2 &rz) {
-    const f32x2 k_m25 = dup2(-2.5f), k_175 = dup2(17.5f), k_m5 = dup2(-5.0f), k_m15 = dup2(-1.5f);
+                                        f32x2 &gx, f32x2 &gy, f32x2 &gz, f32x2 &gM, f32x2 &u3,
+                                        f32x2 &u5, f32x2 &lr, f32x2 &vx, f32x2 &vy, f32x2 &vz,
+                                        f32x2 &rx, f32x2 &ry, f32x2 &rz) {
+    const f32x2 k_m25 = dup2(-2.5f), k_175 = dup2(17.5f), k_m5 = dup2(-5.0f);
     rx = add2(C.x, T.nx);
     ry = add2(C.y, T.ny);
     rz = add2(C.z, T.nz);
@@ -385,7 +387,8 @@ __device__ __forceinline__ void pc_vjp2(const CellDup &C, const TargetPair &T, f
     u2(s2, s0, s1);
     const f32x2 u = p2(rsqrtf(s0), rsqrtf(s1));
     const f32x2 w = mul2(u, u);
-    const f32x2 u3 = mul2(u, w), u5 = mul2(u3, w), u7 = mul2(u5, w);
+    u3 = mul2(u, w);
+    u5 = mul2(u3, w);
     const f32x2 qx = fma2(C.bx, rx, fma2(C.bw, ry, mul2(C.cx, rz)));  // Q'r
     const f32x2 qy = fma2(C.bw, rx, fma2(C.by, ry, mul2(C.cy, rz)));
     const f32x2 qz = fma2(C.cx, rx, fma2(C.cy, ry, mul2(C.bz, rz)));
@@ -394,25 +397,21 @@ __device__ __forceinline__ void pc_vjp2(const CellDup &C, const TargetPair &T, f
     const f32x2 pz = fma2(C.cx, T.lx, fma2(C.cy, T.ly, mul2(C.bz, T.lz)));
     const f32x2 rq = fma2(rx, qx, fma2(ry, qy, mul2(rz, qz)));
     const f32x2 lq = fma2(T.lx, qx, fma2(T.ly, qy, mul2(T.lz, qz)));
-    const f32x2 lr = fma2(T.lx, rx, fma2(T.ly, ry, mul2(T.lz, rz)));
-    // alpha = u^3 (M + w (c.w - 5/2 rq w))
-    const f32x2 alpha = mul2(u3, fma2(w, fma2(mul2(k_m25, rq), w, C.cw), C.M));
-    // beta = lr u^5 (-3M + w (-5 c.w + 35/2 rq w)) + mu alpha - 5 u^7 lq
-    const f32x2 m5u7 = mul2(k_m5, u7);
-    const f32x2 K = mul2(u5, fma2(w, fma2(mul2(k_175, rq), w, C.cw5), C.M3));
-    const f32x2 beta = fma2(lr, K, fma2(T.mu, alpha, mul2(m5u7, lq)));
-    const f32x2 gam = fma2(T.mu, u5, mul2(m5u7, lr));
+    lr = fma2(T.lx, rx, fma2(T.ly, ry, mul2(T.lz, rz)));
+    const f32x2 z = mul2(w, rq);
+    const f32x2 alpha = mul2(u3, fma2(w, fma2(k_m25, z, C.cw), C.M));
+    const f32x2 K = mul2(u5, fma2(w, fma2(k_175, z, C.cw5), C.M3));
+    const f32x2 c5 = mul2(mul2(k_m5, w), u5);  // -5 u^7
+    const f32x2 beta = fma2(lr, K, fma2(T.mu, alpha, mul2(c5, lq)));
+    const f32x2 gam = fma2(T.mu, u5, mul2(c5, lr));
     gx = fma2(alpha, T.lx, fma2(beta, rx, fma2(gam, qx, mul2(u5, px))));
     gy = fma2(alpha, T.ly, fma2(beta, ry, fma2(gam, qy, mul2(u5, py))));
     gz = fma2(alpha, T.lz, fma2(beta, rz, fma2(gam, qz, mul2(u5, pz))));
     gM = fma2(lr, u3, mul2(T.nmu, u));
-    const f32x2 m15u5 = mul2(k_m15, u5);
-    P0 = fma2(T.hmu, u3, mul2(m15u5, lr));
-    const f32x2 p1 = fma2(mul2(k_m15, m5u7), lr, mul2(m15u5, T.mu));  // v2 = p1 r - 3 u^5 lambda
-    const f32x2 m3u5 = add2(m15u5, m15u5);
-    vx = fma2(p1, rx, mul2(m3u5, T.lx));
-    vy = fma2(p1, ry, mul2(m3u5, T.ly));
-    vz = fma2(p1, rz, mul2(m3u5, T.lz));
+    const f32x2 u5x2 = add2(u5, u5);
+    vx = fma2(gam, rx, mul2(u5x2, T.lx));
+    vy = fma2(gam, ry, mul2(u5x2, T.ly));
+    vz = fma2(gam, rz, mul2(u5x2, T.lz));
 }
 
 // Gradient of lambda.a + mu phi for one p-p source on two targets (without G):
@@ -441,10 +440,11 @@ __device__ __forceinline__ void pp_vjp2(f32x2 sx, f32x2 sy, f32x2 sz, f32x2 sm, 
 
 __device__ __forceinline__ TargetPair load_targets(const WarpTargets *T, int p) {
     const ulonglong2 a = lds2(T->nxy[p]), b = lds2(T->nzi[p]), c = lds2(T->lxy[p]);
-    const ulonglong2 d = lds2(T->lzm[p]), e = lds2(T->mus[p]);
+    const ulonglong2 d = lds2(T->lzm[p]);
+    const f32x2 e = *reinterpret_cast<const f32x2 *>(&T->nmu[p]);
     float i0, i1;
     u2(b.y, i0, i1);
-    return TargetPair{a.x, a.y, b.x, c.x, c.y, d.x, d.y, e.x, e.y,
+    return TargetPair{a.x, a.y, b.x, c.x, c.y, d.x, d.y, e,
                       make_int2(__float_as_int(i0), __float_as_int(i1))};
 }
 
@@ -506,8 +506,7 @@ struct AdjointPolicy : Fp32Rings {
             rec[2 * K + 2] = ly;
             rec[3 * K] = lz;
             rec[3 * K + 2] = mu;
-            rec[4 * K] = -mu;
-            rec[4 * K + 2] = 0.5f * mu;
+            reinterpret_cast<float *>(T->nmu)[(li >> 1) * 2 + (li & 1)] = -mu;
         }
         for (int k = lane; k < NCRIT * 3; k += 32) W->tacc[k] = 0.0f;
         __syncwarp();
@@ -537,9 +536,11 @@ struct AdjointPolicy : Fp32Rings {
         __syncwarp();
     }
 
-    // Running cell adjoint of one lane (packed: one half per target parity).
+    // Running cell adjoint of one lane (packed: one half per target parity):
+    // g_com, gM, sum mu u^3, sum u^5 lr, and sum r vq^T (diagonal, symmetric
+    // off-diagonal pairs).
     struct PcAcc {
-        f32x2 ax = 0ull, ay = 0ull, az = 0ull, aM = 0ull, aP = 0ull;
+        f32x2 ax = 0ull, ay = 0ull, az = 0ull, aM = 0ull, aP1 = 0ull, aP2 = 0ull;
         f32x2 dxx = 0ull, dyy = 0ull, dzz = 0ull, oxy = 0ull, oxz = 0ull, oyz = 0ull;
     };
 
@@ -547,13 +548,14 @@ struct AdjointPolicy : Fp32Rings {
     __device__ __forceinline__ void pc_pair(const CellDup &C, f32x2 e2, int t0, int tp, int lane,
                                             PcAcc &S) {
         const TargetPair T2 = load_targets(T, (t0 >> 1) + tp);
-        f32x2 gx, gy, gz, gM, P0, vx, vy, vz, rx, ry, rz;
-        pc_vjp2(C, T2, e2, gx, gy, gz, gM, P0, vx, vy, vz, rx, ry, rz);
+        f32x2 gx, gy, gz, gM, u3, u5, lr, vx, vy, vz, rx, ry, rz;
+        pc_vjp2(C, T2, e2, gx, gy, gz, gM, u3, u5, lr, vx, vy, vz, rx, ry, rz);
         S.ax = add2(S.ax, gx);
         S.ay = add2(S.ay, gy);
         S.az = add2(S.az, gz);
         S.aM = add2(S.aM, gM);
-        S.aP = add2(S.aP, P0);
+        S.aP1 = fma2(T2.mu, u3, S.aP1);
+        S.aP2 = fma2(u5, lr, S.aP2);
         S.dxx = fma2(rx, vx, S.dxx);
         S.dyy = fma2(ry, vy, S.dyy);
         S.dzz = fma2(rz, vz, S.dzz);
@@ -596,11 +598,12 @@ struct AdjointPolicy : Fp32Rings {
             reduce_chunk<ADJ_CHUNK / 2>(t0, lane);
         }
         if (v) {
-            // gQ = P0 I + (r v^T + v r^T) with v2 = 2v accumulated:
-            // diagonal P0 + r_a v2_a, off-diagonal (r_a v2_b + r_b v2_a) / 2
-            const float P = fold(S.aP);
-            const float aQ[6] = {P + fold(S.dxx), P + fold(S.dyy), P + fold(S.dzz),
-                                 0.5f * fold(S.oxy), 0.5f * fold(S.oxz), 0.5f * fold(S.oyz)};
+            // gQ = P0 I + (r v2^T + v2 r^T) / 2 with v2 = -3/2 vq: diagonal
+            // P0 - 3/2 r_a vq_a, off-diagonal -3/4 (r_a vq_b + r_b vq_a)
+            const float P = 0.5f * fold(S.aP1) - 1.5f * fold(S.aP2);
+            const float aQ[6] = {P - 1.5f * fold(S.dxx), P - 1.5f * fold(S.dyy),
+                                 P - 1.5f * fold(S.dzz), -0.75f * fold(S.oxy),
+                                 -0.75f * fold(S.oxz), -0.75f * fold(S.oyz)};
             cell_add(L.cid[j], fold(S.ax), fold(S.ay), fold(S.az), fold(S.aM), aQ);
         }
     }
