@@ -527,15 +527,14 @@ struct AdjointPolicy : Fp32Rings {
     __device__ __forceinline__ void reduce_chunk(int t0, int lane) {
         __syncwarp();
         if (lane < 6 * NP) {
-            float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;  // four short chains
+            float a[8];  // eight short chains
 #pragma unroll
-            for (int r = 0; r < 32; r += 4) {
-                s0 += W->red[r * ADJ_ROW + lane];
-                s1 += W->red[(r + 1) * ADJ_ROW + lane];
-                s2 += W->red[(r + 2) * ADJ_ROW + lane];
-                s3 += W->red[(r + 3) * ADJ_ROW + lane];
-            }
-            const float s = (s0 + s1) + (s2 + s3);
+            for (int k = 0; k < 8; ++k) a[k] = W->red[k * ADJ_ROW + lane];
+#pragma unroll
+            for (int r = 8; r < 32; r += 8)
+#pragma unroll
+                for (int k = 0; k < 8; ++k) a[k] += W->red[(r + k) * ADJ_ROW + lane];
+            const float s = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
             const int t = t0 + 2 * (lane / 6) + (lane & 1);
             if (t < gc) W->tacc[3 * t + (lane % 6) / 2] += s;
         }
