@@ -372,20 +372,29 @@ struct CellDup {
     f32x2 x, y, z, M, bx, by, bz, bw, cx, cy, cw, M3, cw5;
 };
 
-__device__ __forceinline__ void pc_vjp2(const CellDup &C, const TargetPair &T, f32x2 eps2,
-                                        f32x2 &gx, f32x2 &gy, f32x2 &gz, f32x2 &gM, f32x2 &u3,
-                                        f32x2 &u5, f32x2 &lr, f32x2 &vx, f32x2 &vy, f32x2 &vz,
-                                        f32x2 &rx, f32x2 &ry, f32x2 &rz) {
-    const f32x2 k_m25 = dup2(-2.5f), k_175 = dup2(17.5f), k_m5 = dup2(-5.0f);
-    rx = add2(C.x, T.nx);
-    ry = add2(C.y, T.ny);
-    rz = add2(C.z, T.nz);
+// u = 1/s of one cell and two targets (the first, latency-bound part of the
+// p-c VJP, taken for a whole chunk before the rest).
+__device__ __forceinline__ f32x2 pc_inv_s(const CellDup &C, f32x2 nx, f32x2 ny, f32x2 nz,
+                                          f32x2 eps2) {
+    const f32x2 rx = add2(C.x, nx), ry = add2(C.y, ny), rz = add2(C.z, nz);
     f32x2 s2 = fma2(rx, rx, eps2);
     s2 = fma2(ry, ry, s2);
     s2 = fma2(rz, rz, s2);
     float s0, s1;
     u2(s2, s0, s1);
-    const f32x2 u = p2(rsqrtf(s0), rsqrtf(s1));
+    return p2(rsqrtf(s0), rsqrtf(s1));
+}
+
+template <bool GIVEN_U>
+__device__ __forceinline__ void pc_vjp2(const CellDup &C, const TargetPair &T, f32x2 eps2,
+                                        f32x2 ug, f32x2 &gx, f32x2 &gy, f32x2 &gz, f32x2 &gM,
+                                        f32x2 &u3, f32x2 &u5, f32x2 &lr, f32x2 &vx, f32x2 &vy,
+                                        f32x2 &vz, f32x2 &rx, f32x2 &ry, f32x2 &rz) {
+    const f32x2 k_m25 = dup2(-2.5f), k_175 = dup2(17.5f), k_m5 = dup2(-5.0f);
+    rx = add2(C.x, T.nx);
+    ry = add2(C.y, T.ny);
+    rz = add2(C.z, T.nz);
+    const f32x2 u = GIVEN_U ? ug : pc_inv_s(C, T.nx, T.ny, T.nz, eps2);
     const f32x2 w = mul2(u, u);
     u3 = mul2(u, w);
     u5 = mul2(u3, w);
@@ -550,11 +559,12 @@ struct AdjointPolicy : Fp32Rings {
     };
 
     // Target pair tp of the chunk at t0 into the cell adjoint and the row.
+    template <bool GIVEN_U>
     __device__ __forceinline__ void pc_pair(const CellDup &C, f32x2 e2, int t0, int tp, int lane,
-                                            PcAcc &S) {
+                                            PcAcc &S, f32x2 ug = 0ull) {
         const TargetPair T2 = load_targets(T, (t0 >> 1) + tp);
         f32x2 gx, gy, gz, gM, u3, u5, lr, vx, vy, vz, rx, ry, rz;
-        pc_vjp2(C, T2, e2, gx, gy, gz, gM, u3, u5, lr, vx, vy, vz, rx, ry, rz);
+        pc_vjp2<GIVEN_U>(C, T2, e2, ug, gx, gy, gz, gM, u3, u5, lr, vx, vy, vz, rx, ry, rz);
         S.ax = add2(S.ax, gx);
         S.ay = add2(S.ay, gy);
         S.az = add2(S.az, gz);
@@ -592,14 +602,23 @@ struct AdjointPolicy : Fp32Rings {
         PcAcc S;
         int t0 = 0;
         for (; t0 + ADJ_CHUNK <= gc; t0 += ADJ_CHUNK) {
+            // the chunk's four reciprocal distances first: their MUFU
+            // latencies overlap instead of heading four dependent chains
+            f32x2 uu[ADJ_CHUNK / 2];
 #pragma unroll
-            for (int tp = 0; tp < ADJ_CHUNK / 2; ++tp) pc_pair(C, e2, t0, tp, lane, S);
+            for (int tp = 0; tp < ADJ_CHUNK / 2; ++tp) {
+                const int p = (t0 >> 1) + tp;
+                const ulonglong2 a = lds2(T->nxy[p]), b = lds2(T->nzi[p]);
+                uu[tp] = pc_inv_s(C, a.x, a.y, b.x, e2);
+            }
+#pragma unroll
+            for (int tp = 0; tp < ADJ_CHUNK / 2; ++tp) pc_pair<true>(C, e2, t0, tp, lane, S, uu[tp]);
             reduce_chunk<ADJ_CHUNK / 2>(t0, lane);
         }
         const int np = (gc - t0 + 1) >> 1;  // one code copy for the ragged tail
         if (np > 0) {
 #pragma unroll 1
-            for (int tp = 0; tp < np; ++tp) pc_pair(C, e2, t0, tp, lane, S);
+            for (int tp = 0; tp < np; ++tp) pc_pair<false>(C, e2, t0, tp, lane, S);
             reduce_chunk<ADJ_CHUNK / 2>(t0, lane);
         }
         if (v) {
