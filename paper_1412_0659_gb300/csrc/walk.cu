@@ -426,16 +426,23 @@ __device__ __forceinline__ void pc_vjp2(const CellDup &C, const TargetPair &T, f
 // Gradient of lambda.a + mu phi for one p-p source on two targets (without G):
 //   g_r = m u^3 (lambda + (mu - 3 w lr) r),  gm = lr u^3 - mu u;
 // zero for the self pair (u is set to 0, which also avoids r = 0 at eps = 0).
-__device__ __forceinline__ void pp_vjp2(f32x2 sx, f32x2 sy, f32x2 sz, f32x2 sm, int sid,
-                                        const TargetPair &T, f32x2 eps2, f32x2 &gx, f32x2 &gy,
-                                        f32x2 &gz, f32x2 &gm) {
-    const f32x2 rx = add2(sx, T.nx), ry = add2(sy, T.ny), rz = add2(sz, T.nz);
+__device__ __forceinline__ f32x2 pp_inv_s(f32x2 sx, f32x2 sy, f32x2 sz, int sid, f32x2 nx,
+                                          f32x2 ny, f32x2 nz, int2 id, f32x2 eps2) {
+    const f32x2 rx = add2(sx, nx), ry = add2(sy, ny), rz = add2(sz, nz);
     f32x2 s2 = fma2(rx, rx, eps2);
     s2 = fma2(ry, ry, s2);
     s2 = fma2(rz, rz, s2);
     float s0, s1;
     u2(s2, s0, s1);
-    const f32x2 u = p2(sid == T.id.x ? 0.0f : rsqrtf(s0), sid == T.id.y ? 0.0f : rsqrtf(s1));
+    return p2(sid == id.x ? 0.0f : rsqrtf(s0), sid == id.y ? 0.0f : rsqrtf(s1));
+}
+
+template <bool GIVEN_U>
+__device__ __forceinline__ void pp_vjp2(f32x2 sx, f32x2 sy, f32x2 sz, f32x2 sm, int sid,
+                                        const TargetPair &T, f32x2 eps2, f32x2 ug, f32x2 &gx,
+                                        f32x2 &gy, f32x2 &gz, f32x2 &gm) {
+    const f32x2 rx = add2(sx, T.nx), ry = add2(sy, T.ny), rz = add2(sz, T.nz);
+    const f32x2 u = GIVEN_U ? ug : pp_inv_s(sx, sy, sz, sid, T.nx, T.ny, T.nz, T.id, eps2);
     const f32x2 w = mul2(u, u);
     const f32x2 u3 = mul2(u, w);
     const f32x2 lr = fma2(T.lx, rx, fma2(T.ly, ry, mul2(T.lz, rz)));
@@ -646,12 +653,13 @@ struct AdjointPolicy : Fp32Rings {
         atomicAdd(&cell_adj[2 * nn + node], make_float4(G * aQ[4], G * aQ[5], 0.0f, 0.0f));
     }
 
+    template <bool GIVEN_U>
     __device__ __forceinline__ void pp_pair(f32x2 sx, f32x2 sy, f32x2 sz, f32x2 sm, int sid,
                                             f32x2 e2, int t0, int tp, int lane, f32x2 &ax,
-                                            f32x2 &ay, f32x2 &az, f32x2 &am) {
+                                            f32x2 &ay, f32x2 &az, f32x2 &am, f32x2 ug = 0ull) {
         const TargetPair T2 = load_targets(T, (t0 >> 1) + tp);
         f32x2 gx, gy, gz, gm;
-        pp_vjp2(sx, sy, sz, sm, sid, T2, e2, gx, gy, gz, gm);
+        pp_vjp2<GIVEN_U>(sx, sy, sz, sm, sid, T2, e2, ug, gx, gy, gz, gm);
         ax = add2(ax, gx);
         ay = add2(ay, gy);
         az = add2(az, gz);
@@ -671,16 +679,26 @@ struct AdjointPolicy : Fp32Rings {
         f32x2 ax = 0ull, ay = 0ull, az = 0ull, am = 0ull;
         int t0 = 0;
         for (; t0 + ADJ_CHUNK <= gc; t0 += ADJ_CHUNK) {
+            f32x2 uu[ADJ_CHUNK / 2];  // reciprocal distances first, as for p-c
+#pragma unroll
+            for (int tp = 0; tp < ADJ_CHUNK / 2; ++tp) {
+                const int p = (t0 >> 1) + tp;
+                const ulonglong2 a = lds2(T->nxy[p]), b = lds2(T->nzi[p]);
+                float i0, i1;
+                u2(b.y, i0, i1);
+                uu[tp] = pp_inv_s(sx, sy, sz, sid, a.x, a.y, b.x,
+                                  make_int2(__float_as_int(i0), __float_as_int(i1)), e2);
+            }
 #pragma unroll
             for (int tp = 0; tp < ADJ_CHUNK / 2; ++tp)
-                pp_pair(sx, sy, sz, sm, sid, e2, t0, tp, lane, ax, ay, az, am);
+                pp_pair<true>(sx, sy, sz, sm, sid, e2, t0, tp, lane, ax, ay, az, am, uu[tp]);
             reduce_chunk<ADJ_CHUNK / 2>(t0, lane);
         }
         const int np = (gc - t0 + 1) >> 1;
         if (np > 0) {
 #pragma unroll 1
             for (int tp = 0; tp < np; ++tp)
-                pp_pair(sx, sy, sz, sm, sid, e2, t0, tp, lane, ax, ay, az, am);
+                pp_pair<false>(sx, sy, sz, sm, sid, e2, t0, tp, lane, ax, ay, az, am);
             reduce_chunk<ADJ_CHUNK / 2>(t0, lane);
         }
         if (v) atomicAdd(&part_adj[sid], make_float4(G * fold(ax), G * fold(ay), G * fold(az),
