@@ -72,3 +72,30 @@ def test_product_sources_do_not_reference_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "bonsai_oracle" not in txt, f
+
+
+def test_galaxy_parameters_and_checks_without_gpu():
+    """bonsai_galaxy_sec4 is host code: the Sec. IV counts for n particles
+    (those of the oracle's generator), and the generator's argument checks
+    reject bad models before any CUDA call."""
+    from oracle import galaxy_ics as gi
+    from paper_1412_0659_gb300 import capi
+    for n in (1000, 1 << 20, (1 << 32) - 1):
+        g = capi.bonsai_galaxy_sec4(n, 7)
+        assert (g.n_halo, g.n_disk, g.n_bulge) == gi.counts(n)
+        o = gi.milky_way_sec4(n, 7)
+        for k in ("G", "M_halo", "a_halo", "M_bulge", "a_bulge", "r_t", "dr_t", "M_disk", "R_d",
+                  "z0", "R_max", "Q", "R_Q"):
+            assert getattr(g, k) == getattr(o, k), k
+    for n in (0, -5, 1 << 32):
+        with pytest.raises(capi.BonsaiError):
+            capi.bonsai_galaxy_sec4(n, 1)
+    lib = capi.load()
+    for field, value in (("n_halo", -1), ("a_bulge", 0.0), ("Q", float("nan")), ("M_disk", 0.0),
+                         ("R_Q", -1.0), ("G", float("inf"))):
+        g = capi.bonsai_galaxy_sec4(4096, 1)
+        setattr(g, field, value)
+        rc = lib.bonsai_galaxy_generate(ctypes.byref(g), None, None, None, None)
+        assert rc == capi.BONSAI_EINVAL, field
+    g = capi.bonsai_galaxy_sec4(4096, 1)
+    assert lib.bonsai_galaxy_generate(ctypes.byref(g), None, None, None, None) == capi.BONSAI_EINVAL

@@ -170,3 +170,26 @@ def test_spheroids_stay_in_equilibrium_under_the_tree_code():
     assert cold["bulge"][1] < -0.08, cold
     full = _evolve_lagrangian(base)
     assert np.max(np.abs(full["halo"])) < 0.01, full
+
+
+def test_generated_model_conserves_energy_under_the_tree_code():
+    """The Sec. IV model generated on the device at 2^22 particles goes
+    straight into the tree code: 200 KDK steps of 0.1 Myr at theta = 0.4,
+    eps = 10 pc keep the total energy within 1e-5 and the net momentum
+    within 1e-5 of the summed |m v|."""
+    from paper_1412_0659_gb300 import TreeGravity, galaxy
+    g = galaxy.sec4(1 << 22, 1007)
+    pos, vel, mass = galaxy.generate(g)
+    with TreeGravity(G=g.G, theta=0.4, eps=0.01) as t:
+        t.build(pos, mass)
+        t.set_velocities(vel)
+        t.forces()
+        d0 = t.diagnostics()
+        for _ in range(200):
+            t.step(0.1)
+        d1 = t.diagnostics()
+        v = t.state()[1]
+    assert abs(d1["E_tot"] / d0["E_tot"] - 1) < 1e-5, (d0, d1)
+    p = np.array([d1["Px"], d1["Py"], d1["Pz"]])
+    scale = float((mass * torch.sqrt((v * v).sum(0))).sum())
+    assert np.linalg.norm(p) < 1e-5 * scale
