@@ -140,9 +140,37 @@ def walk_traffic(workload: str):
     return WALK_TRAFFIC["bytes"].get(workload)
 
 
-def _workload(name: str, rank: int):
+def _sec4_model(n: int, seed: int, on_gpu: bool):
+    """The Sec. IV model (NFW halo, exponential disk, Hernquist bulge) as a
+    workload: generated by the library on the device for our arm, by the
+    FP64 oracle on the host for the reference arm (the two agree particle
+    for particle)."""
     import workloads
-    if name == "milky-way-2^23":
+    if on_gpu:
+        from paper_1412_0659_gb300 import galaxy
+        gal = galaxy.sec4(n, seed)
+        pos, vel, mass = [x.cpu().numpy() for x in galaxy.generate(gal)]
+        counts = (int(gal.n_halo), int(gal.n_disk), int(gal.n_bulge))
+        G = gal.G
+    else:
+        from oracle import galaxy_ics
+        gal = galaxy_ics.milky_way_sec4(n, seed)
+        pos, vel, mass = galaxy_ics.generate(gal)
+        counts = (gal.n_halo, gal.n_disk, gal.n_bulge)
+        G = gal.G
+    h, d, b = counts
+    comps = {"halo": (0, h), "disk": (h, d), "bulge": (h + d, b)}
+    return workloads.Model(pos, vel, mass, G, 0.01, 0.4, 0.1, f"sec4-{n}", comps)
+
+
+def _workload(name: str, rank: int, on_gpu: bool = True):
+    import workloads
+    if name == "sec4-2^23":
+        m = _sec4_model(1 << 23, 1006 + 17 * rank, on_gpu)
+        desc = ("Sec. IV Milky Way N=2^23 generated on the fly (NFW halo 6.0e11 Msun a=15 kpc, exp. "
+                "disk 5e10 Msun Rd=2.5 kpc z0=0.3 kpc, Hernquist bulge 4.6e9 Msun a=0.5 kpc; counts "
+                "in the paper's ratio), theta=0.4, eps=10 pc, dt=0.1 Myr")
+    elif name == "milky-way-2^23":
         m = workloads.milky_way(1 << 23, seed=1002 + 17 * rank, eps=0.01, theta=0.4, dt=0.1)
         desc = ("Milky-Way-like N=2^23 (Hernquist halo 1e12 Msun a=30 kpc cut 200 kpc, exp. disk "
                 "5e10 Msun Rd=2.5 kpc z0=0.3 kpc Q=1.5, Hernquist bulge 1e10 Msun a=0.5 kpc; "
@@ -481,7 +509,7 @@ def run_reference(args):
     rank, world, local = _dist()
     if rank != 0:
         return
-    m, desc = _workload(args.workload, 0)
+    m, desc = _workload(args.workload, 0, on_gpu=False)
     for _ in range(args.warmup):
         pass
     vals = []
@@ -510,7 +538,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="milky-way-2^23",
                     choices=["milky-way-2^23", "milky-way-2^20", "milky-way-2^25", "milky-way-2^28",
-                             "halo-disk-2^20", "plummer-2^14"])
+                             "halo-disk-2^20", "plummer-2^14", "sec4-2^23"])
     ap.add_argument("--cpu-groups", type=int, default=24000,
                     help="groups walked by the CPU oracle sample (about 10 s of CPU work at 2^23)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
