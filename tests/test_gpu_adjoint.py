@@ -70,6 +70,27 @@ def test_force_vjp_matches_oracle(name, with_mu):
     assert np.median(em) <= 2e-6 and np.quantile(em, 0.999) <= 1e-4, (np.median(em), np.quantile(em, 0.999))
 
 
+@pytest.mark.parametrize("n", [1, 2, 3, 9, 17, 33, 65, 130])
+def test_force_vjp_small_groups(n):
+    """Few-particle models whose groups have 1 to 65 members: every ragged
+    chunk length (1 to 4 target pairs, with and without a full chunk of 8
+    before it) and single-group trees, against the oracle."""
+    m = workloads.plummer(n, seed=300 + n) if n > 1 else workloads.plummer(2, seed=301)
+    if n == 1:
+        m.pos, m.vel, m.mass = m.pos[:, :1].copy(), m.vel[:, :1].copy(), m.mass[:1].copy()
+    rng = np.random.default_rng(n)
+    lam = rng.normal(size=(3, m.n))
+    mu = rng.normal(size=m.n)
+    gx, gm = _gpu_vjp(m, 0.4, 0.01, 1.0, lam, mu)
+    ox, om = _oracle_vjp(m, 0.4, 0.01, 1.0, lam, mu)
+    if n == 1:  # a lone particle: no force, no gradient
+        assert np.all(gx == 0) and np.all(ox == 0)
+        assert np.allclose(gm, om, atol=1e-12)
+        return
+    ex, em = _rel(gx, ox), _rel(gm, om)
+    assert np.max(ex) <= 1e-4 and np.max(em) <= 1e-4, (np.max(ex), np.max(em))
+
+
 def test_force_vjp_tends_to_direct_adjoint():
     m = workloads.plummer(3000, seed=61)
     rng = np.random.default_rng(62)
