@@ -444,8 +444,8 @@ int bonsai_galaxy_sec4(bonsai_galaxy *g, int64_t n, uint64_t seed);
  * Twelve kernels run on stream (a cudaStream_t, NULL = legacy default); the
  * call returns after they finish.  n = 0 does nothing.
  * Errors: EINVAL (null pointer with n > 0, a negative count, n >= 2^32, a
- * non-positive or non-finite length, G, Q or R_Q, a negative mass, zero mass
- * for a component with particles), ENOMEM, ECUDA. */
+ * non-positive or non-finite length, G, Q or R_Q, R_max > 200 R_d, a
+ * negative mass, zero mass for a component with particles), ENOMEM, ECUDA. */
 int bonsai_galaxy_generate(const bonsai_galaxy *g, double *pos, double *vel, double *mass,
                            void *stream);
 

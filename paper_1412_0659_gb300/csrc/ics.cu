@@ -137,7 +137,8 @@ __device__ double block_exclusive_scan(double v, double *sh) {
 
 constexpr int SCAN_T = 1024;
 constexpr int PER_T = K / SCAN_T;
-static_assert(K % SCAN_T == 0 && KD % SCAN_T == 0, "scan shape");
+static_assert(K % SCAN_T == 0, "scan shape");
+static_assert(KD % 256 == 0 && KD % 64 == 0, "disk launch shapes");
 
 // ---------------------------------------------------------------- step 2
 // S[k] = S0 + sum_{j<k} (F_j + F_{j+1}) dl / 2, S0 the closed-form mass of
@@ -686,6 +687,7 @@ int check(const bonsai_galaxy *g) {
         if (Ns[c] > 0 && !(Ms[c] > 0.0)) return BONSAI_EINVAL;
     }
     if (!(g->M_halo + g->M_disk + g->M_bulge > 0.0)) return BONSAI_EINVAL;
+    if (g->R_max > 200.0 * g->R_d) return BONSAI_EINVAL;  // Bessel arguments up to 100
     return BONSAI_OK;
 }
 
