@@ -12,6 +12,17 @@ value = sum over timed steps of (23 n_pp + 65 n_pc) / timed wall time on the
 device (CUDA events, max over ranks).  The state (about 1.7 GB) is far larger
 than the 129 MB L2, so no flush is needed between steps.
 
+Keys beside the contract's: ``roofline`` (the walk kernel against the
+derived FP32 peak, with its captured DRAM bytes), ``e2e`` (tree_solve_host
+with host buffers), ``cpu_baseline`` (the oracle on the host cores),
+``adjoint`` (forward and force VJP on the same tree), ``direct`` (direct
+summation of 2^16 targets, the paper's Fig. 1 comparison), ``io`` (snapshot
+save / load and the face-on surface density), ``ics`` (the Sec. IV model
+generated on the device), ``domains`` (eight domains with local essential
+trees on this GPU), ``clocks`` and ``gpu_launches``.  ``--no-adjoint``,
+``--no-direct``, ``--no-io``, ``--no-ics`` and ``--domains 0`` skip the
+extras; ``--workload`` selects another configuration.
+
 ``--impl reference`` times the FP64 CPU oracle (the stand-in for the
 paper's own code, which is not available) on a bounded sample of the same
 workload on the host cores.
