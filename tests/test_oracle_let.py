@@ -4,7 +4,9 @@ whose trees, built in the global cube, carry exactly the global keys; the
 cells marked for a remote domain are closed under parents and include every
 child of an opened cell; and the force assembled from the own tree plus the
 other domains' trees equals direct summation as theta -> 0 and follows the
-single global tree at theta = 0.4."""
+single global tree at theta = 0.4; and the marks equal, cell for cell, the
+union of the cells reached by every destination group's walk, recomputed
+here in plain Python from the definition."""
 import numpy as np
 import pytest
 
@@ -90,3 +92,42 @@ def test_assembled_forces_follow_the_global_tree(R):
     e_glob = np.linalg.norm(ag[:, ::7] - ad, axis=0) / np.linalg.norm(ad, axis=0)
     # the decomposition approximates direct summation as well as one tree does
     assert np.median(e_dom) < 2.0 * np.median(e_glob) and np.median(e_dom) < 1e-3
+
+
+def _walk_visits(src, dst, theta):
+    """The definition of a local essential tree, walked in plain Python: the
+    cells of src reached by the breadth-first walk of each of dst's groups
+    (the opening test in FP32, each operation rounded, on the FP32 cell and
+    group-box inputs), and those among them that the test opens."""
+    com_f, r2 = src.cell_mac(theta)
+    gc, gh = dst.group_box_f32()
+    nd = src.nodes()
+    zero = np.float32(0.0)
+    v = np.zeros(src.nnodes, bool)
+    o = np.zeros(src.nnodes, bool)
+    for g in range(dst.ngroups):
+        frontier = [0]
+        while frontier:
+            nxt = []
+            for c in frontier:
+                v[c] = True
+                a = [max(np.abs(com_f[d, c] - gc[d, g]) - gh[d, g], zero) for d in range(3)]
+                d2 = (a[0] * a[0] + a[1] * a[1]) + a[2] * a[2]
+                if d2 < r2[c]:
+                    o[c] = True
+                    first, k = int(nd["child"][c]), int(nd["nchild"][c])
+                    nxt.extend(range(first, first + k))
+            frontier = nxt
+    return v, o
+
+
+@pytest.mark.parametrize("pair", [(3, 0), (0, 1)])
+def test_let_marks_equal_the_union_of_the_group_walks(pair):
+    m = workloads.milky_way(20000, seed=41)
+    _, _, _, trees = _domains(m, 4)
+    src, dst = trees[pair[0]], trees[pair[1]]
+    v, o = src.let_mark(dst, 0.4)
+    vw, ow = _walk_visits(src, dst, 0.4)
+    assert np.array_equal(v, vw) and np.array_equal(o, ow)
+    if pair == (3, 0):  # distant domains: only part of the tree is sent
+        assert v.sum() < 0.8 * src.nnodes
