@@ -208,3 +208,34 @@ def test_all_particles_at_one_point(orc):
     assert np.all(acc == 0.0)
     assert np.allclose(pot, -G * (n - 1) * m / eps, rtol=1e-14)
     assert (npp, npc) == (n * n, 0)
+
+
+def test_group_lists_follow_the_opening_test(orc):
+    """Each group's lists, recomputed from the definition in plain Python: a
+    breadth-first walk from the root that accepts a cell when the FP32
+    opening test (each operation rounded) fails and otherwise opens it,
+    descending into an internal cell and taking an opened leaf's particles;
+    the oracle's accepted cells and opened leaves are exactly these sets."""
+    mdl = workloads.milky_way(12000, seed=45)
+    t = orc.Tree(mdl.pos, mdl.mass)
+    com_f, r2 = t.cell_mac(0.4)
+    gc, gh = t.group_box_f32()
+    nd = t.nodes()
+    zero = np.float32(0.0)
+    for gi in range(0, t.ngroups, max(1, t.ngroups // 40)):
+        acc, opened_leaves, frontier = [], [], [0]
+        while frontier:
+            nxt = []
+            for c in frontier:
+                a = [max(np.abs(com_f[d, c] - gc[d, gi]) - gh[d, gi], zero) for d in range(3)]
+                if (a[0] * a[0] + a[1] * a[1]) + a[2] * a[2] < r2[c]:
+                    if nd["nchild"][c] == 0:
+                        opened_leaves.append(c)
+                    else:
+                        nxt.extend(range(int(nd["child"][c]), int(nd["child"][c] + nd["nchild"][c])))
+                else:
+                    acc.append(c)
+            frontier = nxt
+        pc, leaves = t.group_lists(0.4, gi)
+        assert sorted(pc.tolist()) == sorted(acc)
+        assert sorted(leaves.tolist()) == sorted(opened_leaves)
