@@ -403,10 +403,11 @@ int bonsai_sfc_order_noalloc(const double *pos, const double *mass, int64_t n, u
  * (the epicyclic approximation, not a disk distribution function).  The
  * spheroids' distribution functions see the disk through its spherically
  * averaged mass, so they are in equilibrium in that potential; where the
- * flat disk dominates the inner mass the bulge adjusts.  Every particle draws its uniforms from Philox4x32-10 (Salmon
- * et al., SC11) with counter (particle index, component, call, 0) and key
- * (seed low word, seed high word), so the output depends on the seed and n
- * only, not on the launch shape.  Units: kpc, Msun, Myr for the defaults. */
+ * flat disk dominates the inner mass the bulge adjusts.  Every particle
+ * draws its uniforms from Philox4x32-10 (Salmon et al., SC11) with counter
+ * (particle index, component, call, 0) and key (seed low word, seed high
+ * word), so the output depends on the seed and n only, not on the launch
+ * shape.  Units: kpc, Msun, Myr for the defaults. */
 
 #define BONSAI_ICS_K 4096        /* radial nodes of the spheroid tables (1e-4 .. 600, log) */
 #define BONSAI_ICS_V 256         /* speed-fraction nodes per velocity-table row */
