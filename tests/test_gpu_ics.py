@@ -5,7 +5,6 @@ sampled model within the rounding of the tables carried through their
 inversion, at small sizes with ragged component counts and at the 2^23
 benchmark size; argument errors; and the sampled spheroids stay in
 equilibrium when the tree code evolves them."""
-import math
 
 import numpy as np
 import pytest
