@@ -339,6 +339,22 @@ int tree_debug_multipoles(bonsai_ctx *ctx, double *M, double *com, double *Q);
 int tree_debug_groups(bonsai_ctx *ctx, uint32_t *first, uint32_t *count, int32_t *npp,
                       int32_t *npc);
 
+/* The interaction lists of every group, as walked by the last tree_forces
+ * (same tree, same opening angle; Sec. I.A: the walk accepts a cell as one
+ * particle-cell interaction or opens it, an opened leaf giving its
+ * particles as particle-particle interactions).  pc_off and pp_off are
+ * device int64 [n_groups + 1]: exclusive prefix sums of the per-group p-c
+ * list lengths and p-p source counts that tree_debug_groups returns.  Group
+ * g's accepted cells (node indices, breadth-first numbering) go to
+ * pc_cells[pc_off[g] .. pc_off[g+1]) and its p-p sources (key-sorted
+ * particle indices) to pp_sources[pp_off[g] .. pp_off[g+1]), in walk
+ * order; both device uint32, owned by the caller.  Nothing is written
+ * outside a group's range.  Errors: EINVAL (null pointer), ESTATE (no
+ * forces yet), EOVERFLOW (a group's lists do not have the lengths its
+ * offsets give). */
+int tree_debug_lists(bonsai_ctx *ctx, const int64_t *pc_off, const int64_t *pp_off,
+                     uint32_t *pc_cells, uint32_t *pp_sources);
+
 /* Limit the walk's per-warp frontier to cap entries (0 restores the full
  * capacity of 16384).  For tests of the overflow path: a walk that needs
  * more sets the device status word, and tree_forces / tree_forces_vjp

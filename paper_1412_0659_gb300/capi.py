@@ -37,7 +37,7 @@ EXPORTED = (
     "tree_save_snapshot", "tree_load_snapshot", "tree_surface_density",
     "tree_build_cube", "tree_domain_state", "let_create", "let_destroy", "let_build", "let_get_info",
     "let_debug_cells", "let_forces", "bonsai_galaxy_sec4", "bonsai_galaxy_generate",
-    "bonsai_galaxy_tables",
+    "bonsai_galaxy_tables", "tree_debug_lists",
 )
 
 BONSAI_NOALLOC_MAX_N = 1 << 20
@@ -115,6 +115,7 @@ def load(path: str | None = None):
             "tree_debug_nodes": (i32, [P, P, P, P, P, P]),
             "tree_debug_multipoles": (i32, [P, P, P, P]),
             "tree_debug_groups": (i32, [P, P, P, P, P]),
+            "tree_debug_lists": (i32, [P, P, P, P, P]),
             "bonsai_strerror": (ctypes.c_char_p, [i32]),
             "bonsai_sfc_order_noalloc": (i32, [P, P, i64, P, P, P, P]),
             "tree_forces_vjp": (i32, [P, P, P, P, P]),
@@ -392,6 +393,13 @@ def tree_debug_multipoles(ctx, M=None, com=None, Q=None) -> None:
 def tree_debug_groups(ctx, first=None, count=None, npp=None, npc=None) -> None:
     _check(load().tree_debug_groups(ctx, _ptr(first), _ptr(count), _ptr(npp), _ptr(npc)),
            "tree_debug_groups")
+
+
+def tree_debug_lists(ctx, pc_off, pp_off, pc_cells, pp_sources) -> None:
+    """Each group's accepted cells and p-p sources at the given offsets
+    (int64 CUDA tensors [n_groups + 1]; outputs int32 CUDA tensors)."""
+    _check(load().tree_debug_lists(ctx, _ptr(pc_off), _ptr(pp_off), _ptr(pc_cells), _ptr(pp_sources)),
+           "tree_debug_lists")
 
 
 def bonsai_strerror(code: int) -> str:

@@ -578,6 +578,17 @@ int tree_debug_groups(bonsai_ctx *c, uint32_t *first, uint32_t *count, int32_t *
     return BONSAI_OK;
 }
 
+int tree_debug_lists(bonsai_ctx *c, const int64_t *pc_off, const int64_t *pp_off,
+                     uint32_t *pc_cells, uint32_t *pp_sources) {
+    if (!c || !pc_off || !pp_off || !pc_cells || !pp_sources) return BONSAI_EINVAL;
+    if (!c->have_tree || !c->have_forces) return BONSAI_ESTATE;
+    BGB_CUDA(cudaMemsetAsync(&c->dsc->status, 0, 3 * sizeof(int32_t), c->stream));
+    int rc = walk_lists(c, pc_off, pp_off, pc_cells, pp_sources);
+    if (rc) return rc;
+    if ((rc = read_scalars(c))) return rc;
+    return (c->hsc->status & ST_OVERFLOW) ? BONSAI_EOVERFLOW : BONSAI_OK;
+}
+
 int tree_debug_set_frontier_capacity(bonsai_ctx *c, int cap) {
     if (!c || cap < 0) return BONSAI_EINVAL;
     c->walk_fcap = cap;

@@ -198,6 +198,8 @@ struct LetTree {
 int walk_force(bonsai_ctx *c, float theta, float eps, float *acc_caller, float *pot_caller);
 int walk_let(bonsai_ctx *dst, const LetTree &t, float eps);
 int walk_force_fp64(bonsai_ctx *c, float eps, double *acc, double *pot);
+int walk_lists(bonsai_ctx *c, const int64_t *pc_off, const int64_t *pp_off, uint32_t *pc_out,
+               uint32_t *pp_out);
 // direct.cu
 int direct_forces(bonsai_ctx *c, const int64_t *targets, int64_t nt, float eps, double *acc,
                   double *pot);

@@ -88,6 +88,9 @@ struct WalkArgs {
     const double *ndM, *ndcom, *ndQ;  // [nn], [3][nn], [6][nn]
     double *acc64, *pot64;         // caller order [3][n], [n] or null
     double G64, eps2_64;
+    // list recording (parity tests): per-group offsets [ngroups + 1] and outputs
+    const int64_t *lpc_off, *lpp_off;
+    uint32_t *lpc_out, *lpp_out;
 };
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
@@ -875,6 +878,54 @@ __device__ __forceinline__ void do_flush_pp(Fp64Policy &pol, const WarpLists64 &
 }
 
 // ---------------------------------------------------------------------------
+// List recording: the same walk, writing each group's accepted cells (node
+// index) and opened-leaf particles (sorted index) in walk order at the
+// group's offsets, so that the parity tests can compare list membership with
+// the oracle's.  A group whose lists do not fit its offsets sets the
+// overflow bit and writes nothing past its end.
+// ---------------------------------------------------------------------------
+
+struct ListPolicy : Fp32Rings {
+    uint32_t *pc_out, *pp_out;
+    int64_t pc_at, pc_end, pp_at, pp_end;
+    bool over;
+
+    __device__ __forceinline__ void begin(const WalkArgs &A, WarpTargets *, uint32_t g, uint32_t,
+                                          uint32_t, float4, float4, int) {
+        pc_out = A.lpc_out;
+        pp_out = A.lpp_out;
+        pc_at = A.lpc_off[g];
+        pc_end = A.lpc_off[g + 1];
+        pp_at = A.lpp_off[g];
+        pp_end = A.lpp_off[g + 1];
+        over = false;
+    }
+    __device__ __forceinline__ void flush_pc(const WarpLists &L, int hb, int cnt, int lane) {
+        if (pc_at + cnt > pc_end) over = true;
+        else if (lane < cnt) pc_out[pc_at + lane] = (uint32_t)L.cid[hb + lane];
+        pc_at += cnt;
+    }
+    __device__ __forceinline__ void flush_pp(const WarpLists &L, int hb, int cnt, int lane) {
+        if (pp_at + cnt > pp_end) over = true;
+        else if (lane < cnt) pp_out[pp_at + lane] = (uint32_t)L.pid[hb + lane];
+        pp_at += cnt;
+    }
+    __device__ __forceinline__ void finish(const WalkArgs &A, uint32_t, uint32_t, int lane) {
+        if (lane == 0 && (over || pc_at != pc_end || pp_at != pp_end))
+            atomicOr(&A.sc->status, ST_OVERFLOW);
+    }
+};
+
+__device__ __forceinline__ void do_flush_pc(ListPolicy &pol, const WarpLists &L, int hb, int cnt,
+                                            int lane) {
+    pol.flush_pc(L, hb, cnt, lane);
+}
+__device__ __forceinline__ void do_flush_pp(ListPolicy &pol, const WarpLists &L, int hb, int cnt,
+                                            int lane) {
+    pol.flush_pp(L, hb, cnt, lane);
+}
+
+// ---------------------------------------------------------------------------
 // The traversal
 // ---------------------------------------------------------------------------
 
@@ -1039,6 +1090,24 @@ __global__ void __launch_bounds__(WALK_WARPS * 32, 4) k_walk_adjoint(const WalkA
     }
 }
 
+__global__ void __launch_bounds__(WALK_WARPS * 32) k_walk_lists(const WalkArgs A) {
+    __shared__ WarpLists lists[WALK_WARPS];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const uint32_t lt = lanemask_lt();
+    const int64_t gw = (int64_t)blockIdx.x * WALK_WARPS + wib;
+    uint32_t *fa = A.frontier + gw * 2 * FCAP;
+    uint32_t *fb = fa + FCAP;
+    while (true) {
+        uint32_t g = 0;
+        if (lane == 0) g = atomicAdd(&A.sc->group_counter, 1u);
+        g = __shfl_sync(0xffffffffu, g, 0);
+        if (g >= A.ngroups) break;
+        ListPolicy pol;
+        walk_group(A, lists[wib], nullptr, pol, g, fa, fb, lane, lt);
+    }
+}
+
 __global__ void __launch_bounds__(WALK_WARPS * 32) k_walk_fp64(const WalkArgs A) {
     __shared__ WarpLists64 lists[WALK_WARPS];
     const int lane = threadIdx.x & 31;
@@ -1102,6 +1171,10 @@ void fill_args(bonsai_ctx *c, float eps, WalkArgs &a) {
     a.pot64 = nullptr;
     a.G64 = c->prm.G;
     a.eps2_64 = (double)eps * (double)eps;
+    a.lpc_off = nullptr;
+    a.lpp_off = nullptr;
+    a.lpc_out = nullptr;
+    a.lpp_out = nullptr;
 }
 
 }  // namespace
@@ -1190,6 +1263,25 @@ int walk_adjoint(bonsai_ctx *c, float eps, const float *lam, const float *mu, fl
     a.cell_adj = cell_adj;
     a.part_adj = part_adj;
     k_walk_adjoint<<<launch_blocks((const void *)k_walk_adjoint, c), WALK_WARPS * 32, 0, c->stream>>>(a);
+    c->launches += 1;
+    return cudaPeekAtLastError() == cudaSuccess ? BONSAI_OK : BONSAI_ECUDA;
+}
+
+// The interaction lists of the current tree and packed opening test, at the
+// caller's per-group offsets (device arrays, see ListPolicy).
+int walk_lists(bonsai_ctx *c, const int64_t *pc_off, const int64_t *pp_off, uint32_t *pc_out,
+               uint32_t *pp_out) {
+    WalkArgs a;
+    fill_args(c, 0.0f, a);
+    a.acc = nullptr;
+    a.pot = nullptr;
+    a.gnpp = nullptr;
+    a.gnpc = nullptr;
+    a.lpc_off = pc_off;
+    a.lpp_off = pp_off;
+    a.lpc_out = pc_out;
+    a.lpp_out = pp_out;
+    k_walk_lists<<<launch_blocks((const void *)k_walk_lists, c), WALK_WARPS * 32, 0, c->stream>>>(a);
     c->launches += 1;
     return cudaPeekAtLastError() == cudaSuccess ? BONSAI_OK : BONSAI_ECUDA;
 }

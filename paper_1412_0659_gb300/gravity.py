@@ -210,3 +210,19 @@ class TreeGravity:
         npc = torch.empty(st["n_groups"], dtype=torch.int32, device=dev)
         capi.tree_debug_groups(self.ctx, None, None, npp, npc)
         return npp, npc
+
+    def group_list_members(self):
+        """(pc_off, pc_cells, pp_off, pp_sources): every group's accepted
+        cells (node indices) and p-p sources (key-sorted particle indices)
+        from the last forces, group g at [off[g], off[g + 1])."""
+        npp, npc = self.group_lists()
+        dev = npp.device
+        pc_off = torch.zeros(npc.numel() + 1, dtype=torch.int64, device=dev)
+        pp_off = torch.zeros(npp.numel() + 1, dtype=torch.int64, device=dev)
+        torch.cumsum(npc.to(torch.int64), 0, out=pc_off[1:])
+        torch.cumsum(npp.to(torch.int64), 0, out=pp_off[1:])
+        npc_tot, npp_tot = int(pc_off[-1].item()), int(pp_off[-1].item())
+        pc = torch.empty(max(1, npc_tot), dtype=torch.int32, device=dev)  # never a null pointer
+        pp = torch.empty(max(1, npp_tot), dtype=torch.int32, device=dev)
+        capi.tree_debug_lists(self.ctx, pc_off, pp_off, pc, pp)
+        return pc_off, pc[:npc_tot], pp_off, pp[:npp_tot]

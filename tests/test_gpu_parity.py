@@ -80,6 +80,23 @@ def test_interaction_lists_match(run):
     assert (gpu["stats"]["n_pp"], gpu["stats"]["n_pc"]) == (npp, npc)
 
 
+def test_interaction_list_membership(run):
+    """Every group's accepted cells and p-p sources are the oracle's, as sets
+    (the GPU walks breadth-first, the oracle depth-first): a list that traded
+    one cell for another of the same count would fail here."""
+    name, pos, mass, eps, G, gpu, t = run
+    pc_off, pc, pp_off, pp = (a.cpu().numpy() for a in gpu["g"].group_list_members())
+    nd = t.nodes()
+    for g in range(t.ngroups):
+        cells, leaves = t.group_lists(0.4, g)
+        got = np.sort(pc[pc_off[g]:pc_off[g + 1]].astype(np.int64))
+        assert np.array_equal(got, np.sort(cells.astype(np.int64))), (name, g)
+        src = np.concatenate([np.arange(nd["first"][c], nd["first"][c] + nd["count"][c], dtype=np.int64)
+                              for c in leaves]) if len(leaves) else np.zeros(0, np.int64)
+        got = np.sort(pp[pp_off[g]:pp_off[g + 1]].astype(np.int64))
+        assert np.array_equal(got, np.sort(src)), (name, g)
+
+
 def test_forces_within_tolerance(run):
     from gpu_helpers import assert_force_tolerance
     name, pos, mass, eps, G, gpu, t = run
