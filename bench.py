@@ -305,6 +305,10 @@ def run_ours(args):
         e_flops += ge.stats()["flops"]
     torch.cuda.synchronize()
     e_s = time.perf_counter() - t0
+    # the GPU forces of the initial state, kept for the comparison with the
+    # oracle in the CPU-baseline leg
+    g_npp0, g_npc0 = (x.cpu().numpy() for x in ge.group_lists())
+    gpu_forces0 = (pin_acc.double().numpy().copy(), pin_pot.double().numpy().copy(), g_npp0, g_npc0)
     ge.close()
     e_s, e_flops = aggregate(e_s, e_flops, world, dev)
     e2e = {"value": e_flops / e_s / 1e12, "unit": UNIT,
@@ -326,7 +330,8 @@ def run_ours(args):
                 "frac": achieved / peak, "traffic": traffic,
                 "kernel": "k_walk (fused walk + p-p/p-c evaluation)",
                 "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flops x {max_mhz:.0f} MHz",
-                "convention_cap": "23/26 of peak for p-p and 65/76 for p-c at one FP32 instruction per issue slot"}
+                "convention_cap": "82 % of peak for p-p (23 flops in 14 FP32 instructions) and 93 % for p-c "
+                                  "(65 flops in 35) at one FP32 instruction per lane and cycle"}
 
     # --- direct summation on the same particles (the paper's Fig. 1 compares
     # tree and direct N-body performance): 2^16 targets over all sources ---
@@ -454,9 +459,9 @@ def run_ours(args):
                        "source domain, let_build (host-timed, includes its syncs) and let_forces "
                        "(CUDA events of the walk); flops in the 23/65 convention"}
 
-    cpu = None
+    cpu, accuracy = None, None
     if rank == 0 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(m, args.cpu_groups)
+        cpu, accuracy = cpu_baseline(m, args.cpu_groups, gpu_forces0)
 
     if rank == 0:
         line = {
@@ -464,9 +469,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded generator; the paper's Milky Way realisation is not available)",
-            "config": {"workload": desc, "n_per_gpu": n, "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                       "l2_flush": "none: inputs (~1.7 GB state) larger than L2",
-                       "arith": "FP32 forces on group-relative coordinates; FP64 keys, multipoles, state, diagnostics"},
+            "config": _config(desc, n, world),
             "particles_per_s": world * n * args.steps / (t_max * 1e-3),
             "force_particles_per_s": n / (walk_avg * 1e-3),
             "force_kernel_tflops": achieved,
@@ -477,7 +480,7 @@ def run_ours(args):
             "energy": {"E_tot": diag["E_tot"] if diag else None},
             "adjoint": adjoint, "direct": direct, "io": io, "ics": ics, "domains": dom,
             "clocks": clk, "gpu_launches": int(launches), "roofline": roofline, "e2e": e2e,
-            "cpu_baseline": cpu,
+            "cpu_baseline": cpu, "accuracy": accuracy,
         }
         print(json.dumps(line), flush=True)
     g.close()
@@ -485,10 +488,21 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def cpu_baseline(m, n_groups: int):
+def _config(desc: str, n: int, world: int) -> dict:
+    """The workload description, identical in both arms."""
+    return {"workload": desc, "n_per_gpu": n,
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+            "l2_flush": "none: inputs (~1.7 GB state) larger than L2",
+            "arith": "FP32 forces on group-relative coordinates; FP64 keys, multipoles, state, diagnostics"}
+
+
+def cpu_baseline(m, n_groups: int, gpu=None):
     """The FP64 oracle on the host cores: full tree build of the same workload
     plus the force walk of a seeded sample of groups; the force time is scaled
-    to all groups by flops.  Returns the oracle's Tflop/s for one step."""
+    to all groups by flops.  Returns the oracle's Tflop/s for one step, and,
+    when gpu = (acc, pot, g_npp, g_npc) holds the GPU's forces of the same
+    state (caller order) and its per-group list lengths, the GPU's error
+    against the oracle on the sampled groups' particles."""
     import numpy as np
 
     import oracle
@@ -499,7 +513,7 @@ def cpu_baseline(m, n_groups: int):
     sel = np.sort(rng.choice(t.ngroups, min(n_groups, t.ngroups), replace=False))
     g = t.groups()
     t1 = time.perf_counter()
-    _, _, g_npp, g_npc, _ = t.forces_groups(m.theta, m.eps, m.G, sel)
+    acc_s, pot_s, g_npp, g_npc, _ = t.forces_groups(m.theta, m.eps, m.G, sel)
     t_force = time.perf_counter() - t1
     cnt = g["count"][sel].astype(np.float64)
     f_sample = float((23.0 * cnt * g_npp[sel] + 65.0 * cnt * g_npc[sel]).sum())
@@ -507,11 +521,33 @@ def cpu_baseline(m, n_groups: int):
     # the whole step's flops estimated from the sample's flops per particle
     f_total = f_sample * m.n / n_sample
     t_total = t_build + t_force * (f_total / f_sample)
-    return {"value": f_total / t_total / 1e12, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": (f"FP64 C oracle: full tree build of the same N={m.n} workload ({t_build:.1f} s) + force walk "
-                       f"of {len(sel)} seeded random groups ({int(n_sample)} particles, {t_force:.1f} s), "
-                       "force time scaled to all particles by flops"),
-            "force_only_tflops": f_sample / t_force / 1e12}
+    cpu = {"value": f_total / t_total / 1e12, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+           "sample": (f"FP64 C oracle: full tree build of the same N={m.n} workload ({t_build:.1f} s) + force walk "
+                      f"of {len(sel)} seeded random groups ({int(n_sample)} particles, {t_force:.1f} s), "
+                      "force time scaled to all particles by flops"),
+           "force_only_tflops": f_sample / t_force / 1e12}
+    if gpu is None:
+        return cpu, None
+    acc_g, pot_g, gnpp, gnpc = gpu
+    _, perm = t.keys()
+    rows = np.concatenate([np.arange(g["first"][k], g["first"][k] + g["count"][k]) for k in sel])
+    ci = perm[rows]                                   # caller indices of the sampled particles
+    ao, po = acc_s[:, rows], pot_s[rows]
+    e = np.linalg.norm(acc_g[:, ci] - ao, axis=0) / np.linalg.norm(ao, axis=0)
+    pe = np.abs(pot_g[ci] - po) / np.abs(po)
+    acc = {"median_rel": float(np.median(e)), "p999_rel": float(np.quantile(e, 0.999)),
+           "max_rel": float(e.max()), "pot_median_rel": float(np.median(pe)),
+           "pot_p999_rel": float(np.quantile(pe, 0.999)),
+           "n_pp_match": float(np.mean(gnpp[sel] == g_npp[sel])),
+           "n_pc_match": float(np.mean(gnpc[sel] == g_npc[sel])),
+           "groups": int(len(sel)), "particles": int(len(rows)),
+           "tolerance": {"median_rel": 2e-6, "p999_rel": 1e-4, "counts": "equal"},
+           "within_tolerance": bool(np.median(e) <= 2e-6 and np.quantile(e, 0.999) <= 1e-4
+                                    and np.median(pe) <= 2e-6 and np.quantile(pe, 0.999) <= 1e-4
+                                    and np.all(gnpp[sel] == g_npp[sel]) and np.all(gnpc[sel] == g_npc[sel])),
+           "what": "GPU forces of the initial state (tree_solve_host) against the FP64 oracle tree on the "
+                   "particles of the sampled groups; per-group list lengths compared"}
+    return cpu, acc
 
 
 def run_reference(args):
@@ -520,13 +556,15 @@ def run_reference(args):
     if rank != 0:
         return
     m, desc = _workload(args.workload, 0, on_gpu=False)
+    import oracle
     for _ in range(args.warmup):
-        pass
+        # untimed: a small force walk (threads spun up, code and tables paged in)
+        oracle.forces(m.pos[:, :4096], m.mass[:4096], m.theta, m.eps, m.G)
     vals = []
     t0 = time.perf_counter()
     cpu = None
     for _ in range(max(1, args.steps)):
-        cpu = cpu_baseline(m, args.cpu_groups)
+        cpu, _ = cpu_baseline(m, args.cpu_groups)
         vals.append(cpu["value"])
     wall = time.perf_counter() - t0
     value = statistics.mean(vals)
@@ -534,7 +572,8 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / max(1, args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic (seeded generator)", "config": {"workload": desc, "n_per_gpu": m.n},
+            "data": "synthetic (seeded generator; the paper's Milky Way realisation is not available)",
+            "config": _config(desc, m.n, world),
             "cpu_baseline": cpu,
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
