@@ -47,6 +47,8 @@ extern "C" {
 #define BONSAI_ESTATE (-5)    /* call out of order, e.g. forces before a tree was built */
 #define BONSAI_EIO (-6)       /* a snapshot file could not be opened, read or written, or
                                  is not a snapshot of this format (size, magic, version) */
+#define BONSAI_ETIMEOUT (-7)  /* a host wait on the device exceeded the wait limit
+                                 (bonsai_set_wait_timeout); the work stays queued */
 
 typedef struct bonsai_ctx bonsai_ctx;
 typedef struct bonsai_let bonsai_let;
@@ -218,13 +220,51 @@ void let_destroy(bonsai_let *let);
  * EOVERFLOW (a marking walk's frontier overflowed), ENOMEM, ECUDA. */
 int let_build(bonsai_let *let, bonsai_ctx *src, const bonsai_ctx *dst, float theta);
 
+/* tree_get_group_boxes -- the walk's group boxes of the last build (Sec.
+ * III.B.2: what a remote process needs to know of this one to build the
+ * LET it sends here): box and half, device float [4][...] as float4 per
+ * group, {centre.xyz (FP32, rounded to nearest), 0} and {half-size.xyz
+ * (FP32, rounded up), 0}; either may be NULL; *ngroups (host, may be NULL)
+ * receives the group count.  Errors: EINVAL, ESTATE (no tree), ECUDA. */
+int tree_get_group_boxes(bonsai_ctx *ctx, float *box, float *half, int64_t *ngroups);
+
+/* let_build_boxes -- let_build for group boxes received from a remote
+ * process (tree_get_group_boxes there) instead of a context: the part of
+ * src's tree that those groups need (Sec. III.B.2).  box, half: device
+ * float4 [ngroups] as above; the remote tree must be a branch of the same
+ * global octree (tree_build_cube in the same cube), which the caller
+ * guarantees.  ngroups = 0 gives an empty LET.  Errors: EINVAL, ESTATE,
+ * EOVERFLOW, ENOMEM, ECUDA. */
+int let_build_boxes(bonsai_let *let, bonsai_ctx *src, const float *box, const float *half,
+                    int64_t ngroups, float theta);
+
+/* let_pack -- the LET as one contiguous buffer, the message a process sends
+ * to another (Sec. III.B.2): a 64-byte header (magic "BGBLET01", cells,
+ * particles, total bytes, theta), the cell records (4 x float4 per cell,
+ * then the topology as uint2 per cell padded to 16 bytes) and the particle
+ * records (2 x float4 per particle).  *bytes receives the packed size; with
+ * buf NULL nothing else happens, otherwise buf (device, 16-byte aligned,
+ * cap bytes >= *bytes, owned by the caller) receives the packed LET.
+ * Errors: EINVAL (null, cap too small, misaligned buf), ECUDA. */
+int let_pack(const bonsai_let *let, void *buf, int64_t cap, int64_t *bytes);
+
+/* let_unpack -- a packed LET received from another process (buf: device,
+ * 16-byte aligned, exactly the packed size) into let, ready for let_forces.
+ * The header and the topology are checked (every internal cell's children
+ * after it and inside the cell array, every leaf's particles inside the
+ * particle array) before the LET is accepted.  The source-cell map of
+ * let_debug_cells stays with the sender.  Errors: EINVAL (bad header,
+ * size or topology; the LET is left empty), ENOMEM, ECUDA. */
+int let_unpack(bonsai_let *let, const void *buf, int64_t bytes);
+
 /* LET size: out = {cells, particles, bytes of its records, cells of the
  * source tree}.  Errors: EINVAL. */
 int let_get_info(const bonsai_let *let, int64_t out[4]);
 
 /* For tests: the source cell of each LET cell and its kind (0 used whole,
  * 1 opened cell, 2 opened leaf), device uint32 [cells] each; either may be
- * NULL.  Errors: EINVAL, ESTATE (empty LET), ECUDA. */
+ * NULL.  Errors: EINVAL, ESTATE (empty LET, or one received by
+ * let_unpack), ECUDA. */
 int let_debug_cells(const bonsai_let *let, uint32_t *src_node, uint32_t *kind);
 
 /* let_forces -- add the force of the LET's sources on dst's particles to
@@ -361,6 +401,40 @@ int tree_debug_lists(bonsai_ctx *ctx, const int64_t *pc_off, const int64_t *pp_o
  * return BONSAI_EOVERFLOW; the context stays usable.  Errors: EINVAL. */
 int tree_debug_set_frontier_capacity(bonsai_ctx *ctx, int cap);
 
+/* Limit of every host wait on the device, in seconds, for all contexts of
+ * the process (default 600).  Each call that needs a device result polls
+ * an event recorded on its stream and returns BONSAI_ETIMEOUT once the
+ * limit has passed; the work already queued still runs, and a later call
+ * on the same stream is ordered after it.  (No paper counterpart: the
+ * failure contract of this library.)  Errors: EINVAL (seconds not > 0 or
+ * not finite). */
+int bonsai_set_wait_timeout(double seconds);
+
+/* Queue a host function on the context's stream that sleeps for the given
+ * number of seconds (at most 60), holding back everything queued after it.
+ * A test hook for the bounded waits: the device is not involved.  Errors:
+ * EINVAL, ECUDA. */
+int tree_debug_hold_stream(bonsai_ctx *ctx, double seconds);
+
+/* tree_bounds -- the componentwise minimum mn[3] and maximum mx[3] (host)
+ * of device positions pos [3][n] (with the input check of tree_build on
+ * pos and mass [n]), by the bounding-box kernels of tree_build (Sec.
+ * III.B.1); the context's tree is not touched.  Errors: EINVAL (null, bad
+ * n, a non-finite position or a mass <= 0), ENOMEM, ECUDA. */
+int tree_bounds(bonsai_ctx *ctx, const double *pos, const double *mass, int64_t n, double mn[3],
+                double mx[3]);
+
+/* bonsai_cube_from_bounds -- host: the cube the keys are taken in (Sec.
+ * III.B.1: the global bounding box maps every coordinate to a global PH
+ * key) from the componentwise minimum mn[3] and maximum mx[3] of all
+ * positions, by the same FP64 steps as tree_build: side L = largest extent
+ * x (1 + 2^-20) (1 when all points coincide), centred on the box.  For
+ * processes that each hold part of the particles: reduce mn and mx over
+ * them, then every process gets the same cube for tree_build_cube.
+ * cube: host double[4] {lo_x, lo_y, lo_z, L}.  Errors: EINVAL (null,
+ * non-finite, mn > mx). */
+int bonsai_cube_from_bounds(const double mn[3], const double mx[3], double cube[4]);
+
 /* Name of a status code. */
 const char *bonsai_strerror(int code);
 
@@ -385,11 +459,16 @@ const char *bonsai_strerror(int code);
  *
  * Scratch: a fixed static device array of about 12.3 MB (two ping-pong
  * halves of the sort for up to BONSAI_NOALLOC_MAX_N pairs, the histograms,
- * the bounding-box partials and a status word), part of the library image:
- * every GPU that loads the library keeps it until the process exits.  The
- * first call on a device looks up that array's device address (with the
- * device current) and caches it; make that first call before any stream
- * capture.  Every call on a device shares the same array, so calls whose
+ * the bounding-box partials and a status word), part of the library's
+ * device code.  The CUDA runtime places it on a device when it loads that
+ * code there: with the default lazy module loading at the first call on
+ * the device, with CUDA_MODULE_LOADING=EAGER when the library is loaded.
+ * The runtime, not this function, makes that placement, and it can fail
+ * when another allocator already holds nearly all device memory; the first
+ * call then returns ECUDA.  Once placed, the array stays on the device
+ * until the process exits.  The first call on a device also looks up the
+ * array's device address (with the device current) and caches it; make
+ * that first call before any stream capture.  Every call on a device shares the same array, so calls whose
  * work overlaps on the GPU (different streams or threads without ordering)
  * race and must not be issued; calls on one stream are ordered and safe.
  *

@@ -25,6 +25,7 @@ BONSAI_EOVERFLOW = -3
 BONSAI_ECUDA = -4
 BONSAI_ESTATE = -5
 BONSAI_EIO = -6
+BONSAI_ETIMEOUT = -7
 
 # every symbol include/bonsai_gb.h declares
 EXPORTED = (
@@ -37,7 +38,9 @@ EXPORTED = (
     "tree_save_snapshot", "tree_load_snapshot", "tree_surface_density",
     "tree_build_cube", "tree_domain_state", "let_create", "let_destroy", "let_build", "let_get_info",
     "let_debug_cells", "let_forces", "bonsai_galaxy_sec4", "bonsai_galaxy_generate",
-    "bonsai_galaxy_tables", "tree_debug_lists",
+    "bonsai_galaxy_tables", "tree_debug_lists", "bonsai_set_wait_timeout", "tree_debug_hold_stream",
+    "tree_get_group_boxes", "let_build_boxes", "let_pack", "let_unpack", "bonsai_cube_from_bounds",
+    "tree_bounds",
 )
 
 BONSAI_NOALLOC_MAX_N = 1 << 20
@@ -116,6 +119,14 @@ def load(path: str | None = None):
             "tree_debug_multipoles": (i32, [P, P, P, P]),
             "tree_debug_groups": (i32, [P, P, P, P, P]),
             "tree_debug_lists": (i32, [P, P, P, P, P]),
+            "bonsai_set_wait_timeout": (i32, [f64]),
+            "tree_get_group_boxes": (i32, [P, P, P, ctypes.POINTER(i64)]),
+            "let_build_boxes": (i32, [P, P, P, P, i64, f32]),
+            "let_pack": (i32, [P, P, i64, ctypes.POINTER(i64)]),
+            "let_unpack": (i32, [P, P, i64]),
+            "bonsai_cube_from_bounds": (i32, [ctypes.POINTER(f64), ctypes.POINTER(f64), ctypes.POINTER(f64)]),
+            "tree_bounds": (i32, [P, P, P, i64, ctypes.POINTER(f64), ctypes.POINTER(f64)]),
+            "tree_debug_hold_stream": (i32, [P, f64]),
             "bonsai_strerror": (ctypes.c_char_p, [i32]),
             "bonsai_sfc_order_noalloc": (i32, [P, P, i64, P, P, P, P]),
             "tree_forces_vjp": (i32, [P, P, P, P, P]),
@@ -285,6 +296,62 @@ def let_debug_cells(let, src_node=None, kind=None) -> None:
                                   _ptr(kind, torch.int32, None, "kind")), "let_debug_cells")
 
 
+def tree_get_group_boxes(ctx, box=None, half=None) -> int:
+    """The group boxes (float32 CUDA tensors (ng, 4) each, or None); returns ng."""
+    import torch
+    ng = ctypes.c_int64()
+    _check(load().tree_get_group_boxes(ctx, _ptr(box, torch.float32, None, "box"),
+                                       _ptr(half, torch.float32, None, "half"), ctypes.byref(ng)),
+           "tree_get_group_boxes")
+    return ng.value
+
+
+def let_build_boxes(let, src, box, half, theta: float) -> None:
+    import torch
+    ng = int(box.shape[0])
+    if tuple(box.shape) != (ng, 4) or tuple(half.shape) != (ng, 4):
+        raise ValueError("box and half must be (ngroups, 4)")
+    if ng == 0:
+        box = half = None
+        bp = hp = ctypes.c_void_p(16)  # never read with no groups
+    else:
+        bp, hp = _ptr(box, torch.float32, 4 * ng, "box"), _ptr(half, torch.float32, 4 * ng, "half")
+    _check(load().let_build_boxes(let, src, bp, hp, ng, float(theta)), "let_build_boxes")
+
+
+def let_pack(let, buf=None) -> int:
+    """Packed size in bytes; with buf (uint8 CUDA tensor) also the packed LET."""
+    import torch
+    nb = ctypes.c_int64()
+    cap = 0 if buf is None else int(buf.numel())
+    _check(load().let_pack(let, _ptr(buf, torch.uint8, None, "buf"), cap, ctypes.byref(nb)), "let_pack")
+    return nb.value
+
+
+def let_unpack(let, buf) -> None:
+    import torch
+    _check(load().let_unpack(let, _ptr(buf, torch.uint8, None, "buf"), int(buf.numel())), "let_unpack")
+
+
+def bonsai_cube_from_bounds(mn, mx) -> list:
+    a = (ctypes.c_double * 3)(*[float(v) for v in mn])
+    b = (ctypes.c_double * 3)(*[float(v) for v in mx])
+    out = (ctypes.c_double * 4)()
+    _check(load().bonsai_cube_from_bounds(a, b, out), "bonsai_cube_from_bounds")
+    return list(out)
+
+
+def tree_bounds(ctx, pos, mass):
+    """(mn[3], mx[3]) of device positions (3, n) float64 with masses (n,)."""
+    import torch
+    n = int(mass.numel())
+    mn = (ctypes.c_double * 3)()
+    mx = (ctypes.c_double * 3)()
+    _check(load().tree_bounds(ctx, _ptr(pos, torch.float64, 3 * n, "pos"), _ptr(mass, torch.float64, n, "mass"),
+                              n, mn, mx), "tree_bounds")
+    return list(mn), list(mx)
+
+
 def let_forces(dst, let, eps: float) -> None:
     _check(load().let_forces(dst, let, float(eps)), "let_forces")
 
@@ -400,6 +467,16 @@ def tree_debug_lists(ctx, pc_off, pp_off, pc_cells, pp_sources) -> None:
     (int64 CUDA tensors [n_groups + 1]; outputs int32 CUDA tensors)."""
     _check(load().tree_debug_lists(ctx, _ptr(pc_off), _ptr(pp_off), _ptr(pc_cells), _ptr(pp_sources)),
            "tree_debug_lists")
+
+
+def bonsai_set_wait_timeout(seconds: float) -> None:
+    """Limit of every host wait on the device (seconds, process-wide)."""
+    _check(load().bonsai_set_wait_timeout(float(seconds)), "bonsai_set_wait_timeout")
+
+
+def tree_debug_hold_stream(ctx, seconds: float) -> None:
+    """Queue a host-side sleep on the context's stream (test hook)."""
+    _check(load().tree_debug_hold_stream(ctx, float(seconds)), "tree_debug_hold_stream")
 
 
 def bonsai_strerror(code: int) -> str:

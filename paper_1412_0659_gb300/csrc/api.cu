@@ -4,7 +4,10 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
+#include <chrono>
 #include <new>
+#include <thread>
 
 #include "internal.cuh"
 
@@ -34,6 +37,37 @@ void release(DBuf<T> &b) {
     b.cap = 0;
 }
 
+static std::atomic<double> g_wait_limit_s{600.0};
+
+int wait_stream(cudaStream_t s) {
+    cudaEvent_t e;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return BONSAI_ECUDA;
+    if (cudaEventRecord(e, s) != cudaSuccess) {
+        cudaEventDestroy(e);
+        return BONSAI_ECUDA;
+    }
+    const auto t0 = std::chrono::steady_clock::now();
+    const double limit = g_wait_limit_s.load();
+    int rc = BONSAI_OK;
+    while (true) {
+        const cudaError_t r = cudaEventQuery(e);
+        if (r == cudaSuccess) break;
+        if (r != cudaErrorNotReady) {
+            rc = BONSAI_ECUDA;
+            break;
+        }
+        const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (el > limit) {
+            rc = BONSAI_ETIMEOUT;
+            break;
+        }
+        // poll continuously for the first 2 ms (short calls), then every 50 us
+        if (el > 2e-3) std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+    cudaEventDestroy(e);  // released by the runtime once the event completes
+    return rc;
+}
+
 template int ensure<double>(DBuf<double> &, size_t);
 template int ensure<float>(DBuf<float> &, size_t);
 template int ensure<uint32_t>(DBuf<uint32_t> &, size_t);
@@ -53,8 +87,38 @@ using namespace bgb;
 
 namespace bgb {
 
+// Bytes that ensure(b, n) would newly allocate, and the bytes it would free first.
+template <typename T>
+static void grow_bytes(const DBuf<T> &b, size_t n, size_t &alloc, size_t &freed) {
+    if (n == 0) n = 1;
+    if (b.cap >= n) return;
+    alloc += (n + n / 8) * sizeof(T);
+    freed += b.cap * sizeof(T);
+}
+
 int particle_buffers(bonsai_ctx *c, int64_t n) {
     const size_t n3 = 3 * (size_t)n;
+    // the memory budget first: an n whose buffers cannot fit in the device
+    // memory that is free (plus what the context would release to grow them)
+    // fails with ENOMEM before anything is allocated or launched
+    size_t alloc = 0, freed = 0;
+    for (const DBuf<double> *b : {&c->pos, &c->pos2, &c->vel, &c->vel2}) grow_bytes(*b, n3, alloc, freed);
+    grow_bytes(c->mass, n, alloc, freed);
+    grow_bytes(c->mass2, n, alloc, freed);
+    grow_bytes(c->id, n, alloc, freed);
+    grow_bytes(c->id2, n, alloc, freed);
+    grow_bytes(c->acc, n3, alloc, freed);
+    grow_bytes(c->pot, n, alloc, freed);
+    grow_bytes(c->key, n, alloc, freed);
+    grow_bytes(c->key2, n, alloc, freed);
+    grow_bytes(c->val, n, alloc, freed);
+    grow_bytes(c->val2, n, alloc, freed);
+    grow_bytes(c->body_hi, n, alloc, freed);
+    grow_bytes(c->body_lo, n, alloc, freed);
+    grow_bytes(c->grp_flag, 2 * (size_t)n + 2, alloc, freed);
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return BONSAI_ECUDA;
+    if (alloc > free_b + freed) return BONSAI_ENOMEM;
     if (ensure(c->pos, n3) || ensure(c->pos2, n3) || ensure(c->vel, n3) || ensure(c->vel2, n3) ||
         ensure(c->mass, n) || ensure(c->mass2, n) || ensure(c->id, n) || ensure(c->id2, n) ||
         ensure(c->acc, n3) || ensure(c->pot, n) || ensure(c->key, n) || ensure(c->key2, n) ||
@@ -79,7 +143,7 @@ int node_buffers(bonsai_ctx *c) {
 int read_scalars(bonsai_ctx *c) {
     BGB_CUDA(cudaMemcpyAsync(c->hsc, c->dsc, sizeof(DevScalars), cudaMemcpyDeviceToHost,
                              c->stream));
-    BGB_CUDA(cudaStreamSynchronize(c->stream));
+    BGB_WAIT(c->stream);
     return BONSAI_OK;
 }
 
@@ -210,7 +274,7 @@ int bonsai_create(bonsai_ctx **out, const bonsai_params *p, void *stream) {
 
 void bonsai_destroy(bonsai_ctx *c) {
     if (!c) return;
-    cudaStreamSynchronize(c->stream);
+    wait_stream(c->stream);  // bounded; cudaFree below waits for the device in any case
     release(c->pos); release(c->pos2); release(c->vel); release(c->vel2);
     release(c->mass); release(c->mass2); release(c->id); release(c->id2);
     release(c->acc); release(c->pot); release(c->key); release(c->key2);
@@ -265,7 +329,10 @@ static int build_common(bonsai_ctx *c, const double *pos, const double *mass, in
     c->have_tree = c->have_forces = c->have_vel = false;
     c->n = n;
     int rc = particle_buffers(c, n);
-    if (rc) return rc;
+    if (rc) {
+        c->n = 0;
+        return rc;
+    }
     rc = rebuild(c, pos, mass, true);
     if (rc) return rc;
     c->stats.n = n;
@@ -322,7 +389,7 @@ int tree_set_velocities(bonsai_ctx *c, const double *vel) {
     if (!c || !vel) return BONSAI_EINVAL;
     if (!c->have_tree) return BONSAI_ESTATE;
     launch_permute_in_vel(c, vel);
-    BGB_CUDA(cudaStreamSynchronize(c->stream));
+    BGB_WAIT(c->stream);
     c->have_vel = true;
     return BONSAI_OK;
 }
@@ -342,7 +409,7 @@ int tree_step(bonsai_ctx *c, double dt) {
     if ((rc = forces_internal(c, c->prm.theta, c->prm.eps, nullptr, nullptr))) return rc;
     BGB_CUDA(cudaEventRecord(c->ev[7], c->stream));
     launch_kick(c, 0.5 * dt);
-    BGB_CUDA(cudaStreamSynchronize(c->stream));
+    BGB_WAIT(c->stream);
     float a = 0.0f;
     cudaEventElapsedTime(&a, c->ev[5], c->ev[6]);
     c->stats.ms_integrate = 2.0f * a;
@@ -356,7 +423,7 @@ int tree_get_state(bonsai_ctx *c, double *pos, double *vel, double *mass) {
     if (!c) return BONSAI_EINVAL;
     if (!c->have_tree) return BONSAI_ESTATE;
     launch_unpermute_state(c, pos, vel, mass);
-    BGB_CUDA(cudaStreamSynchronize(c->stream));
+    BGB_WAIT(c->stream);
     return BONSAI_OK;
 }
 
@@ -364,7 +431,7 @@ int tree_get_forces(bonsai_ctx *c, float *acc, float *pot) {
     if (!c) return BONSAI_EINVAL;
     if (!c->have_forces) return BONSAI_ESTATE;
     launch_unpermute_forces(c, acc, pot);
-    BGB_CUDA(cudaStreamSynchronize(c->stream));
+    BGB_WAIT(c->stream);
     return BONSAI_OK;
 }
 
@@ -374,7 +441,7 @@ int bonsai_diagnostics(bonsai_ctx *c, double out[10]) {
     double *dev = c->diag_part.p + (size_t)diag_blocks(c) * 10;
     launch_diagnostics(c, dev);
     BGB_CUDA(cudaMemcpyAsync(out, dev, 10 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    BGB_CUDA(cudaStreamSynchronize(c->stream));
+    BGB_WAIT(c->stream);
     out[2] = out[0] + out[1];
     return BONSAI_OK;
 }
@@ -417,7 +484,7 @@ int tree_run(bonsai_ctx *c, int nsteps, double dt, int ckpt_every) {
         }
         if ((rc = tree_step(c, dt))) return rc;
     }
-    BGB_CUDA(cudaStreamSynchronize(c->stream));
+    BGB_WAIT(c->stream);
     c->run_steps = nsteps;
     c->run_ckpt = ckpt_every;
     c->run_dt = dt;
@@ -438,7 +505,7 @@ int tree_run_vjp(bonsai_ctx *c, const double *xbar, const double *vbar, const do
     else
         BGB_CUDA(cudaMemsetAsync(mbar0, 0, n * sizeof(double), c->stream));
     if (K == 0) {
-        BGB_CUDA(cudaStreamSynchronize(c->stream));
+        BGB_WAIT(c->stream);
         return BONSAI_OK;
     }
     // the reverse drift writes the kick cotangent (caller order) before the
@@ -484,7 +551,10 @@ int tree_solve_host(bonsai_ctx *c, const double *pos, const double *mass, int64_
     c->have_tree = c->have_forces = c->have_vel = false;
     c->n = n;
     int rc = particle_buffers(c, n);
-    if (rc) return rc;
+    if (rc) {
+        c->n = 0;
+        return rc;
+    }
     // stage the caller's arrays in the second state buffers, then build from them
     BGB_CUDA(cudaMemcpyAsync(c->pos2.p, pos, 3 * n * sizeof(double), cudaMemcpyHostToDevice,
                              c->stream));
@@ -503,7 +573,7 @@ int tree_solve_host(bonsai_ctx *c, const double *pos, const double *mass, int64_
     if (pot)
         BGB_CUDA(cudaMemcpyAsync(pot, stage + 3 * n, n * sizeof(float), cudaMemcpyDeviceToHost,
                                  c->stream));
-    BGB_CUDA(cudaStreamSynchronize(c->stream));
+    BGB_WAIT(c->stream);
     c->stats.n = n;
     c->stats.n_nodes = c->n_nodes;
     c->stats.n_groups = c->n_groups;
@@ -516,7 +586,7 @@ int tree_debug_cube(bonsai_ctx *c, double lo[3], double *L) {
     if (!c->have_tree) return BONSAI_ESTATE;
     BGB_CUDA(cudaMemcpyAsync(c->hsc, c->dsc, sizeof(DevScalars), cudaMemcpyDeviceToHost,
                              c->stream));
-    BGB_CUDA(cudaStreamSynchronize(c->stream));
+    BGB_WAIT(c->stream);
     for (int d = 0; d < 3; ++d) lo[d] = c->hsc->lo[d];
     *L = c->hsc->L;
     return BONSAI_OK;
@@ -531,7 +601,7 @@ int tree_debug_keys(bonsai_ctx *c, uint64_t *keys, uint32_t *perm) {
     if (perm)
         BGB_CUDA(cudaMemcpyAsync(perm, c->id.p, c->n * sizeof(uint32_t), cudaMemcpyDeviceToDevice,
                                  c->stream));
-    BGB_CUDA(cudaStreamSynchronize(c->stream));
+    BGB_WAIT(c->stream);
     return BONSAI_OK;
 }
 
@@ -546,7 +616,7 @@ int tree_debug_nodes(bonsai_ctx *c, uint32_t *first, uint32_t *count, uint32_t *
     for (int k = 0; k < 5; ++k)
         if (dst[k])
             BGB_CUDA(cudaMemcpyAsync(dst[k], src[k], b, cudaMemcpyDeviceToDevice, c->stream));
-    BGB_CUDA(cudaStreamSynchronize(c->stream));
+    BGB_WAIT(c->stream);
     return BONSAI_OK;
 }
 
@@ -558,7 +628,7 @@ int tree_debug_multipoles(bonsai_ctx *c, double *M, double *com, double *Q) {
     if (com)
         BGB_CUDA(cudaMemcpyAsync(com, c->nd_com.p, 3 * nn * 8, cudaMemcpyDeviceToDevice, c->stream));
     if (Q) BGB_CUDA(cudaMemcpyAsync(Q, c->nd_Q.p, 6 * nn * 8, cudaMemcpyDeviceToDevice, c->stream));
-    BGB_CUDA(cudaStreamSynchronize(c->stream));
+    BGB_WAIT(c->stream);
     return BONSAI_OK;
 }
 
@@ -574,7 +644,7 @@ int tree_debug_groups(bonsai_ctx *c, uint32_t *first, uint32_t *count, int32_t *
         BGB_CUDA(cudaMemcpyAsync(count, c->grp_count.p, ng * 4, cudaMemcpyDeviceToDevice, c->stream));
     if (npp) BGB_CUDA(cudaMemcpyAsync(npp, c->grp_npp.p, ng * 4, cudaMemcpyDeviceToDevice, c->stream));
     if (npc) BGB_CUDA(cudaMemcpyAsync(npc, c->grp_npc.p, ng * 4, cudaMemcpyDeviceToDevice, c->stream));
-    BGB_CUDA(cudaStreamSynchronize(c->stream));
+    BGB_WAIT(c->stream);
     return BONSAI_OK;
 }
 
@@ -587,6 +657,46 @@ int tree_debug_lists(bonsai_ctx *c, const int64_t *pc_off, const int64_t *pp_off
     if (rc) return rc;
     if ((rc = read_scalars(c))) return rc;
     return (c->hsc->status & ST_OVERFLOW) ? BONSAI_EOVERFLOW : BONSAI_OK;
+}
+
+int tree_bounds(bonsai_ctx *c, const double *pos, const double *mass, int64_t n, double mn[3],
+                double mx[3]) {
+    if (!c || !pos || !mass || !mn || !mx || n < 1 || n > 0x7fffffffll) return BONSAI_EINVAL;
+    if (ensure(c->box_part, (size_t)c->sm_count * 4 + 8)) return BONSAI_ENOMEM;
+    BGB_CUDA(cudaMemsetAsync(&c->dsc->status, 0, sizeof(int32_t), c->stream));
+    launch_bbox(c, pos, mass, n);  // also checks the input
+    BGB_CUDA(cudaPeekAtLastError());
+    int rc = read_scalars(c);
+    if (rc) return rc;
+    if (c->hsc->status & ST_BAD_INPUT) return BONSAI_EINVAL;
+    for (int d = 0; d < 3; ++d) {
+        mn[d] = c->hsc->mn[d];
+        mx[d] = c->hsc->mx[d];
+    }
+    return BONSAI_OK;
+}
+
+int bonsai_set_wait_timeout(double seconds) {
+    if (!(seconds > 0.0) || !isfinite(seconds)) return BONSAI_EINVAL;
+    g_wait_limit_s.store(seconds);
+    return BONSAI_OK;
+}
+
+static void CUDART_CB hold_host(void *arg) {
+    const double s = *static_cast<double *>(arg);
+    delete static_cast<double *>(arg);
+    std::this_thread::sleep_for(std::chrono::duration<double>(s));
+}
+
+int tree_debug_hold_stream(bonsai_ctx *c, double seconds) {
+    if (!c || !(seconds >= 0.0) || !(seconds <= 60.0)) return BONSAI_EINVAL;
+    double *arg = new (std::nothrow) double(seconds);
+    if (!arg) return BONSAI_ENOMEM;
+    if (cudaLaunchHostFunc(c->stream, hold_host, arg) != cudaSuccess) {
+        delete arg;
+        return BONSAI_ECUDA;
+    }
+    return BONSAI_OK;
 }
 
 int tree_debug_set_frontier_capacity(bonsai_ctx *c, int cap) {
@@ -604,6 +714,7 @@ const char *bonsai_strerror(int code) {
         case BONSAI_ECUDA: return "CUDA runtime error";
         case BONSAI_ESTATE: return "call out of order";
         case BONSAI_EIO: return "snapshot file could not be opened, read or written, or has the wrong format";
+        case BONSAI_ETIMEOUT: return "a wait on the device exceeded the wait limit";
         default: return "unknown status";
     }
 }

@@ -766,7 +766,7 @@ extern "C" int bonsai_galaxy_tables(const bonsai_galaxy *g, double *radial, doub
         cudaMemcpyAsync(disk, t.disk, sizeof(double) * (size_t)BONSAI_ICS_NDISK_OUT * KD,
                         cudaMemcpyDeviceToDevice, s) != cudaSuccess)
         return BONSAI_ECUDA;
-    return cudaStreamSynchronize(s) == cudaSuccess ? BONSAI_OK : BONSAI_ECUDA;
+    return bgb::wait_stream(s);
 }
 
 extern "C" int bonsai_galaxy_generate(const bonsai_galaxy *g, double *pos, double *vel,
@@ -801,5 +801,5 @@ extern "C" int bonsai_galaxy_generate(const bonsai_galaxy *g, double *pos, doubl
     k_moments<<<nparts, MOM_T, 0, s>>>(pos, vel, mass, n, part);
     k_shift<<<blocks, 256, 0, s>>>(pos, vel, n, part, nparts);
     if (cudaGetLastError() != cudaSuccess) return BONSAI_ECUDA;
-    return cudaStreamSynchronize(s) == cudaSuccess ? BONSAI_OK : BONSAI_ECUDA;
+    return bgb::wait_stream(s);
 }

@@ -34,6 +34,7 @@ struct DevScalars {
     uint32_t group_counter;  // dynamic scheduling of the walk
     uint32_t n_groups;
     int32_t pad;
+    double mn[3], mx[3];  // componentwise bounds of the last bounding-box reduction
 };
 
 // Bounding-cube reduction partials (per block)
@@ -210,8 +211,29 @@ void launch_diagnostics(bonsai_ctx *c, double *out_dev);
 int diag_blocks(bonsai_ctx *c);
 int walk_resident_warps(bonsai_ctx *c);
 size_t walk_frontier_elems(int warps);
-size_t scan_tmp_elems(int64_t n);
-size_t sort_hist_elems(int64_t n);
+// Tiles of the radix sort and of the scan, and the scratch sizes derived
+// from them (constexpr, so that a fixed scratch layout can be checked at
+// compile time).
+constexpr int SORT_BLOCK = 256;
+constexpr int SORT_IPT = 16;
+constexpr int SORT_TILE = SORT_BLOCK * SORT_IPT;
+constexpr int SCAN_BLOCK = 1024;
+constexpr int SCAN_IPT = 4;
+constexpr int SCAN_TILE = SCAN_BLOCK * SCAN_IPT;
+// entries of the scan's block-sum scratch for n inputs
+constexpr size_t scan_tmp_elems(int64_t n) {
+    size_t t = 0;
+    int64_t m = n;
+    while (m > SCAN_TILE) {
+        m = (m + SCAN_TILE - 1) / SCAN_TILE;
+        t += 2 * (size_t)m;
+    }
+    return t + 64;
+}
+// entries of the per-tile digit histograms of a sort of n pairs
+constexpr size_t sort_hist_elems(int64_t n) {
+    return 256 * (size_t)((n + SORT_TILE - 1) / SORT_TILE) + 64;
+}
 void launch_unpermute_state(bonsai_ctx *c, double *pos, double *vel, double *mass);
 void launch_unpermute_forces(bonsai_ctx *c, float *acc, float *pot);
 void launch_permute_in_vel(bonsai_ctx *c, const double *vel);
@@ -254,6 +276,18 @@ inline int grid_for(int64_t n, int block, int max_blocks = 1 << 30) {
 }
 
 }  // namespace bgb
+
+// Every host wait on the device is bounded (api.cu): the stream's work is
+// polled through an event until it completes (BONSAI_OK), fails (ECUDA) or
+// the process-wide limit passes (ETIMEOUT).
+namespace bgb {
+int wait_stream(cudaStream_t s);
+}
+#define BGB_WAIT(stream)                           \
+    do {                                           \
+        const int _w = bgb::wait_stream(stream);   \
+        if (_w != BONSAI_OK) return _w;            \
+    } while (0)
 
 #define BGB_CUDA(call)                                  \
     do {                                                \

@@ -6,6 +6,8 @@
 // the keys are bit-identical to any IEEE implementation of the same formula.
 #include <math.h>
 
+#include <cmath>
+
 #include "internal.cuh"
 
 namespace bgb {
@@ -115,6 +117,10 @@ __global__ void __launch_bounds__(BOX_BLOCK) k_box_final(const BoxPartial *part,
         }
         sc->L = L;
         sc->scale = __ddiv_rn(0x1p21, L);
+        for (int d = 0; d < 3; ++d) {
+            sc->mn[d] = lo[d];
+            sc->mx[d] = hi[d];
+        }
         if (sbad) atomicOr(&sc->status, ST_BAD_INPUT);
     }
 }
@@ -228,3 +234,24 @@ void launch_keys(bonsai_ctx *c, const double *pos, int64_t n, const uint32_t *id
 }
 
 }  // namespace bgb
+
+// The cube of k_box_final, on the host, for bounds reduced over processes.
+// Each step is one IEEE FP64 operation in the kernel's order (the product
+// by 0.5 is exact, so a fused multiply-add could not change the result).
+extern "C" int bonsai_cube_from_bounds(const double mn[3], const double mx[3], double cube[4]) {
+    if (!mn || !mx || !cube) return BONSAI_EINVAL;
+    for (int d = 0; d < 3; ++d)
+        if (!std::isfinite(mn[d]) || !std::isfinite(mx[d]) || mn[d] > mx[d]) return BONSAI_EINVAL;
+    double ext = mx[0] - mn[0];
+    const double e1 = mx[1] - mn[1], e2 = mx[2] - mn[2];
+    if (e1 > ext) ext = e1;
+    if (e2 > ext) ext = e2;
+    double L = ext * (1.0 + 0x1p-20);
+    if (ext == 0.0) L = 1.0;
+    for (int d = 0; d < 3; ++d) {
+        const double w = mx[d] - mn[d];
+        cube[d] = mn[d] - (L - w) * 0.5;
+    }
+    cube[3] = L;
+    return BONSAI_OK;
+}

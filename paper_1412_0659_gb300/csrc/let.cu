@@ -28,6 +28,7 @@ struct bonsai_let {
     bgb::DBuf<uint32_t> src_node, kind;  // per LET cell: source cell, 0 used whole / 1 opened cell / 2 opened leaf
     bgb::DBuf<uint32_t> vis, opn, vscan, pcount, pscan, tmp, front;
     bgb::DBuf<int32_t> status;  // [0]: frontier overflow
+    bool has_sources = false;   // src_node / kind describe the current cells
     uint32_t *dtot = nullptr;   // device: {cells, particles}
     uint32_t *htot = nullptr;   // pinned host mirror
 };
@@ -179,6 +180,22 @@ __global__ void __launch_bounds__(256) k_let_compact(
     }
 }
 
+// A received LET's topology must describe a tree that the walk can follow
+// safely: an internal cell's 1-8 children come after it (so no path
+// returns to a cell) and inside the cell array, a leaf's particles inside
+// the particle array.  Any other entry sets status[0].
+__global__ void __launch_bounds__(256) k_let_validate(const uint2 *__restrict__ topo, int64_t nn,
+                                                     int64_t np, int32_t *__restrict__ status) {
+    for (int64_t i = blockIdx.x * 256ll + threadIdx.x; i < nn; i += (int64_t)gridDim.x * 256) {
+        const uint2 t = topo[i];
+        const uint64_t cnt = t.y & ~LEAF_FLAG;
+        const bool ok = (t.y & LEAF_FLAG) ? (uint64_t)t.x + cnt <= (uint64_t)np
+                                          : (cnt >= 1 && cnt <= 8 && (int64_t)t.x > i &&
+                                             (uint64_t)t.x + cnt <= (uint64_t)nn);
+        if (!ok) atomicOr(&status[0], 1);
+    }
+}
+
 }  // namespace
 
 void launch_set_cube(bonsai_ctx *c) {
@@ -199,7 +216,7 @@ extern "C" int tree_domain_state(bonsai_ctx *c, int64_t first, int64_t count, do
         c->pos.p, c->vel.p, c->mass.p, c->id.p, c->n, first, count, pos, vel, mass, caller_id);
     c->launches += 1;
     BGB_CUDA(cudaPeekAtLastError());
-    BGB_CUDA(cudaStreamSynchronize(c->stream));
+    BGB_WAIT(c->stream);
     return BONSAI_OK;
 }
 
@@ -225,7 +242,7 @@ extern "C" int let_create(bonsai_let **out, void *stream) {
 
 extern "C" void let_destroy(bonsai_let *l) {
     if (!l) return;
-    cudaStreamSynchronize(l->stream);
+    wait_stream(l->stream);  // bounded; cudaFree below waits for the device in any case
     release(l->mac); release(l->ca); release(l->cb); release(l->cc); release(l->hi); release(l->lo);
     release(l->topo); release(l->src_node); release(l->kind); release(l->vis); release(l->opn);
     release(l->vscan); release(l->pcount); release(l->pscan); release(l->tmp); release(l->front);
@@ -235,19 +252,19 @@ extern "C" void let_destroy(bonsai_let *l) {
     delete l;
 }
 
-extern "C" int let_build(bonsai_let *l, bonsai_ctx *src, const bonsai_ctx *dst, float theta) {
-    if (!l || !src || !dst || !(theta > 0.0f) || !isfinite(theta)) return BONSAI_EINVAL;
-    if (!src->have_tree || !dst->have_tree) return BONSAI_ESTATE;
-    if (src->cube[3] != dst->cube[3] || src->cube[3] <= 0.0 || src->cube[0] != dst->cube[0] ||
-        src->cube[1] != dst->cube[1] || src->cube[2] != dst->cube[2])
-        return BONSAI_EINVAL;  // both must be branches of one global octree
+namespace bgb {
+
+// The LET of src's tree for the group boxes (box, half: device float4 [ng],
+// {c.xyz, 0} and {h.xyz, 0} as the walk stores them).
+static int let_build_impl(bonsai_let *l, bonsai_ctx *src, const float4 *box, const float4 *half,
+                          int64_t ng, float theta) {
     cudaStream_t s = l->stream;
     if (src->packed_theta != theta) {  // the source's cell records at this theta
         launch_cell_pack(src, theta);
         src->packed_theta = theta;
     }
-    BGB_CUDA(cudaStreamSynchronize(src->stream));  // dst's records come from a finished build
-    const int64_t nn = src->n_nodes, ng = dst->n_groups;
+    BGB_WAIT(src->stream);  // the boxes and records come from finished work
+    const int64_t nn = src->n_nodes;
     int blocks = src->sm_count * 2;
     const int64_t need_blocks = (ng + MARK_WARPS - 1) / MARK_WARPS;
     if (blocks > need_blocks) blocks = (int)need_blocks;
@@ -259,19 +276,16 @@ extern "C" int let_build(bonsai_let *l, bonsai_ctx *src, const bonsai_ctx *dst, 
     BGB_CUDA(cudaMemsetAsync(l->vis.p, 0, nn * sizeof(uint32_t), s));
     BGB_CUDA(cudaMemsetAsync(l->opn.p, 0, nn * sizeof(uint32_t), s));
     BGB_CUDA(cudaMemsetAsync(l->status.p, 0, 4 * sizeof(int32_t), s));
-    k_let_mark<<<blocks, MARK_WARPS * 32, 0, s>>>(src->cell_mac.p, src->cell_topo.p, dst->grp_box.p,
-                                                 dst->grp_half.p, ng, l->vis.p, l->opn.p,
-                                                 l->front.p, l->status.p);
+    k_let_mark<<<blocks, MARK_WARPS * 32, 0, s>>>(src->cell_mac.p, src->cell_topo.p, box, half, ng,
+                                                 l->vis.p, l->opn.p, l->front.p, l->status.p);
     k_let_counts<<<grid_for(nn, 256, l->sm_count * 16), 256, 0, s>>>(src->cell_topo.p, l->vis.p,
                                                                      l->opn.p, nn, l->pcount.p);
     exclusive_scan_into(s, l->vis.p, l->vscan.p, nn, l->tmp.p, l->dtot);
     exclusive_scan_into(s, l->pcount.p, l->pscan.p, nn, l->tmp.p, l->dtot + 1);
     BGB_CUDA(cudaMemcpyAsync(l->htot, l->dtot, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-    int32_t hstatus = 0;
     BGB_CUDA(cudaMemcpyAsync(&l->htot[2], l->status.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    BGB_CUDA(cudaStreamSynchronize(s));
-    hstatus = (int32_t)l->htot[2];
-    if (hstatus) return BONSAI_EOVERFLOW;
+    BGB_WAIT(s);
+    if ((int32_t)l->htot[2]) return BONSAI_EOVERFLOW;
     const int64_t lnn = l->htot[0], lnp = l->htot[1];
     if (ensure(l->mac, lnn) || ensure(l->topo, lnn) || ensure(l->ca, lnn) || ensure(l->cb, lnn) ||
         ensure(l->cc, lnn) || ensure(l->src_node, lnn) || ensure(l->kind, lnn) ||
@@ -282,11 +296,155 @@ extern "C" int let_build(bonsai_let *l, bonsai_ctx *src, const bonsai_ctx *dst, 
         src->body_hi.p, src->body_lo.p, nn, l->vis.p, l->opn.p, l->vscan.p, l->pscan.p, l->mac.p,
         l->topo.p, l->ca.p, l->cb.p, l->cc.p, l->hi.p, l->lo.p, l->src_node.p, l->kind.p);
     BGB_CUDA(cudaPeekAtLastError());
-    BGB_CUDA(cudaStreamSynchronize(s));
+    BGB_WAIT(s);
     l->nn = lnn;
     l->np = lnp;
     l->src_nodes = nn;
     l->theta = theta;
+    l->has_sources = true;
+    return BONSAI_OK;
+}
+
+}  // namespace bgb
+
+extern "C" int let_build(bonsai_let *l, bonsai_ctx *src, const bonsai_ctx *dst, float theta) {
+    if (!l || !src || !dst || !(theta > 0.0f) || !isfinite(theta)) return BONSAI_EINVAL;
+    if (!src->have_tree || !dst->have_tree) return BONSAI_ESTATE;
+    if (src->cube[3] != dst->cube[3] || src->cube[3] <= 0.0 || src->cube[0] != dst->cube[0] ||
+        src->cube[1] != dst->cube[1] || src->cube[2] != dst->cube[2])
+        return BONSAI_EINVAL;  // both must be branches of one global octree
+    BGB_WAIT(dst->stream);  // dst's group boxes come from a finished build
+    return let_build_impl(l, src, dst->grp_box.p, dst->grp_half.p, dst->n_groups, theta);
+}
+
+extern "C" int let_build_boxes(bonsai_let *l, bonsai_ctx *src, const float *box, const float *half,
+                               int64_t ngroups, float theta) {
+    if (!l || !src || !box || !half || ngroups < 0 || !(theta > 0.0f) || !isfinite(theta))
+        return BONSAI_EINVAL;
+    if (!src->have_tree) return BONSAI_ESTATE;
+    if (ngroups == 0) {  // nothing to walk: an empty LET
+        l->nn = l->np = 0;
+        l->src_nodes = src->n_nodes;
+        l->has_sources = false;
+        return BONSAI_OK;
+    }
+    return let_build_impl(l, src, reinterpret_cast<const float4 *>(box),
+                          reinterpret_cast<const float4 *>(half), ngroups, theta);
+}
+
+extern "C" int tree_get_group_boxes(bonsai_ctx *c, float *box, float *half, int64_t *ngroups) {
+    if (!c) return BONSAI_EINVAL;
+    if (!c->have_tree) return BONSAI_ESTATE;
+    if (ngroups) *ngroups = c->n_groups;
+    const size_t bytes = (size_t)c->n_groups * sizeof(float4);
+    if (box) BGB_CUDA(cudaMemcpyAsync(box, c->grp_box.p, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    if (half) BGB_CUDA(cudaMemcpyAsync(half, c->grp_half.p, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    BGB_WAIT(c->stream);
+    return BONSAI_OK;
+}
+
+namespace {
+
+// Packed LET: a 64-byte header, then the cell records (mac, ca, cb, cc as
+// float4 [nn], topo as uint2 [nn] padded to 16 bytes) and the particle
+// records (hi, lo as float4 [np]).
+struct LetHeader {
+    uint64_t magic;   // "BGBLET01"
+    int64_t nn, np;
+    int64_t bytes;    // total packed size
+    float theta;
+    uint32_t pad[7];
+};
+static_assert(sizeof(LetHeader) == 64, "LET header");
+constexpr uint64_t LET_MAGIC = 0x31305445'4C424742ull;  // "BGBLET01" little-endian
+
+int64_t pad16(int64_t b) { return (b + 15) & ~(int64_t)15; }
+int64_t packed_bytes(int64_t nn, int64_t np) {
+    return (int64_t)sizeof(LetHeader) + 4 * 16 * nn + pad16(8 * nn) + 2 * 16 * np;
+}
+
+}  // namespace
+
+extern "C" int let_pack(const bonsai_let *l, void *buf, int64_t cap, int64_t *bytes) {
+    if (!l || !bytes) return BONSAI_EINVAL;
+    const int64_t b = packed_bytes(l->nn, l->np);
+    *bytes = b;
+    if (!buf) return BONSAI_OK;
+    if (cap < b || (reinterpret_cast<uintptr_t>(buf) & 15u)) return BONSAI_EINVAL;
+    LetHeader h{};
+    h.magic = LET_MAGIC;
+    h.nn = l->nn;
+    h.np = l->np;
+    h.bytes = b;
+    h.theta = l->theta;
+    cudaStream_t s = l->stream;
+    char *p = static_cast<char *>(buf);
+    BGB_CUDA(cudaMemcpyAsync(p, &h, sizeof(h), cudaMemcpyHostToDevice, s));
+    p += sizeof(h);
+    const size_t c16 = 16 * (size_t)l->nn, p16 = 16 * (size_t)l->np;
+    if (l->nn) {
+        BGB_CUDA(cudaMemcpyAsync(p, l->mac.p, c16, cudaMemcpyDeviceToDevice, s));
+        BGB_CUDA(cudaMemcpyAsync(p + c16, l->ca.p, c16, cudaMemcpyDeviceToDevice, s));
+        BGB_CUDA(cudaMemcpyAsync(p + 2 * c16, l->cb.p, c16, cudaMemcpyDeviceToDevice, s));
+        BGB_CUDA(cudaMemcpyAsync(p + 3 * c16, l->cc.p, c16, cudaMemcpyDeviceToDevice, s));
+        BGB_CUDA(cudaMemcpyAsync(p + 4 * c16, l->topo.p, 8 * (size_t)l->nn, cudaMemcpyDeviceToDevice, s));
+    }
+    p += 4 * c16 + pad16(8 * l->nn);
+    if (l->np) {
+        BGB_CUDA(cudaMemcpyAsync(p, l->hi.p, p16, cudaMemcpyDeviceToDevice, s));
+        BGB_CUDA(cudaMemcpyAsync(p + p16, l->lo.p, p16, cudaMemcpyDeviceToDevice, s));
+    }
+    BGB_WAIT(s);  // h lives on this stack frame
+    return BONSAI_OK;
+}
+
+extern "C" int let_unpack(bonsai_let *l, const void *buf, int64_t bytes) {
+    if (!l || !buf || bytes < (int64_t)sizeof(LetHeader) || (reinterpret_cast<uintptr_t>(buf) & 15u))
+        return BONSAI_EINVAL;
+    cudaStream_t s = l->stream;
+    LetHeader h{};
+    BGB_CUDA(cudaMemcpyAsync(&h, buf, sizeof(h), cudaMemcpyDeviceToHost, s));
+    BGB_WAIT(s);
+    if (h.magic != LET_MAGIC || h.nn < 0 || h.np < 0 || h.nn > 0xffffffffll || h.np > 0xffffffffll ||
+        h.bytes != bytes || packed_bytes(h.nn, h.np) != bytes || !(h.theta > 0.0f))
+        return BONSAI_EINVAL;
+    if (ensure(l->mac, h.nn) || ensure(l->topo, h.nn) || ensure(l->ca, h.nn) || ensure(l->cb, h.nn) ||
+        ensure(l->cc, h.nn) || ensure(l->hi, h.np) || ensure(l->lo, h.np))
+        return BONSAI_ENOMEM;
+    const char *p = static_cast<const char *>(buf) + sizeof(LetHeader);
+    const size_t c16 = 16 * (size_t)h.nn, p16 = 16 * (size_t)h.np;
+    if (ensure(l->status, 4)) return BONSAI_ENOMEM;
+    if (h.nn) {
+        BGB_CUDA(cudaMemcpyAsync(l->mac.p, p, c16, cudaMemcpyDeviceToDevice, s));
+        BGB_CUDA(cudaMemcpyAsync(l->ca.p, p + c16, c16, cudaMemcpyDeviceToDevice, s));
+        BGB_CUDA(cudaMemcpyAsync(l->cb.p, p + 2 * c16, c16, cudaMemcpyDeviceToDevice, s));
+        BGB_CUDA(cudaMemcpyAsync(l->cc.p, p + 3 * c16, c16, cudaMemcpyDeviceToDevice, s));
+        BGB_CUDA(cudaMemcpyAsync(l->topo.p, p + 4 * c16, 8 * (size_t)h.nn, cudaMemcpyDeviceToDevice, s));
+    }
+    p += 4 * c16 + pad16(8 * h.nn);
+    if (h.np) {
+        BGB_CUDA(cudaMemcpyAsync(l->hi.p, p, p16, cudaMemcpyDeviceToDevice, s));
+        BGB_CUDA(cudaMemcpyAsync(l->lo.p, p + p16, p16, cudaMemcpyDeviceToDevice, s));
+    }
+    BGB_CUDA(cudaMemsetAsync(l->status.p, 0, 4 * sizeof(int32_t), s));
+    if (h.nn) {
+        k_let_validate<<<grid_for(h.nn, 256, l->sm_count * 16), 256, 0, s>>>(l->topo.p, h.nn, h.np,
+                                                                            l->status.p);
+        BGB_CUDA(cudaPeekAtLastError());
+    }
+    int32_t bad = 0;
+    BGB_CUDA(cudaMemcpyAsync(&bad, l->status.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    BGB_WAIT(s);
+    if (bad) {
+        l->nn = l->np = 0;
+        l->has_sources = false;
+        return BONSAI_EINVAL;
+    }
+    l->nn = h.nn;
+    l->np = h.np;
+    l->theta = h.theta;
+    l->src_nodes = 0;
+    l->has_sources = false;  // the source-cell map stays with the sender
     return BONSAI_OK;
 }
 
@@ -301,12 +459,12 @@ extern "C" int let_get_info(const bonsai_let *l, int64_t out[4]) {
 
 extern "C" int let_debug_cells(const bonsai_let *l, uint32_t *src_node, uint32_t *kind) {
     if (!l) return BONSAI_EINVAL;
-    if (l->nn == 0) return BONSAI_ESTATE;
+    if (l->nn == 0 || !l->has_sources) return BONSAI_ESTATE;
     if (src_node) BGB_CUDA(cudaMemcpyAsync(src_node, l->src_node.p, l->nn * sizeof(uint32_t),
                                            cudaMemcpyDeviceToDevice, l->stream));
     if (kind) BGB_CUDA(cudaMemcpyAsync(kind, l->kind.p, l->nn * sizeof(uint32_t),
                                        cudaMemcpyDeviceToDevice, l->stream));
-    BGB_CUDA(cudaStreamSynchronize(l->stream));
+    BGB_WAIT(l->stream);
     return BONSAI_OK;
 }
 
@@ -320,7 +478,7 @@ extern "C" int let_forces(bonsai_ctx *dst, const bonsai_let *l, float eps) {
     if (rc) return rc;
     BGB_CUDA(cudaMemcpyAsync(dst->hsc, dst->dsc, sizeof(DevScalars), cudaMemcpyDeviceToHost,
                              dst->stream));
-    BGB_CUDA(cudaStreamSynchronize(dst->stream));
+    BGB_WAIT(dst->stream);
     cudaEventElapsedTime(&dst->stats.ms_walk, dst->ev[8], dst->ev[9]);
     dst->stats.n_pp = dst->hsc->n_pp;
     dst->stats.n_pc = dst->hsc->n_pc;

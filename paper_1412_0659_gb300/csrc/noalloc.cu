@@ -13,8 +13,7 @@ using bgb::BoxPartial;
 using bgb::DevScalars;
 
 constexpr int64_t MAX_N = BONSAI_NOALLOC_MAX_N;
-constexpr int64_t MAX_TILES = (MAX_N + 4095) / 4096;  // sort tiles of 4096 pairs
-constexpr int MAX_PART = 1024;                         // bounding-box block partials
+constexpr int MAX_PART = 1024;  // bounding-box block partials
 constexpr int MAX_DEVICES = 64;
 
 constexpr size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -22,11 +21,20 @@ constexpr size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 // byte offsets of the regions of the scratch array
 constexpr size_t OFF_KEY2 = 0;
 constexpr size_t OFF_VAL2 = OFF_KEY2 + align256(sizeof(uint64_t) * MAX_N);
+constexpr size_t HIST_ELEMS = bgb::sort_hist_elems(MAX_N);
+// the sort scans its 256 x tiles histogram entries
+constexpr size_t SCAN_ELEMS = bgb::scan_tmp_elems((int64_t)(HIST_ELEMS - 64));
 constexpr size_t OFF_HIST = OFF_VAL2 + align256(sizeof(uint32_t) * MAX_N);
-constexpr size_t OFF_SCAN = OFF_HIST + align256(sizeof(uint32_t) * (256 * MAX_TILES + 64));
-constexpr size_t OFF_PART = OFF_SCAN + align256(sizeof(uint32_t) * 4096);
+constexpr size_t OFF_SCAN = OFF_HIST + align256(sizeof(uint32_t) * HIST_ELEMS);
+constexpr size_t OFF_PART = OFF_SCAN + align256(sizeof(uint32_t) * SCAN_ELEMS);
 constexpr size_t OFF_DSC = OFF_PART + align256(sizeof(BoxPartial) * MAX_PART);
 constexpr size_t SCRATCH_BYTES = OFF_DSC + align256(sizeof(DevScalars));
+// the regions are sized from the sort's own tile constants, so a retuned sort
+// cannot write past its region; the total stays modest
+static_assert(OFF_SCAN - OFF_HIST >= sizeof(uint32_t) * bgb::sort_hist_elems(MAX_N), "histogram region");
+static_assert(OFF_PART - OFF_SCAN >= sizeof(uint32_t) * bgb::scan_tmp_elems(256 * ((MAX_N + bgb::SORT_TILE - 1) / bgb::SORT_TILE)),
+              "scan region");
+static_assert(SCRATCH_BYTES < (16u << 20), "scratch array above 16 MB");
 
 // The scratch of every call on this device.  Host code must not use its name
 // as an address: the device address comes from cudaGetSymbolAddress.
@@ -85,7 +93,7 @@ extern "C" int bonsai_sfc_order_noalloc(const double *pos, const double *mass, i
     BGB_CUDA(cudaGetLastError());
     DevScalars h;
     BGB_CUDA(cudaMemcpyAsync(&h, dsc, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
-    BGB_CUDA(cudaStreamSynchronize(s));
+    BGB_WAIT(s);
     if (h.status & bgb::ST_BAD_INPUT) return BONSAI_EINVAL;
     if (cube) {
         cube[0] = h.lo[0];

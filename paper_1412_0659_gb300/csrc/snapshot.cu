@@ -146,7 +146,8 @@ extern "C" int tree_save_snapshot(bonsai_ctx *c, const char *path, double time) 
     }
     if (fclose(f) != 0) ok = false;
     if (!ok) {
-        cudaStreamSynchronize(c->stream);
+        const int w = wait_stream(c->stream);
+        if (w != BONSAI_OK) return w;
         return cudaGetLastError() != cudaSuccess ? BONSAI_ECUDA : BONSAI_EIO;
     }
     return BONSAI_OK;
@@ -194,7 +195,7 @@ extern "C" int tree_load_snapshot(bonsai_ctx *c, const char *path, double *time)
                  cudaEventRecord(ev[b], c->stream) == cudaSuccess;
     }
     fclose(f);
-    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return BONSAI_ECUDA;
+    BGB_WAIT(c->stream);
     if (!ok) return BONSAI_EIO;
     rc = rebuild(c, c->pos2.p, c->mass2.p, true);
     if (rc) return rc;
@@ -203,7 +204,7 @@ extern "C" int tree_load_snapshot(bonsai_ctx *c, const char *path, double *time)
     c->stats.n_groups = c->n_groups;
     c->stats.depth = c->depth;
     launch_permute_in_vel(c, c->vel2.p);
-    BGB_CUDA(cudaStreamSynchronize(c->stream));
+    BGB_WAIT(c->stream);
     c->have_vel = true;
     if (time) *time = h.time;
     return BONSAI_OK;
@@ -224,6 +225,6 @@ extern "C" int tree_surface_density(bonsai_ctx *c, int64_t first, int64_t count,
         window[2], hx, hy, nx, ny, map);
     c->launches += 1;
     BGB_CUDA(cudaPeekAtLastError());
-    BGB_CUDA(cudaStreamSynchronize(c->stream));
+    BGB_WAIT(c->stream);
     return BONSAI_OK;
 }

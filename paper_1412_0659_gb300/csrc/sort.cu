@@ -15,14 +15,9 @@ namespace bgb {
 
 namespace {
 
-constexpr int SORT_BLOCK = 256;
-constexpr int SORT_IPT = 16;
-constexpr int SORT_TILE = SORT_BLOCK * SORT_IPT;
+// SORT_BLOCK, SORT_IPT, SORT_TILE, SCAN_BLOCK, SCAN_IPT and SCAN_TILE are
+// in internal.cuh: the scratch sizes of every caller derive from them.
 constexpr int SORT_WARPS = SORT_BLOCK / 32;
-
-constexpr int SCAN_BLOCK = 1024;
-constexpr int SCAN_IPT = 4;
-constexpr int SCAN_TILE = SCAN_BLOCK * SCAN_IPT;
 
 __device__ inline uint32_t lanemask_lt() {
     uint32_t m;
@@ -266,18 +261,6 @@ int exclusive_scan_into(cudaStream_t s, const uint32_t *in, uint32_t *out, int64
     }
     return launches;
 }
-
-size_t scan_tmp_elems(int64_t n) {
-    size_t t = 0;
-    int64_t m = n;
-    while (m > SCAN_TILE) {
-        m = (m + SCAN_TILE - 1) / SCAN_TILE;
-        t += 2 * (size_t)m;
-    }
-    return t + 64;
-}
-
-size_t sort_hist_elems(int64_t n) { return 256 * (size_t)((n + SORT_TILE - 1) / SORT_TILE) + 64; }
 
 // The same eight passes on explicit buffers: (ka, va) hold the input and the
 // result, (kb, vb) are the second ping-pong half, hist holds

@@ -22,7 +22,6 @@
 
 namespace bgb {
 
-size_t scan_tmp_elems(int64_t n);
 
 namespace {
 
@@ -225,6 +224,43 @@ __global__ void __launch_bounds__(256) k_group_flags(const uint32_t *__restrict_
     }
 }
 
+#ifdef GROUP_EXP_MERGE
+// experiment: consecutive sibling groups merged greedily up to NCRIT
+__global__ void __launch_bounds__(256) k_group_flags_merge(const uint32_t *__restrict__ first,
+                                                           const uint32_t *__restrict__ count,
+                                                           const uint32_t *__restrict__ nchild,
+                                                           const uint32_t *__restrict__ child,
+                                                           uint32_t *__restrict__ flag, int64_t nn) {
+    int64_t i = blockIdx.x * 256ll + threadIdx.x;
+    if (i >= nn) return;
+    const uint32_t c = count[i];
+    if (c <= (uint32_t)NCRIT) {
+        if (i == 0) flag[first[0]] = 1u;
+        return;
+    }
+    if (nchild[i] == 0) {
+        for (uint32_t s = 0; s < c; s += NCRIT) flag[first[i] + s] = 1u;
+        return;
+    }
+    uint32_t run = 0;
+    bool open = false;
+    for (uint32_t k = 0; k < nchild[i]; ++k) {
+        const uint32_t j = child[i] + k, cj = count[j];
+        if (cj > (uint32_t)NCRIT) {
+            open = false;
+            continue;
+        }
+        if (!open || run + cj > (uint32_t)NCRIT) {
+            flag[first[j]] = 1u;
+            run = cj;
+            open = true;
+        } else {
+            run += cj;
+        }
+    }
+}
+#endif
+
 __global__ void __launch_bounds__(256) k_group_write(const uint32_t *__restrict__ flag,
                                                      const uint32_t *__restrict__ gid, int64_t n,
                                                      uint32_t *__restrict__ gfirst) {
@@ -383,7 +419,7 @@ static int grow_nodes(bonsai_ctx *c, int64_t need, int64_t keep) {
         if (cudaMalloc(&p, cap * sizeof(uint32_t)) != cudaSuccess) return BONSAI_ENOMEM;
         if (keep > 0 && b->p)
             cudaMemcpyAsync(p, b->p, keep * sizeof(uint32_t), cudaMemcpyDeviceToDevice, c->stream);
-        cudaStreamSynchronize(c->stream);
+        BGB_WAIT(c->stream);
         cudaFree(b->p);
         b->p = p;
         b->cap = cap;
@@ -394,7 +430,7 @@ static int grow_nodes(bonsai_ctx *c, int64_t need, int64_t keep) {
         if (keep > 0 && c->cell_topo.p)
             cudaMemcpyAsync(p, c->cell_topo.p, keep * sizeof(uint2), cudaMemcpyDeviceToDevice,
                             c->stream);
-        cudaStreamSynchronize(c->stream);
+        BGB_WAIT(c->stream);
         cudaFree(c->cell_topo.p);
         c->cell_topo.p = p;
         c->cell_topo.cap = cap;
@@ -436,7 +472,7 @@ int build_octree(bonsai_ctx *c) {
         exclusive_scan_u32(c, c->nd_scan.p, c->grp_flag.p, m, &c->dsc->level_count);
         BGB_CUDA(cudaMemcpyAsync(&c->hsc->level_count, &c->dsc->level_count, sizeof(uint32_t),
                                  cudaMemcpyDeviceToHost, c->stream));
-        BGB_CUDA(cudaStreamSynchronize(c->stream));
+        BGB_WAIT(c->stream);
         const int64_t tot = c->hsc->level_count;
         rc = grow_nodes(c, e + tot, e);
         if (rc) return rc;
@@ -455,15 +491,21 @@ int build_octree(bonsai_ctx *c) {
 int build_groups(bonsai_ctx *c) {
     const int64_t n = c->n, nn = c->n_nodes;
     BGB_CUDA(cudaMemsetAsync(c->grp_flag.p, 0, (n + 1) * sizeof(uint32_t), c->stream));
+#ifdef GROUP_EXP_MERGE
+    k_group_flags_merge<<<grid_for(nn, 256), 256, 0, c->stream>>>(c->nd_first.p, c->nd_count.p,
+                                                                   c->nd_nchild.p, c->nd_child.p,
+                                                                   c->grp_flag.p, nn);
+#else
     k_group_flags<<<grid_for(nn, 256), 256, 0, c->stream>>>(c->nd_first.p, c->nd_count.p,
                                                              c->nd_nchild.p, c->nd_parent.p,
                                                              c->grp_flag.p, nn);
+#endif
     c->launches += 1;
     uint32_t *gid = c->grp_flag.p + (n + 1);
     exclusive_scan_u32(c, c->grp_flag.p, gid, n, &c->dsc->n_groups);
     BGB_CUDA(cudaMemcpyAsync(&c->hsc->n_groups, &c->dsc->n_groups, sizeof(uint32_t),
                              cudaMemcpyDeviceToHost, c->stream));
-    BGB_CUDA(cudaStreamSynchronize(c->stream));
+    BGB_WAIT(c->stream);
     const int64_t ng = c->hsc->n_groups;
     c->n_groups = ng;
     if (ensure(c->grp_first, ng) || ensure(c->grp_count, ng) || ensure(c->grp_centre, 3 * ng) ||

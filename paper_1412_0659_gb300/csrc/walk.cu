@@ -24,6 +24,7 @@
 // shared memory) and the adjoint one (list entries in lanes, targets
 // broadcast), which recomputes exactly the same lists.
 #include "internal.cuh"
+#include "packed.cuh"
 
 namespace bgb {
 
@@ -40,6 +41,9 @@ struct __align__(16) WarpLists {
     float4 pp[RING];  // {dx, dy, dz, m}: particle relative to the group centre
     int pid[RING];    // sorted index of the particle
     int cid[RING];    // node index of the cell
+#ifdef WALK_EXP_DIET
+    float4 gbox, ghalf, glo;  // the group's box, read from here rather than kept in registers
+#endif
 };
 
 // Targets of one group for the adjoint policy, two per record (targets 2p
@@ -97,6 +101,15 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
     return m;
+}
+
+// A shared-memory float4 read that the compiler may not hoist into registers.
+__device__ __forceinline__ float4 lds_f4(const float4 *p) {
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"((unsigned)__cvta_generic_to_shared(p)));
+    return v;
 }
 
 __device__ __forceinline__ uint32_t warp_excl_scan(uint32_t v, uint32_t &total) {
@@ -204,10 +217,21 @@ struct Fp32Rings {
                                                 uint32_t node, float4 m, float4 box, float4 clo,
                                                 uint32_t) {
         const float4 a = A.ca[node];
+#ifdef WALK_EXP_CPASYNC
+        {
+            const unsigned sb = (unsigned)__cvta_generic_to_shared(&L.cb[s]);
+            const unsigned sc2 = (unsigned)__cvta_generic_to_shared(&L.cc[s]);
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(sb), "l"(A.cb + node));
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(sc2), "l"(A.cc + node));
+        }
+        L.ca[s] = make_float4((m.x - box.x) + (a.x - clo.x), (m.y - box.y) + (a.y - clo.y),
+                              (m.z - box.z) + (a.z - clo.z), a.w);
+#else
         L.ca[s] = make_float4((m.x - box.x) + (a.x - clo.x), (m.y - box.y) + (a.y - clo.y),
                               (m.z - box.z) + (a.z - clo.z), a.w);
         L.cb[s] = A.cb[node];
         L.cc[s] = A.cc[node];
+#endif
         L.cid[s] = (int)node;
     }
     __device__ __forceinline__ void append_particle(const WalkArgs &A, WarpLists &L, uint32_t s,
@@ -253,6 +277,25 @@ struct ForwardPolicy : Fp32Rings {
     // entries [hb, hb + cnt) of the p-c ring (hb a multiple of 32, cnt <= 32)
     __device__ __forceinline__ void flush_pc(const WarpLists &L, int hb, int cnt) {
         const int end = hb + cnt;
+#ifdef WALK_EXP_UNROLL2
+        int j = hb + j0;
+#pragma unroll 1
+        for (; j + S < end; j += 2 * S) {
+            const float4 a = L.ca[j], b = L.cb[j], c = L.cc[j];
+            const float4 a1 = L.ca[j + S], b1 = L.cb[j + S], c1 = L.cc[j + S];
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                pc_one(a, b, c, t.x[k], t.y[k], t.z[k], eps2, t.ax[k], t.ay[k], t.az[k], t.ph[k]);
+                pc_one(a1, b1, c1, t.x[k], t.y[k], t.z[k], eps2, t.ax[k], t.ay[k], t.az[k], t.ph[k]);
+            }
+        }
+        if (j < end) {
+            const float4 a = L.ca[j], b = L.cb[j], c = L.cc[j];
+#pragma unroll
+            for (int k = 0; k < 2; ++k)
+                pc_one(a, b, c, t.x[k], t.y[k], t.z[k], eps2, t.ax[k], t.ay[k], t.az[k], t.ph[k]);
+        }
+#else
 #pragma unroll 1
         for (int j = hb + j0; j < end; j += S) {
             const float4 a = L.ca[j], b = L.cb[j], c = L.cc[j];
@@ -260,6 +303,7 @@ struct ForwardPolicy : Fp32Rings {
             for (int k = 0; k < 2; ++k)
                 pc_one(a, b, c, t.x[k], t.y[k], t.z[k], eps2, t.ax[k], t.ay[k], t.az[k], t.ph[k]);
         }
+#endif
     }
 
     __device__ __forceinline__ void flush_pp(const WarpLists &L, int hb, int cnt) {
@@ -314,36 +358,7 @@ struct ForwardPolicy : Fp32Rings {
 // Adjoint evaluation
 // ---------------------------------------------------------------------------
 
-// Two FP32 values in one 64-bit register pair, operated on by the packed
-// FP32 instructions of sm_100 and later (add/mul/fma.rn.f32x2): one issue
-// slot performs two IEEE round-to-nearest operations, each bit-identical to
-// its scalar counterpart.  The adjoint evaluates two targets per operation.
-typedef unsigned long long f32x2;
-
-__device__ __forceinline__ f32x2 p2(float lo, float hi) {
-    f32x2 r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-    return r;
-}
-__device__ __forceinline__ void u2(f32x2 v, float &lo, float &hi) {
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-}
-__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b) {
-    f32x2 d;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
-    f32x2 d;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
-    f32x2 d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
-__device__ __forceinline__ f32x2 dup2(float v) { return p2(v, v); }
+// The adjoint evaluates two targets per packed FP32 operation (packed.cuh).
 __device__ __forceinline__ ulonglong2 lds2(const float4 &v) {
     return *reinterpret_cast<const ulonglong2 *>(&v);
 }
@@ -759,6 +774,9 @@ struct __align__(16) WarpLists64 {
     double q[6][RING];  // xx yy zz xy xz yz
     double px[RING], py[RING], pz[RING], pm[RING];
     int pid[RING];
+#ifdef WALK_EXP_DIET
+    float4 gbox, ghalf, glo;
+#endif
 };
 
 __device__ __forceinline__ void pc_one64(double rx, double ry, double rz, double M, double qxx,
@@ -934,11 +952,24 @@ __device__ __forceinline__ void walk_group(const WalkArgs &A, LT &L, WarpTargets
                                            uint32_t g, uint32_t *fa, uint32_t *fb, int lane,
                                            uint32_t lt) {
     const uint32_t gf = A.gfirst[g], gc = A.gcount[g];
+#ifdef WALK_EXP_DIET
+    {
+        const float4 box = A.gbox[g], clo = A.glo[g];
+        if (lane == 0) {
+            L.gbox = box;
+            L.ghalf = A.ghalf[g];
+            L.glo = clo;
+        }
+        pol.begin(A, tgt, g, gf, gc, box, clo, lane);
+    }
+    __syncwarp();
+#else
     const float4 box = A.gbox[g], half = A.ghalf[g], clo = A.glo[g];
     pol.begin(A, tgt, g, gf, gc, box, clo, lane);
+#endif
 
+    // pc_tail and pp_tail count every entry ever appended: the list lengths
     uint32_t pc_head = 0, pc_tail = 0, pp_head = 0, pp_tail = 0;
-    uint32_t npc = 0, npp = 0;
     uint32_t *cur = fa, *nxt = fb;
     if (lane == 0) cur[0] = 0u;  // the root
     uint32_t ncur = 1;
@@ -954,6 +985,9 @@ __device__ __forceinline__ void walk_group(const WalkArgs &A, LT &L, WarpTargets
             const uint32_t node = valid ? cur[idx] : 0u;
             const float4 m = A.mac[node];
             const uint2 tp = A.topo[node];
+#ifdef WALK_EXP_DIET
+            const float4 box = lds_f4(&L.gbox), half = lds_f4(&L.ghalf), clo = lds_f4(&L.glo);
+#endif
             const bool open = mac_open(m, box, half);  // Sec. I.A opening test
             const bool leaf = (tp.y & LEAF_FLAG) != 0u;
             const bool accept = valid && !open;
@@ -964,7 +998,6 @@ __device__ __forceinline__ void walk_group(const WalkArgs &A, LT &L, WarpTargets
                 pol.append_cell(A, L, (pc_tail + __popc(am & lt)) & (RING - 1), node, m, box, clo,
                                 g);
             pc_tail += __popc(am);
-            npc += __popc(am);
 
             // one warp scan for both the children of opened internal cells
             // (low 9 bits: at most 8 per lane) and the particles of opened
@@ -992,7 +1025,6 @@ __device__ __forceinline__ void walk_group(const WalkArgs &A, LT &L, WarpTargets
             }
 
             // opened leaves -> p-p ring, 32 particles per round
-            npp += ltot;
             for (uint32_t r = 0; r < ltot; r += 32) {
                 const uint32_t k = r + lane;
                 // owner lane: the last lane whose offset is <= k
@@ -1004,6 +1036,9 @@ __device__ __forceinline__ void walk_group(const WalkArgs &A, LT &L, WarpTargets
                 }
                 const uint32_t sfirst = __shfl_sync(0xffffffffu, tp.x, src);
                 const uint32_t soff = __shfl_sync(0xffffffffu, loff, src);
+#ifdef WALK_EXP_DIET
+                const float4 box = lds_f4(&L.gbox), clo = lds_f4(&L.glo);
+#endif
                 if (k < ltot)
                     pol.append_particle(A, L, (pp_tail + lane) & (RING - 1), sfirst + (k - soff),
                                         box, clo, g);
@@ -1016,6 +1051,9 @@ __device__ __forceinline__ void walk_group(const WalkArgs &A, LT &L, WarpTargets
                     __syncwarp();
                 }
             }
+#ifdef WALK_EXP_CPASYNC
+            asm volatile("cp.async.wait_all;" ::: "memory");
+#endif
             __syncwarp();
             while (pc_tail - pc_head >= 32u) {
                 do_flush_pc(pol, L, (int)(pc_head & (RING - 1)), 32, lane);
@@ -1037,18 +1075,23 @@ __device__ __forceinline__ void walk_group(const WalkArgs &A, LT &L, WarpTargets
     __syncwarp();
     pol.finish(A, gf, gc, lane);
     if (lane == 0) {
-        if (A.gnpp) A.gnpp[g] = (int32_t)npp;
-        if (A.gnpc) A.gnpc[g] = (int32_t)npc;
-        atomicAdd((unsigned long long *)&A.sc->n_pp, (unsigned long long)gc * npp);
-        atomicAdd((unsigned long long *)&A.sc->n_pc, (unsigned long long)gc * npc);
+        if (A.gnpp) A.gnpp[g] = (int32_t)pp_tail;
+        if (A.gnpc) A.gnpc[g] = (int32_t)pc_tail;
+        atomicAdd((unsigned long long *)&A.sc->n_pp, (unsigned long long)gc * pp_tail);
+        atomicAdd((unsigned long long *)&A.sc->n_pc, (unsigned long long)gc * pc_tail);
         atomicMax(&A.sc->max_frontier, (int)maxf);
         if (overflow) atomicOr(&A.sc->status, ST_OVERFLOW);
     }
     __syncwarp();
 }
 
+#ifdef WALK_EXP_MINB
+#define WALK_BOUNDS __launch_bounds__(WALK_WARPS * 32, WALK_EXP_MINB)
+#else
+#define WALK_BOUNDS __launch_bounds__(WALK_WARPS * 32)
+#endif
 template <int SELF>
-__global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(const WalkArgs A) {
+__global__ void WALK_BOUNDS k_walk(const WalkArgs A) {
     __shared__ WarpLists lists[WALK_WARPS];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;

@@ -38,6 +38,22 @@ class Let:
         capi.let_build(self.h, src.ctx, dst.ctx, theta)
         return self
 
+    def build_boxes(self, src: TreeGravity, box: torch.Tensor, half: torch.Tensor, theta: float) -> "Let":
+        """The LET of src's tree for group boxes received from elsewhere."""
+        capi.let_build_boxes(self.h, src.ctx, box, half, theta)
+        return self
+
+    def pack(self) -> torch.Tensor:
+        """The LET as one contiguous uint8 CUDA tensor (the message)."""
+        dev = torch.device("cuda", torch.cuda.current_device())
+        buf = torch.empty(capi.let_pack(self.h), dtype=torch.uint8, device=dev)
+        capi.let_pack(self.h, buf)
+        return buf
+
+    def unpack(self, buf: torch.Tensor) -> "Let":
+        capi.let_unpack(self.h, buf)
+        return self
+
     def info(self) -> dict:
         return capi.let_get_info(self.h)
 

@@ -53,6 +53,38 @@ def test_noalloc_order_equals_tree_build_on_consecutive_calls():
         assert cube == [*ref["lo"], ref["L"]]
 
 
+def test_noalloc_at_the_size_limit_allocates_nothing():
+    """n = BONSAI_NOALLOC_MAX_N, the only size that fills the fixed
+    histogram and scan regions: keys, order and cube equal tree_build's bit
+    for bit.  After a first call (which has looked up the scratch address),
+    a second call changes neither the device's free memory nor what torch's
+    caching allocator holds."""
+    from paper_1412_0659_gb300 import TreeGravity, capi
+    lib = capi.load()
+    dev = torch.device("cuda", 0)
+    m = workloads.milky_way(capi.BONSAI_NOALLOC_MAX_N, seed=34)
+    pos = torch.from_numpy(m.pos).to(dev)
+    mass = torch.from_numpy(m.mass).to(dev)
+    keys = torch.full((m.n,), -1, dtype=torch.int64, device=dev)
+    perm = torch.full((m.n,), -1, dtype=torch.int32, device=dev)
+    rc, cube = _call_c_abi(lib, pos, mass, keys, perm)
+    assert rc == 0, capi.strerror(rc)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    reserved0 = torch.cuda.memory_reserved()
+    rc2, cube2 = _call_c_abi(lib, pos, mass, keys, perm)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert rc2 == 0 and cube2 == cube
+    assert free1 == free0 and torch.cuda.memory_reserved() == reserved0
+    with TreeGravity(G=m.G, theta=0.4, eps=0.01) as g:
+        g.build(pos, mass)
+        ref = g.debug()
+    assert torch.equal(keys, ref["keys"])
+    assert torch.equal(perm, ref["perm"])
+    assert cube == [*ref["lo"], ref["L"]]
+
+
 def test_noalloc_rejects_bad_sizes_and_inputs():
     from paper_1412_0659_gb300 import capi
     lib = capi.load()
