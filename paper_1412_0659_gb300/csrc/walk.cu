@@ -41,9 +41,7 @@ struct __align__(16) WarpLists {
     float4 pp[RING];  // {dx, dy, dz, m}: particle relative to the group centre
     int pid[RING];    // sorted index of the particle
     int cid[RING];    // node index of the cell
-#ifdef WALK_EXP_DIET
     float4 gbox, ghalf, glo;  // the group's box, read from here rather than kept in registers
-#endif
 };
 
 // Targets of one group for the adjoint policy, two per record (targets 2p
@@ -182,22 +180,32 @@ __device__ __forceinline__ void pp_one(const float4 s, int sid, int tid, float t
     az = fmaf(mr3, dz, az);
 }
 
-// Targets of one lane: two slots.  A group of c targets is spread over
-// T2 = ceil(c/2) lanes (slot k of lane tl holds target tl + k*T2), and the
-// S = floor(32/T2) copies of that layout each take every S-th list entry;
-// the S partial sums of a target are added with shuffles at the end.  This
-// keeps most lanes busy for the small groups that dominate real trees.
+// Targets of one lane: K = 2 or 3 slots, chosen per group.  A group of c
+// targets is spread over T = ceil(c/K) lanes (slot k of lane tl holds
+// target tl + k*T), and the S = floor(32/T) copies of that layout each
+// take every S-th list entry; the S partial sums of a target are added with
+// shuffles at the end.  K is the one of 2 and 3 that keeps more of the
+// warp's target slots busy (c S / (32 K)): groups of 33-48 targets use 48 of
+// 64 slots or fewer with two slots per lane, and up to 96 of 96 with three.
+constexpr int KMAX = 3;
 struct Targets {
-    float x[2], y[2], z[2];
-    float ax[2], ay[2], az[2], ph[2];
-    int id[2];
+    float x[KMAX], y[KMAX], z[KMAX];
+    float ax[KMAX], ay[KMAX], az[KMAX], ph[KMAX];
+    int id[KMAX];
 };
 
 // Sum the S partial results of a target into the lanes of the first copy.
-__device__ __forceinline__ float sum_copies(float v, int lane, int T2, int S) {
+__device__ __forceinline__ float sum_copies(float v, int lane, int T, int S) {
     float r = v;
-    for (int m = 1; m < S; ++m) r += __shfl_sync(0xffffffffu, v, min(lane + m * T2, 31));
+    for (int m = 1; m < S; ++m) r += __shfl_sync(0xffffffffu, v, min(lane + m * T, 31));
     return r;
+}
+
+// Slots per lane for a group of c targets: 3 when that fills more slots.
+__device__ __forceinline__ int slots_for(uint32_t c) {
+    const uint32_t t2 = (c + 1u) >> 1, t3 = (c + 2u) / 3u;
+    const uint32_t s2 = 32u / t2, s3 = 32u / t3;
+    return (2u * s3 > 3u * s2) ? 3 : 2;  // c s3 / 96 > c s2 / 64
 }
 
 // Self pairs.  SELF_MASK: skip the self pair inside the p-p loop (needed when
@@ -217,21 +225,10 @@ struct Fp32Rings {
                                                 uint32_t node, float4 m, float4 box, float4 clo,
                                                 uint32_t) {
         const float4 a = A.ca[node];
-#ifdef WALK_EXP_CPASYNC
-        {
-            const unsigned sb = (unsigned)__cvta_generic_to_shared(&L.cb[s]);
-            const unsigned sc2 = (unsigned)__cvta_generic_to_shared(&L.cc[s]);
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(sb), "l"(A.cb + node));
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(sc2), "l"(A.cc + node));
-        }
-        L.ca[s] = make_float4((m.x - box.x) + (a.x - clo.x), (m.y - box.y) + (a.y - clo.y),
-                              (m.z - box.z) + (a.z - clo.z), a.w);
-#else
         L.ca[s] = make_float4((m.x - box.x) + (a.x - clo.x), (m.y - box.y) + (a.y - clo.y),
                               (m.z - box.z) + (a.z - clo.z), a.w);
         L.cb[s] = A.cb[node];
         L.cc[s] = A.cc[node];
-#endif
         L.cid[s] = (int)node;
     }
     __device__ __forceinline__ void append_particle(const WalkArgs &A, WarpLists &L, uint32_t s,
@@ -245,23 +242,24 @@ struct Fp32Rings {
 
 template <int SELF>
 struct ForwardPolicy : Fp32Rings {
-    int T2, S, cp, tl, j0;
+    int K, T, S, cp, tl, j0;
     Targets t;
-    float self[2];
+    float self[KMAX];
     float eps2;
 
     __device__ __forceinline__ void begin(const WalkArgs &A, WarpTargets *, uint32_t, uint32_t gf,
                                           uint32_t gc, float4 box, float4 clo, int lane) {
         eps2 = A.eps2;
-        T2 = (int)((gc + 1u) >> 1);
-        S = 32 / T2;
-        cp = lane / T2;
-        tl = lane - cp * T2;
+        K = slots_for(gc);
+        T = (int)((gc + (uint32_t)K - 1u) / (uint32_t)K);
+        S = 32 / T;
+        cp = lane / T;
+        tl = lane - cp * T;
         const bool active = cp < S;
 #pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            const uint32_t li = (uint32_t)(tl + k * T2);
-            const bool v = active && li < gc;
+        for (int k = 0; k < KMAX; ++k) {
+            const uint32_t li = (uint32_t)(tl + k * T);
+            const bool v = active && k < K && li < gc;
             const int64_t i = gf + (v ? li : 0u);
             const float4 h = A.body_hi[i], l = A.body_lo[i];
             t.x[k] = (h.x - box.x) + (l.x - clo.x);
@@ -277,58 +275,61 @@ struct ForwardPolicy : Fp32Rings {
     // entries [hb, hb + cnt) of the p-c ring (hb a multiple of 32, cnt <= 32)
     __device__ __forceinline__ void flush_pc(const WarpLists &L, int hb, int cnt) {
         const int end = hb + cnt;
-#ifdef WALK_EXP_UNROLL2
-        int j = hb + j0;
+        if (K == 2) {
 #pragma unroll 1
-        for (; j + S < end; j += 2 * S) {
-            const float4 a = L.ca[j], b = L.cb[j], c = L.cc[j];
-            const float4 a1 = L.ca[j + S], b1 = L.cb[j + S], c1 = L.cc[j + S];
+            for (int j = hb + j0; j < end; j += S) {
+                const float4 a = L.ca[j], b = L.cb[j], c = L.cc[j];
 #pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                pc_one(a, b, c, t.x[k], t.y[k], t.z[k], eps2, t.ax[k], t.ay[k], t.az[k], t.ph[k]);
-                pc_one(a1, b1, c1, t.x[k], t.y[k], t.z[k], eps2, t.ax[k], t.ay[k], t.az[k], t.ph[k]);
+                for (int k = 0; k < 2; ++k)
+                    pc_one(a, b, c, t.x[k], t.y[k], t.z[k], eps2, t.ax[k], t.ay[k], t.az[k], t.ph[k]);
+            }
+        } else {
+#pragma unroll 1
+            for (int j = hb + j0; j < end; j += S) {
+                const float4 a = L.ca[j], b = L.cb[j], c = L.cc[j];
+#pragma unroll
+                for (int k = 0; k < 3; ++k)
+                    pc_one(a, b, c, t.x[k], t.y[k], t.z[k], eps2, t.ax[k], t.ay[k], t.az[k], t.ph[k]);
             }
         }
-        if (j < end) {
-            const float4 a = L.ca[j], b = L.cb[j], c = L.cc[j];
-#pragma unroll
-            for (int k = 0; k < 2; ++k)
-                pc_one(a, b, c, t.x[k], t.y[k], t.z[k], eps2, t.ax[k], t.ay[k], t.az[k], t.ph[k]);
-        }
-#else
-#pragma unroll 1
-        for (int j = hb + j0; j < end; j += S) {
-            const float4 a = L.ca[j], b = L.cb[j], c = L.cc[j];
-#pragma unroll
-            for (int k = 0; k < 2; ++k)
-                pc_one(a, b, c, t.x[k], t.y[k], t.z[k], eps2, t.ax[k], t.ay[k], t.az[k], t.ph[k]);
-        }
-#endif
     }
 
     __device__ __forceinline__ void flush_pp(const WarpLists &L, int hb, int cnt) {
         const int end = hb + cnt;
+        if (K == 2) {
 #pragma unroll 1
-        for (int j = hb + j0; j < end; j += S) {
-            const float4 p = L.pp[j];
-            const int sid = L.pid[j];
+            for (int j = hb + j0; j < end; j += S) {
+                const float4 p = L.pp[j];
+                const int sid = L.pid[j];
 #pragma unroll
-            for (int k = 0; k < 2; ++k)
-                pp_one<SELF == SELF_MASK>(p, sid, t.id[k], t.x[k], t.y[k], t.z[k], eps2, t.ax[k],
-                                          t.ay[k], t.az[k], t.ph[k]);
+                for (int k = 0; k < 2; ++k)
+                    pp_one<SELF == SELF_MASK>(p, sid, t.id[k], t.x[k], t.y[k], t.z[k], eps2, t.ax[k],
+                                              t.ay[k], t.az[k], t.ph[k]);
+            }
+        } else {
+#pragma unroll 1
+            for (int j = hb + j0; j < end; j += S) {
+                const float4 p = L.pp[j];
+                const int sid = L.pid[j];
+#pragma unroll
+                for (int k = 0; k < 3; ++k)
+                    pp_one<SELF == SELF_MASK>(p, sid, t.id[k], t.x[k], t.y[k], t.z[k], eps2, t.ax[k],
+                                              t.ay[k], t.az[k], t.ph[k]);
+            }
         }
     }
 
     __device__ __forceinline__ void finish(const WalkArgs &A, uint32_t gf, uint32_t gc, int lane) {
 #pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            const float ax = A.G * sum_copies(t.ax[k], lane, T2, S);
-            const float ay = A.G * sum_copies(t.ay[k], lane, T2, S);
-            const float az = A.G * sum_copies(t.az[k], lane, T2, S);
-            float phs = sum_copies(t.ph[k], lane, T2, S);
+        for (int k = 0; k < KMAX; ++k) {
+            if (k >= K) break;
+            const float ax = A.G * sum_copies(t.ax[k], lane, T, S);
+            const float ay = A.G * sum_copies(t.ay[k], lane, T, S);
+            const float az = A.G * sum_copies(t.az[k], lane, T, S);
+            float phs = sum_copies(t.ph[k], lane, T, S);
             if (SELF == SELF_SUB) phs = phs + self[k] * rsqrtf(eps2);  // remove the self pair
             const float ph = A.G * phs;
-            const uint32_t li = (uint32_t)(tl + k * T2);
+            const uint32_t li = (uint32_t)(tl + k * T);
             if (cp == 0 && li < gc) {
                 const int64_t i = gf + li;
                 if (A.accumulate) {
@@ -774,9 +775,7 @@ struct __align__(16) WarpLists64 {
     double q[6][RING];  // xx yy zz xy xz yz
     double px[RING], py[RING], pz[RING], pm[RING];
     int pid[RING];
-#ifdef WALK_EXP_DIET
     float4 gbox, ghalf, glo;
-#endif
 };
 
 __device__ __forceinline__ void pc_one64(double rx, double ry, double rz, double M, double qxx,
@@ -952,7 +951,6 @@ __device__ __forceinline__ void walk_group(const WalkArgs &A, LT &L, WarpTargets
                                            uint32_t g, uint32_t *fa, uint32_t *fb, int lane,
                                            uint32_t lt) {
     const uint32_t gf = A.gfirst[g], gc = A.gcount[g];
-#ifdef WALK_EXP_DIET
     {
         const float4 box = A.gbox[g], clo = A.glo[g];
         if (lane == 0) {
@@ -963,10 +961,6 @@ __device__ __forceinline__ void walk_group(const WalkArgs &A, LT &L, WarpTargets
         pol.begin(A, tgt, g, gf, gc, box, clo, lane);
     }
     __syncwarp();
-#else
-    const float4 box = A.gbox[g], half = A.ghalf[g], clo = A.glo[g];
-    pol.begin(A, tgt, g, gf, gc, box, clo, lane);
-#endif
 
     // pc_tail and pp_tail count every entry ever appended: the list lengths
     uint32_t pc_head = 0, pc_tail = 0, pp_head = 0, pp_tail = 0;
@@ -985,9 +979,7 @@ __device__ __forceinline__ void walk_group(const WalkArgs &A, LT &L, WarpTargets
             const uint32_t node = valid ? cur[idx] : 0u;
             const float4 m = A.mac[node];
             const uint2 tp = A.topo[node];
-#ifdef WALK_EXP_DIET
             const float4 box = lds_f4(&L.gbox), half = lds_f4(&L.ghalf), clo = lds_f4(&L.glo);
-#endif
             const bool open = mac_open(m, box, half);  // Sec. I.A opening test
             const bool leaf = (tp.y & LEAF_FLAG) != 0u;
             const bool accept = valid && !open;
@@ -1036,9 +1028,7 @@ __device__ __forceinline__ void walk_group(const WalkArgs &A, LT &L, WarpTargets
                 }
                 const uint32_t sfirst = __shfl_sync(0xffffffffu, tp.x, src);
                 const uint32_t soff = __shfl_sync(0xffffffffu, loff, src);
-#ifdef WALK_EXP_DIET
                 const float4 box = lds_f4(&L.gbox), clo = lds_f4(&L.glo);
-#endif
                 if (k < ltot)
                     pol.append_particle(A, L, (pp_tail + lane) & (RING - 1), sfirst + (k - soff),
                                         box, clo, g);
@@ -1051,9 +1041,6 @@ __device__ __forceinline__ void walk_group(const WalkArgs &A, LT &L, WarpTargets
                     __syncwarp();
                 }
             }
-#ifdef WALK_EXP_CPASYNC
-            asm volatile("cp.async.wait_all;" ::: "memory");
-#endif
             __syncwarp();
             while (pc_tail - pc_head >= 32u) {
                 do_flush_pc(pol, L, (int)(pc_head & (RING - 1)), 32, lane);
@@ -1085,13 +1072,8 @@ __device__ __forceinline__ void walk_group(const WalkArgs &A, LT &L, WarpTargets
     __syncwarp();
 }
 
-#ifdef WALK_EXP_MINB
-#define WALK_BOUNDS __launch_bounds__(WALK_WARPS * 32, WALK_EXP_MINB)
-#else
-#define WALK_BOUNDS __launch_bounds__(WALK_WARPS * 32)
-#endif
 template <int SELF>
-__global__ void WALK_BOUNDS k_walk(const WalkArgs A) {
+__global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(const WalkArgs A) {
     __shared__ WarpLists lists[WALK_WARPS];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
