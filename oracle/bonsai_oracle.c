@@ -22,7 +22,8 @@
  *       3. sort by key (Table 2 "Sorting SFC"),
  *       4. octree: octants split until a node holds at most 16 particles
  *          (Sec. I.A, "critical value ... 16"), children in key order,
- *       5. walk groups (nodes of <= 64 particles whose parent has more),
+ *       5. walk groups (runs of consecutive sibling cells of <= 64
+ *          particles each, at most 64 in all, under a cell with more),
  *       6. multipoles: mass, centre of mass, 3x3 symmetric quadrupole
  *          (Sec. VI.A below Eq. 2) by a parallel-axis upward pass,
  *       7. multipole acceptance criterion parameterised by theta (Sec. I.A),
@@ -33,8 +34,10 @@
  * Readings where the paper is silent (each one also listed in the design
  * notes): 21 bits per axis (63-bit key); Skilling's transpose form of the
  * Hilbert curve with axis 0 most significant in each 3-bit digit; leaf rule
- * count <= 16; group = node with <= 64 particles whose parent has > 64
- * (a max-depth leaf with > 64 particles is cut into runs of 64); MAC
+ * count <= 16; group = a run of consecutive children (each with <= 64
+ * particles) of a node with > 64, at most 64 particles in all, formed
+ * greedily in key order (a max-depth leaf with > 64 particles is cut into
+ * runs of 64; the root is the one group when it has <= 64); MAC
  * "open if d^2 < r_open^2" with r_open = l/theta + |com - centre| and d the
  * distance from the cell's com to the group's box, evaluated in FP32 on
  * FP32-rounded inputs; Plummer softening in every power of |r| in Eq. 1-2;
@@ -230,34 +233,65 @@ static int orc_group_cmp(const void *a, const void *b) {
     return (p[0] < r[0]) ? -1 : (p[0] > r[0]);
 }
 
-/* 5. Groups: a node with <= ncrit particles whose parent has more (the root
- *    if it has <= ncrit); a max-depth leaf with more than ncrit particles is
- *    cut into consecutive runs of ncrit.  Each group's FP64 bounding box
- *    gives its centre and half-size.                                       */
+/* 5. Groups.  Under every node with more than ncrit particles, its children
+ *    that hold at most ncrit particles are taken in key order and gathered
+ *    into runs: a child joins the current run while the run's total stays
+ *    at most ncrit, otherwise it starts the next run; a child with more
+ *    than ncrit particles ends the run (its own children form groups one
+ *    level down).  Each run is one group: a contiguous range of the sorted
+ *    particles.  The root is the single group if it has at most ncrit; a
+ *    max-depth leaf with more than ncrit particles is cut into consecutive
+ *    runs of ncrit.  Each group's FP64 bounding box gives its centre and
+ *    half-size.                                                            */
+static int orc_push_group(uint32_t **g, int64_t *cap, int64_t *ng, uint32_t first, uint32_t count) {
+    if (*ng == *cap) {
+        *cap *= 2;
+        uint32_t *p = (uint32_t *)realloc(*g, (size_t)*cap * 2 * sizeof(uint32_t));
+        if (!p) return -1;
+        *g = p;
+    }
+    (*g)[2 * *ng] = first;
+    (*g)[2 * *ng + 1] = count;
+    ++*ng;
+    return 0;
+}
+
 static int orc_make_groups(orc_tree *t) {
     int64_t cap = 1024, ng = 0;
     uint32_t *g = (uint32_t *)malloc((size_t)cap * 2 * sizeof(uint32_t));
     if (!g) return -1;
     uint32_t ncrit = (uint32_t)t->ncrit;
-    for (int64_t i = 0; i < t->nnodes; ++i) {
+    int rc = 0;
+    if (t->count[0] <= ncrit) rc = orc_push_group(&g, &cap, &ng, t->first[0], t->count[0]);
+    for (int64_t i = 0; i < t->nnodes && rc == 0; ++i) {
         uint32_t c = t->count[i];
-        int is_leaf = (t->nchild[i] == 0);
-        int parent_big = (i == 0) || (t->count[t->parent[i]] > ncrit);
-        if (!parent_big) continue;
-        if (c <= ncrit || is_leaf) {
-            for (uint32_t s = 0; s < c; s += ncrit) {
-                if (ng == cap) {
-                    cap *= 2;
-                    uint32_t *p = (uint32_t *)realloc(g, (size_t)cap * 2 * sizeof(uint32_t));
-                    if (!p) { free(g); return -1; }
-                    g = p;
-                }
-                g[2 * ng] = t->first[i] + s;
-                g[2 * ng + 1] = (c - s < ncrit) ? (c - s) : ncrit;
-                ++ng;
+        if (c <= ncrit) continue;
+        if (t->nchild[i] == 0) {  /* a max-depth leaf: runs of ncrit */
+            for (uint32_t s = 0; s < c && rc == 0; s += ncrit)
+                rc = orc_push_group(&g, &cap, &ng, t->first[i] + s, (c - s < ncrit) ? (c - s) : ncrit);
+            continue;
+        }
+        uint32_t run_first = 0, run_count = 0;
+        int open = 0;
+        for (uint32_t k = 0; k < t->nchild[i] && rc == 0; ++k) {
+            uint32_t j = t->child[i] + k;
+            if (t->count[j] > ncrit) {          /* a big child ends the run */
+                if (open) rc = orc_push_group(&g, &cap, &ng, run_first, run_count);
+                open = 0;
+                continue;
+            }
+            if (open && run_count + t->count[j] <= ncrit) {
+                run_count += t->count[j];
+            } else {
+                if (open) rc = orc_push_group(&g, &cap, &ng, run_first, run_count);
+                run_first = t->first[j];
+                run_count = t->count[j];
+                open = 1;
             }
         }
+        if (open && rc == 0) rc = orc_push_group(&g, &cap, &ng, run_first, run_count);
     }
+    if (rc) { free(g); return -1; }
     qsort(g, (size_t)ng, 2 * sizeof(uint32_t), orc_group_cmp);
     t->ngroups = ng;
     t->gfirst = (uint32_t *)malloc((size_t)ng * sizeof(uint32_t));

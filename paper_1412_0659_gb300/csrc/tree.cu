@@ -204,29 +204,17 @@ __global__ void __launch_bounds__(128) k_multipoles(
     Q[5 * nn + i] = q5;
 }
 
-// ---- groups: a node with <= NCRIT particles whose parent has more (the
-// root if it has <= NCRIT); a leaf above NCRIT (max depth) is cut into runs
-// of NCRIT.  Each group start is flagged in a per-particle array, a scan
+// ---- groups: runs of consecutive sibling cells of at most NCRIT particles
+// in all.  Each group start is flagged in a per-particle array, a scan
 // numbers them in particle order.
+// Group starts (flags at the first particle of each group).  A thread per
+// node; only nodes with more than NCRIT particles act.  Their children of at
+// most NCRIT particles are taken in key order and gathered greedily into runs
+// of at most NCRIT particles, a child with more than NCRIT ending the run
+// (its own children are grouped by its thread): each run is one group.  The
+// root is the one group when it holds at most NCRIT; a max-depth leaf with
+// more than NCRIT is cut into runs of NCRIT.
 __global__ void __launch_bounds__(256) k_group_flags(const uint32_t *__restrict__ first,
-                                                     const uint32_t *__restrict__ count,
-                                                     const uint32_t *__restrict__ nchild,
-                                                     const uint32_t *__restrict__ parent,
-                                                     uint32_t *__restrict__ flag, int64_t nn) {
-    int64_t i = blockIdx.x * 256ll + threadIdx.x;
-    if (i >= nn) return;
-    uint32_t c = count[i];
-    bool parent_big = (i == 0) || count[parent[i]] > (uint32_t)NCRIT;
-    if (!parent_big) return;
-    if (c <= (uint32_t)NCRIT || nchild[i] == 0) {
-        uint32_t f = first[i];
-        for (uint32_t s = 0; s < c; s += NCRIT) flag[f + s] = 1u;
-    }
-}
-
-#ifdef GROUP_EXP_MERGE
-// experiment: consecutive sibling groups merged greedily up to NCRIT
-__global__ void __launch_bounds__(256) k_group_flags_merge(const uint32_t *__restrict__ first,
                                                            const uint32_t *__restrict__ count,
                                                            const uint32_t *__restrict__ nchild,
                                                            const uint32_t *__restrict__ child,
@@ -259,7 +247,6 @@ __global__ void __launch_bounds__(256) k_group_flags_merge(const uint32_t *__res
         }
     }
 }
-#endif
 
 __global__ void __launch_bounds__(256) k_group_write(const uint32_t *__restrict__ flag,
                                                      const uint32_t *__restrict__ gid, int64_t n,
@@ -491,15 +478,9 @@ int build_octree(bonsai_ctx *c) {
 int build_groups(bonsai_ctx *c) {
     const int64_t n = c->n, nn = c->n_nodes;
     BGB_CUDA(cudaMemsetAsync(c->grp_flag.p, 0, (n + 1) * sizeof(uint32_t), c->stream));
-#ifdef GROUP_EXP_MERGE
-    k_group_flags_merge<<<grid_for(nn, 256), 256, 0, c->stream>>>(c->nd_first.p, c->nd_count.p,
-                                                                   c->nd_nchild.p, c->nd_child.p,
-                                                                   c->grp_flag.p, nn);
-#else
     k_group_flags<<<grid_for(nn, 256), 256, 0, c->stream>>>(c->nd_first.p, c->nd_count.p,
-                                                             c->nd_nchild.p, c->nd_parent.p,
+                                                             c->nd_nchild.p, c->nd_child.p,
                                                              c->grp_flag.p, nn);
-#endif
     c->launches += 1;
     uint32_t *gid = c->grp_flag.p + (n + 1);
     exclusive_scan_u32(c, c->grp_flag.p, gid, n, &c->dsc->n_groups);

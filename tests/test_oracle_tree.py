@@ -108,21 +108,46 @@ def test_groups_tile_and_follow_the_rule(case):
     assert np.array_equal(g["first"][1:], (g["first"] + g["count"])[:-1])
     assert int(g["first"][-1] + g["count"][-1]) == n
     assert np.all((g["count"] >= 1) & (g["count"] <= 64))
-    # each group is a node with <= 64 particles whose parent has > 64, or a
-    # run of 64 inside a max-depth leaf
-    parent = np.zeros(t.nnodes, np.int64)
-    for i in range(t.nnodes):
-        for k in range(nd["child"][i], nd["child"][i] + nd["nchild"][i]):
-            parent[k] = i
-    by_range = {(int(nd["first"][i]), int(nd["count"][i])): i for i in range(t.nnodes)}
+    # each group is the root (n <= 64), a run of 64 inside a max-depth leaf,
+    # or a run of consecutive children of one node with > 64 particles, each
+    # child holding <= 64 and the run <= 64 in all; runs are greedy: a run
+    # ends at a big child, at the last child, or where the next child would
+    # push it past 64
+    first, count = nd["first"].astype(np.int64), nd["count"].astype(np.int64)
+    child, nchild = nd["child"].astype(np.int64), nd["nchild"].astype(np.int64)
+    owner = {}                               # first particle of a small child of a big node
+    for i in range(t.nnodes):              # -> (that node, the child's index)
+        if count[i] > 64:
+            for k in range(nchild[i]):
+                if count[child[i] + k] <= 64:
+                    owner[int(first[child[i] + k])] = (i, k)
     for f, c in zip(g["first"].tolist(), g["count"].tolist()):
-        if (f, c) in by_range:
-            i = by_range[(f, c)]
-            assert i == 0 or nd["count"][parent[i]] > 64
+        if c == n and f == 0 and n <= 64:
+            continue                          # the root is the one group
+        if f in owner:
+            p, k0 = owner[f]
+            ks, tot, k = [], 0, k0
+            while tot < c:                    # the children that make up the run
+                ck = count[child[p] + k]
+                assert ck <= 64 and first[child[p] + k] == f + tot
+                tot += ck
+                ks.append(k)
+                k += 1
+            assert tot == c <= 64
+            # greedy: it could not have joined the previous run, and the next
+            # child could not join it
+            if k0 > 0:
+                prev = child[p] + k0 - 1
+                if count[prev] <= 64:
+                    j = g["first"].tolist().index(f) - 1
+                    assert g["count"][j] + count[child[p] + k0] > 64
+            if k < nchild[p]:
+                assert count[child[p] + k] > 64 or tot + count[child[p] + k] > 64
         else:
-            host = [i for i in range(t.nnodes) if nd["nchild"][i] == 0 and nd["first"][i] <= f
-                    and f + c <= nd["first"][i] + nd["count"][i]]
-            assert host and nd["level"][host[0]] == 21 and nd["count"][host[0]] > 64
+            host = [i for i in range(t.nnodes) if nchild[i] == 0 and first[i] <= f
+                    and f + c <= first[i] + count[i]]
+            assert host and nd["level"][host[0]] == 21 and count[host[0]] > 64
+            assert (f - first[host[0]]) % 64 == 0
     # the FP64 box contains every member
     spos, _ = t.sorted_state()
     for k in range(t.ngroups):
