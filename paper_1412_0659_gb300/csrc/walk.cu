@@ -394,8 +394,10 @@ struct CellDup {
 // u = 1/s of one cell and two targets (the first, latency-bound part of the
 // p-c VJP, taken for a whole chunk before the rest).
 __device__ __forceinline__ f32x2 pc_inv_s(const CellDup &C, f32x2 nx, f32x2 ny, f32x2 nz,
-                                          f32x2 eps2) {
-    const f32x2 rx = add2(C.x, nx), ry = add2(C.y, ny), rz = add2(C.z, nz);
+                                          f32x2 eps2, f32x2 &rx, f32x2 &ry, f32x2 &rz) {
+    rx = add2(C.x, nx);
+    ry = add2(C.y, ny);
+    rz = add2(C.z, nz);
     f32x2 s2 = fma2(rx, rx, eps2);
     s2 = fma2(ry, ry, s2);
     s2 = fma2(rz, rz, s2);
@@ -410,10 +412,9 @@ __device__ __forceinline__ void pc_vjp2(const CellDup &C, const TargetPair &T, f
                                         f32x2 &u3, f32x2 &u5, f32x2 &lr, f32x2 &vx, f32x2 &vy,
                                         f32x2 &vz, f32x2 &rx, f32x2 &ry, f32x2 &rz) {
     const f32x2 k_m25 = dup2(-2.5f), k_175 = dup2(17.5f), k_m5 = dup2(-5.0f);
-    rx = add2(C.x, T.nx);
-    ry = add2(C.y, T.ny);
-    rz = add2(C.z, T.nz);
-    const f32x2 u = GIVEN_U ? ug : pc_inv_s(C, T.nx, T.ny, T.nz, eps2);
+    // with GIVEN_U the caller passes u and r = com - x (rx, ry, rz) of the
+    // first phase; otherwise both are computed here
+    const f32x2 u = GIVEN_U ? ug : pc_inv_s(C, T.nx, T.ny, T.nz, eps2, rx, ry, rz);
     const f32x2 w = mul2(u, u);
     u3 = mul2(u, w);
     u5 = mul2(u3, w);
@@ -446,8 +447,11 @@ __device__ __forceinline__ void pc_vjp2(const CellDup &C, const TargetPair &T, f
 //   g_r = m u^3 (lambda + (mu - 3 w lr) r),  gm = lr u^3 - mu u;
 // zero for the self pair (u is set to 0, which also avoids r = 0 at eps = 0).
 __device__ __forceinline__ f32x2 pp_inv_s(f32x2 sx, f32x2 sy, f32x2 sz, int sid, f32x2 nx,
-                                          f32x2 ny, f32x2 nz, int2 id, f32x2 eps2) {
-    const f32x2 rx = add2(sx, nx), ry = add2(sy, ny), rz = add2(sz, nz);
+                                          f32x2 ny, f32x2 nz, int2 id, f32x2 eps2, f32x2 &rx,
+                                          f32x2 &ry, f32x2 &rz) {
+    rx = add2(sx, nx);
+    ry = add2(sy, ny);
+    rz = add2(sz, nz);
     f32x2 s2 = fma2(rx, rx, eps2);
     s2 = fma2(ry, ry, s2);
     s2 = fma2(rz, rz, s2);
@@ -458,10 +462,11 @@ __device__ __forceinline__ f32x2 pp_inv_s(f32x2 sx, f32x2 sy, f32x2 sz, int sid,
 
 template <bool GIVEN_U>
 __device__ __forceinline__ void pp_vjp2(f32x2 sx, f32x2 sy, f32x2 sz, f32x2 sm, int sid,
-                                        const TargetPair &T, f32x2 eps2, f32x2 ug, f32x2 &gx,
-                                        f32x2 &gy, f32x2 &gz, f32x2 &gm) {
-    const f32x2 rx = add2(sx, T.nx), ry = add2(sy, T.ny), rz = add2(sz, T.nz);
-    const f32x2 u = GIVEN_U ? ug : pp_inv_s(sx, sy, sz, sid, T.nx, T.ny, T.nz, T.id, eps2);
+                                        const TargetPair &T, f32x2 eps2, f32x2 ug, f32x2 rx,
+                                        f32x2 ry, f32x2 rz, f32x2 &gx, f32x2 &gy, f32x2 &gz,
+                                        f32x2 &gm) {
+    // with GIVEN_U the caller passes u and r of the first phase
+    const f32x2 u = GIVEN_U ? ug : pp_inv_s(sx, sy, sz, sid, T.nx, T.ny, T.nz, T.id, eps2, rx, ry, rz);
     const f32x2 w = mul2(u, u);
     const f32x2 u3 = mul2(u, w);
     const f32x2 lr = fma2(T.lx, rx, fma2(T.ly, ry, mul2(T.lz, rz)));
@@ -555,23 +560,37 @@ struct AdjointPolicy : Fp32Rings {
         row[2] = gz;
     }
 
-    // add the chunk's target gradients (all rows) to tacc: column c is
-    // component (c % 6) / 2 of target t0 + 2 (c / 6) + (c & 1); a chunk of
-    // NP target pairs fills the first 6 NP columns
+    // add the chunk's target gradients (all rows) to tacc.  A row holds, as
+    // packed pairs, column c = 3 tp + component for target pair tp (its two
+    // halves are targets t0 + 2 tp and t0 + 2 tp + 1); a chunk of NP pairs
+    // fills the first 3 NP columns.  Lane c of each half-warp sums column c
+    // over 16 rows with packed adds (half h takes rows 16 h .. 16 h + 15, so
+    // each half-warp reads 12 consecutive pairs of one row: no bank
+    // conflict), and one 64-bit shuffle adds the two halves.
     template <int NP>
     __device__ __forceinline__ void reduce_chunk(int t0, int lane) {
         __syncwarp();
-        if (lane < 6 * NP) {
-            float a[8];  // eight short chains
+        const int h = lane >> 4, c = lane & 15;
+        f32x2 s = 0ull;
+        if (c < 3 * NP) {
+            const f32x2 *col = reinterpret_cast<const f32x2 *>(W->red) + (16 * h) * (ADJ_ROW / 2) + c;
+            f32x2 a[4];  // four short chains
 #pragma unroll
-            for (int k = 0; k < 8; ++k) a[k] = W->red[k * ADJ_ROW + lane];
+            for (int k = 0; k < 4; ++k) a[k] = col[k * (ADJ_ROW / 2)];
 #pragma unroll
-            for (int r = 8; r < 32; r += 8)
+            for (int r = 4; r < 16; r += 4)
 #pragma unroll
-                for (int k = 0; k < 8; ++k) a[k] += W->red[(r + k) * ADJ_ROW + lane];
-            const float s = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
-            const int t = t0 + 2 * (lane / 6) + (lane & 1);
-            if (t < gc) W->tacc[3 * t + (lane % 6) / 2] += s;
+                for (int k = 0; k < 4; ++k) a[k] = add2(a[k], col[(r + k) * (ADJ_ROW / 2)]);
+            s = add2(add2(a[0], a[1]), add2(a[2], a[3]));
+        }
+        s = add2(s, __shfl_down_sync(0xffffffffu, s, 16));
+        if (h == 0 && c < 3 * NP) {
+            float lo, hi;
+            u2(s, lo, hi);
+            const int tp = c / 3, comp = c - 3 * tp;
+            const int t = t0 + 2 * tp;
+            if (t < gc) W->tacc[3 * t + comp] += lo;
+            if (t + 1 < gc) W->tacc[3 * (t + 1) + comp] += hi;
         }
         __syncwarp();
     }
@@ -587,9 +606,10 @@ struct AdjointPolicy : Fp32Rings {
     // Target pair tp of the chunk at t0 into the cell adjoint and the row.
     template <bool GIVEN_U>
     __device__ __forceinline__ void pc_pair(const CellDup &C, f32x2 e2, int t0, int tp, int lane,
-                                            PcAcc &S, f32x2 ug = 0ull) {
+                                            PcAcc &S, f32x2 ug = 0ull, f32x2 rx = 0ull,
+                                            f32x2 ry = 0ull, f32x2 rz = 0ull) {
         const TargetPair T2 = load_targets(T, (t0 >> 1) + tp);
-        f32x2 gx, gy, gz, gM, u3, u5, lr, vx, vy, vz, rx, ry, rz;
+        f32x2 gx, gy, gz, gM, u3, u5, lr, vx, vy, vz;
         pc_vjp2<GIVEN_U>(C, T2, e2, ug, gx, gy, gz, gM, u3, u5, lr, vx, vy, vz, rx, ry, rz);
         S.ax = add2(S.ax, gx);
         S.ay = add2(S.ay, gy);
@@ -630,15 +650,16 @@ struct AdjointPolicy : Fp32Rings {
         for (; t0 + ADJ_CHUNK <= gc; t0 += ADJ_CHUNK) {
             // the chunk's four reciprocal distances first: their MUFU
             // latencies overlap instead of heading four dependent chains
-            f32x2 uu[ADJ_CHUNK / 2];
+            f32x2 uu[ADJ_CHUNK / 2], rr[ADJ_CHUNK / 2][3];
 #pragma unroll
             for (int tp = 0; tp < ADJ_CHUNK / 2; ++tp) {
                 const int p = (t0 >> 1) + tp;
                 const ulonglong2 a = lds2(T->nxy[p]), b = lds2(T->nzi[p]);
-                uu[tp] = pc_inv_s(C, a.x, a.y, b.x, e2);
+                uu[tp] = pc_inv_s(C, a.x, a.y, b.x, e2, rr[tp][0], rr[tp][1], rr[tp][2]);
             }
 #pragma unroll
-            for (int tp = 0; tp < ADJ_CHUNK / 2; ++tp) pc_pair<true>(C, e2, t0, tp, lane, S, uu[tp]);
+            for (int tp = 0; tp < ADJ_CHUNK / 2; ++tp)
+                pc_pair<true>(C, e2, t0, tp, lane, S, uu[tp], rr[tp][0], rr[tp][1], rr[tp][2]);
             reduce_chunk<ADJ_CHUNK / 2>(t0, lane);
         }
         const int np = (gc - t0 + 1) >> 1;  // one code copy for the ragged tail
@@ -675,10 +696,11 @@ struct AdjointPolicy : Fp32Rings {
     template <bool GIVEN_U>
     __device__ __forceinline__ void pp_pair(f32x2 sx, f32x2 sy, f32x2 sz, f32x2 sm, int sid,
                                             f32x2 e2, int t0, int tp, int lane, f32x2 &ax,
-                                            f32x2 &ay, f32x2 &az, f32x2 &am, f32x2 ug = 0ull) {
+                                            f32x2 &ay, f32x2 &az, f32x2 &am, f32x2 ug = 0ull,
+                                            f32x2 rx = 0ull, f32x2 ry = 0ull, f32x2 rz = 0ull) {
         const TargetPair T2 = load_targets(T, (t0 >> 1) + tp);
         f32x2 gx, gy, gz, gm;
-        pp_vjp2<GIVEN_U>(sx, sy, sz, sm, sid, T2, e2, ug, gx, gy, gz, gm);
+        pp_vjp2<GIVEN_U>(sx, sy, sz, sm, sid, T2, e2, ug, rx, ry, rz, gx, gy, gz, gm);
         ax = add2(ax, gx);
         ay = add2(ay, gy);
         az = add2(az, gz);
@@ -698,7 +720,7 @@ struct AdjointPolicy : Fp32Rings {
         f32x2 ax = 0ull, ay = 0ull, az = 0ull, am = 0ull;
         int t0 = 0;
         for (; t0 + ADJ_CHUNK <= gc; t0 += ADJ_CHUNK) {
-            f32x2 uu[ADJ_CHUNK / 2];  // reciprocal distances first, as for p-c
+            f32x2 uu[ADJ_CHUNK / 2], rr[ADJ_CHUNK / 2][3];  // reciprocal distances first, as for p-c
 #pragma unroll
             for (int tp = 0; tp < ADJ_CHUNK / 2; ++tp) {
                 const int p = (t0 >> 1) + tp;
@@ -706,11 +728,13 @@ struct AdjointPolicy : Fp32Rings {
                 float i0, i1;
                 u2(b.y, i0, i1);
                 uu[tp] = pp_inv_s(sx, sy, sz, sid, a.x, a.y, b.x,
-                                  make_int2(__float_as_int(i0), __float_as_int(i1)), e2);
+                                  make_int2(__float_as_int(i0), __float_as_int(i1)), e2, rr[tp][0],
+                                  rr[tp][1], rr[tp][2]);
             }
 #pragma unroll
             for (int tp = 0; tp < ADJ_CHUNK / 2; ++tp)
-                pp_pair<true>(sx, sy, sz, sm, sid, e2, t0, tp, lane, ax, ay, az, am, uu[tp]);
+                pp_pair<true>(sx, sy, sz, sm, sid, e2, t0, tp, lane, ax, ay, az, am, uu[tp], rr[tp][0],
+                              rr[tp][1], rr[tp][2]);
             reduce_chunk<ADJ_CHUNK / 2>(t0, lane);
         }
         const int np = (gc - t0 + 1) >> 1;
