@@ -45,8 +45,8 @@ if ROOT not in sys.path:
 # DRAM bytes (read + written) of one walk/force launch, from a one-pass ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum) of the benchmark
 # command, valid only for the walk source it was taken on (checked by hash).
-WALK_TRAFFIC = {"walk_cu_sha256": "3e5a979745743a33227d3bf6f0db8a598f06b9e36667dfd6b05ca76c81badd6c",
-                "bytes": {"milky-way-2^23": 708.60e6 + 276.45e6}}
+WALK_TRAFFIC = {"walk_cu_sha256": "aa770e6bc2b82ea78e672bc1213a34f8bed451ae4707c43099bff61da3b10f31",
+                "bytes": {"milky-way-2^23": 946.907904e6 + 458.898944e6}}
 
 METRIC = "tree-force Tflop/s (23 flops/p-p + 65 flops/p-c, Sec. VI.A) per full KDK step, theta=0.4"
 UNIT = "Tflop/s"
