@@ -15,7 +15,8 @@ module states, step by step in plain numpy, what the GPU generator computes:
    masses by the trapezoid rule in ln r; rho0_c sets each total mass.
 2. The spherically averaged potential of all three components,
    Psi(r) = G M(<r) / r + G int_r (dM/dr') d ln r', where the disk enters
-   through the mass of a thin exponential disk inside radius r.
+   through its mass inside the sphere of radius r (the sech^2 layer's
+   density averaged over each sphere, Simpson in the polar angle).
 3. Each spheroid's isotropic distribution function by Eddington's formula,
    f(E) = 1/(sqrt(8) pi^2) int_Psimin^E d2rho/dPsi2 dPsi / sqrt(E - Psi),
    with d2rho/dPsi2 = (rho'' Psi' - rho' Psi'') / Psi'^3 from the radial
@@ -35,8 +36,8 @@ module states, step by step in plain numpy, what the GPU generator computes:
    R_d), held within [0, v_c^2] (the epicyclic closure fails where sigma_R
    approaches v_c, near the centre, and would make the disk rotate faster
    than circular), in the potential of the spheroids (their enclosed mass)
-   plus the thin exponential disk (Freeman's circular speed with modified
-   Bessel functions).
+   plus the disk's own midplane force (the Hankel integral of the
+   exponential disk with e^{-k|z|} averaged over its sech^2 layer).
 6. Sampling: every particle draws its uniforms from Philox4x32-10 (Salmon,
    Moraes, Dror & Shaw, SC11) with counter (particle index, component,
    call, 0) and key (seed low, seed high); each uniform takes two 32-bit
@@ -219,10 +220,55 @@ def disk_fraction(x):
     return np.where(x < 0.5, s, 1.0 - (1.0 + x) * np.exp(-x))
 
 
-def disk_sph_mass(r, Md, Rd):
-    """Mass of a thin exponential disk inside radius r, and its r-derivative."""
-    x = r / Rd
-    return Md * disk_fraction(x), Md * x * np.exp(-x) / Rd
+SHELL_N = 2048   # Simpson intervals of the disk's spherical shell average
+VC_NK = 4000     # Simpson intervals of the disk's Hankel integral in k
+VC_KMAX = 40.0   # k range, in units of 1 / R_d
+IZ_NT = 4096     # Simpson intervals of the vertical factor in t = z / z0
+IZ_TMAX = 40.0
+
+
+def simpson(y, h, axis=-1):
+    """Composite Simpson rule of samples y (an odd count) with step h."""
+    y = np.moveaxis(np.asarray(y), axis, -1)
+    return h / 3.0 * (y[..., 0] + y[..., -1] + 4.0 * y[..., 1:-1:2].sum(-1) + 2.0 * y[..., 2:-1:2].sum(-1))
+
+
+def disk_sigma0(g: Galaxy):
+    """Central surface density of the truncated disk (total mass M_disk)."""
+    return g.M_disk / (2.0 * math.pi * g.R_d * g.R_d * float(disk_fraction(g.R_max / g.R_d)))
+
+
+def disk_shell_rate(r, g: Galaxy):
+    """dM/dr of the disk, rho = Sigma0 e^{-R/R_d} sech^2(z/z0) / (2 z0) for
+    R <= R_max: 4 pi r^2 times the density averaged over the sphere of
+    radius r, int_0^{pi/2} rho(r cos phi, r sin phi) cos phi dphi, by
+    Simpson's rule on [phi_lo, phi_hi] with phi_hi = asin(min(1, 40 z0 / r))
+    (sech^2 < 1e-34 beyond) and phi_lo = acos(min(1, R_max / r)) (the disk
+    ends at R_max)."""
+    sig0 = disk_sigma0(g)
+    out = np.zeros_like(r)
+    for k, rk in enumerate(r):
+        hi = math.asin(min(1.0, IZ_TMAX * g.z0 / rk))
+        lo = math.acos(min(1.0, g.R_max / rk))
+        if hi <= lo:
+            continue
+        phi = lo + (hi - lo) * np.arange(SHELL_N + 1) / SHELL_N
+        R, z = rk * np.cos(phi), rk * np.sin(phi)
+        rho = sig0 * np.exp(-R / g.R_d) / (2.0 * g.z0) / np.cosh(z / g.z0) ** 2
+        out[k] = 4.0 * math.pi * rk * rk * simpson(rho * np.cos(phi), (hi - lo) / SHELL_N)
+    return out
+
+
+def disk_sph_mass(r, dl, g: Galaxy):
+    """Mass of the disk inside radius r and its r-derivative: the shell rate
+    above, integrated by the trapezoid rule in ln r from the mass of the
+    central density inside the first node."""
+    dM = disk_shell_rate(r, g)
+    F = r * dM
+    M = np.empty_like(r)
+    M[0] = 4.0 / 3.0 * math.pi * r[0] ** 3 * disk_sigma0(g) / (2.0 * g.z0)
+    M[1:] = M[0] + np.cumsum(0.5 * (F[1:] + F[:-1]) * dl)
+    return M, dM
 
 
 def profiles(g: Galaxy):
@@ -235,7 +281,7 @@ def profiles(g: Galaxy):
         rho0 = M / S[-1]
         comp[name] = {"rho": rho0 * s0, "rho1": rho0 * s1, "rho2": rho0 * s2, "M": rho0 * S,
                       "P": S / S[-1]}
-    Md, dMd = disk_sph_mass(r, g.M_disk, g.R_d)
+    Md, dMd = disk_sph_mass(r, dl, g)
     Mt = comp["halo"]["M"] + comp["bulge"]["M"] + Md
     dMt = 4.0 * math.pi * r * r * (comp["halo"]["rho"] + comp["bulge"]["rho"]) + dMd
     seg = 0.5 * (dMt[1:] + dMt[:-1]) * dl
@@ -300,12 +346,41 @@ def speed_cdf(Psi, f):
 # ---------------------------------------------------------------------------
 
 def freeman_vc2(R, G, Md, Rd):
-    """Circular speed squared in the plane of a thin exponential disk."""
+    """Circular speed squared in the plane of a thin exponential disk
+    (Freeman 1970), the thin limit of disk_vc2 (used by the tests)."""
     from scipy import special
     y = R / (2.0 * Rd)
     s0 = Md / (2.0 * math.pi * Rd * Rd)
     return 4.0 * math.pi * G * s0 * Rd * y * y * (
         special.i0(y) * special.k0(y) - special.i1(y) * special.k1(y))
+
+
+def vertical_factor(kz):
+    """I(k z0) = int_0^inf sech^2(t) e^{-k z0 t} dt (the sech^2 layer's
+    weight of e^{-k|z|}; 1 for a thin disk), Simpson on t in [0, 40]."""
+    t = IZ_TMAX * np.arange(IZ_NT + 1) / IZ_NT
+    kz = np.asarray(kz, dtype=np.float64)
+    y = np.exp(-kz[..., None] * t) / np.cosh(t) ** 2
+    return simpson(y, IZ_TMAX / IZ_NT)
+
+
+def disk_vc2(R, g: Galaxy):
+    """Circular speed squared in the midplane of the sech^2 exponential disk
+    (surface density Sigma0 e^{-R/R_d}, Sigma0 = M_disk / (2 pi R_d^2)):
+    v_c^2 = 2 pi G Sigma0 R_d^2 R int_0^inf k J1(kR) I(k z0) (1 + k^2 R_d^2)^{-3/2} dk
+    (the thin disk's Hankel form with e^{-k|z|} averaged over the layer), by
+    Simpson's rule on k in [0, 40 / R_d]."""
+    from scipy import special
+    s0 = g.M_disk / (2.0 * math.pi * g.R_d * g.R_d)
+    hk = VC_KMAX / g.R_d / VC_NK
+    k = hk * np.arange(VC_NK + 1)
+    w = k * vertical_factor(k * g.z0) * (1.0 + (k * g.R_d) ** 2) ** -1.5
+    R = np.asarray(R, dtype=np.float64)
+    out = np.empty_like(R)
+    for a in range(0, R.size, 256):
+        Rb = R[a:a + 256]
+        out[a:a + 256] = simpson(special.j1(Rb[:, None] * k[None, :]) * w[None, :], hk)
+    return 2.0 * math.pi * g.G * s0 * g.R_d * g.R_d * R * out
 
 
 def central_diff(y, h):
@@ -334,7 +409,7 @@ def disk_tables(g: Galaxy, pr):
     cdf[-1] = 1.0
     R = (np.arange(KD) + 0.5) * h            # kinematic grid
     msph = sph_mass_at(pr, "halo", R) + sph_mass_at(pr, "bulge", R)
-    vc2 = g.G * msph / R + freeman_vc2(R, g.G, g.M_disk, g.R_d)
+    vc2 = g.G * msph / R + disk_vc2(R, g)
     om2 = vc2 / (R * R)
     kap2 = R * central_diff(om2, h) + 4.0 * om2
     kap = np.sqrt(np.maximum(kap2, 1e-30))

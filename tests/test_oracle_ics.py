@@ -9,7 +9,10 @@ inversion against Hernquist's closed-form distribution function (Hernquist
 defining integral) and against the isotropic Jeans equation; sampled radii,
 heights and speeds against their distributions; the virial theorem for a
 sampled halo (forces by direct summation); Freeman's disk rotation against
-its Keplerian limit and the position of its maximum."""
+its Keplerian limit and the position of its maximum; the thick disk's
+vertical factor against its closed forms, its spherical mass against an
+independent cylindrical integral, and its midplane rotation against
+Freeman's curve in the thin limit."""
 import math
 
 import numpy as np
@@ -212,6 +215,66 @@ def test_freeman_rotation_limits():
     Rg = np.linspace(0.5, 5, 9001)
     Rpk = Rg[np.argmax(gi.freeman_vc2(Rg, G, M, Rd))]
     assert abs(Rpk - 2.15) < 0.01
+
+
+def test_vertical_factor_closed_forms():
+    """I(kappa) = int_0^inf sech^2(t) e^{-kappa t} dt: 1, pi/2 - 1,
+    2 ln 2 - 1 and 3 - 4 ln 2 at kappa = 0, 1, 2, 4 (from sech^2 t = 4
+    sum_n (-1)^(n+1) n e^{-2nt}, summed in the Abel sense); kappa = 4 is
+    near the top of the range the disk uses (40 z0 / R_d = 4.8)."""
+    I = gi.vertical_factor(np.array([0.0, 1.0, 2.0, 4.0]))
+    assert abs(I[0] - 1) < 1e-12
+    assert abs(I[1] - (math.pi / 2 - 1)) < 1e-8
+    assert abs(I[2] - (2 * math.log(2) - 1)) < 1e-8
+    assert abs(I[3] - (3 - 4 * math.log(2))) < 1e-8
+
+
+def test_disk_spherical_mass_against_cylindrical_integral(sec4):
+    """M(<r) of the sech^2 disk from its shell rate (Simpson in the polar
+    angle, trapezoid in ln r) equals the independent integral over
+    cylinders, int_0^min(r, R_max) 2 pi R Sigma(R) tanh(sqrt(r^2 - R^2)/z0)
+    dR (a sech^2 column holds tanh(h/z0) of its mass within |z| < h); the
+    total is M_disk; far inside z0 it is the central density times the
+    volume; in the thin limit it is the thin disk's 1 - (1 + x) e^-x."""
+    from scipy import integrate
+    g, _ = sec4
+    r, dl = gi.radial_grid()
+    M, dM = gi.disk_sph_mass(r, dl, g)
+    sig0 = gi.disk_sigma0(g)
+    for rr in (0.05, 0.3, 1.0, 3.0, 10.0, 29.0, 40.0):
+        k = int(np.argmin(np.abs(r - rr)))
+        rk = r[k]
+        cyl = integrate.quad(lambda R: 2 * math.pi * R * sig0 * math.exp(-R / g.R_d)
+                             * math.tanh(math.sqrt(max(rk * rk - R * R, 0.0)) / g.z0),
+                             0.0, min(rk, g.R_max), limit=400, epsabs=0, epsrel=1e-11)[0]
+        assert abs(M[k] / cyl - 1) < 2e-5, (rr, M[k], cyl)
+    assert abs(M[-1] / g.M_disk - 1) < 1e-5
+    k = int(np.argmin(np.abs(r - 1e-3)))
+    # to first order in r / R_d (the radial fall-off of Sigma inside the sphere)
+    assert abs(M[k] / (4 / 3 * math.pi * r[k] ** 3 * sig0 / (2 * g.z0)) - 1) < 2 * r[k] / g.R_d
+    import dataclasses
+    thin = dataclasses.replace(g, z0=1e-4)
+    Mt, _ = gi.disk_sph_mass(r, dl, thin)
+    sel = (r > 0.5) & (r < 25)
+    want = g.M_disk * gi.disk_fraction(r[sel] / g.R_d) / gi.disk_fraction(g.R_max / g.R_d)
+    assert np.max(np.abs(Mt[sel] / want - 1)) < 2e-3
+
+
+def test_thick_disk_rotation_limits(sec4):
+    """The sech^2 disk's midplane circular speed tends to Freeman's thin-disk
+    curve as z0 -> 0 (within the k range's truncation), lies below it for
+    z0 = 0.3 kpc by an amount that shrinks outwards, and is Keplerian far
+    out."""
+    import dataclasses
+    g, _ = sec4
+    R = np.array([1.0, 2.0, 4.0, 8.0, 16.0])
+    fr = gi.freeman_vc2(R, g.G, g.M_disk, g.R_d)
+    thin = dataclasses.replace(g, z0=1e-7)
+    assert np.max(np.abs(gi.disk_vc2(R, thin) / fr - 1)) < 2e-3
+    ratio = gi.disk_vc2(R, g) / fr
+    assert np.all(ratio < 1) and np.all(np.diff(ratio) > 0) and ratio[-1] > 0.99
+    far = np.array([60.0 * g.R_d])
+    assert abs(gi.disk_vc2(far, g)[0] * far[0] / (g.G * g.M_disk) - 1) < 2e-3
 
 
 def test_disk_kinematic_tables(sec4):
