@@ -6,10 +6,11 @@
 //   1. k_shapes: a logarithmic radial grid r_k = R_MIN e^{k dl}; for both
 //      spheroids the tapered shape C(r) / (x (1+x)^beta) (beta = 2 NFW, 3
 //      Hernquist; C = erfc((r - r_t)/(sqrt(2) dr_t))/2) and its first two
-//      radial derivatives in closed form; the thin exponential disk's mass
-//      inside radius r.
+//      radial derivatives in closed form; the sech^2 exponential disk's
+//      spherical shell mass rate (Simpson in the polar angle).
 //   2. k_cumulative: enclosed shape masses (closed form below the first
-//      node, trapezoid rule in ln r above), one block per spheroid.
+//      node, trapezoid rule in ln r above), one block per spheroid and one
+//      for the disk.
 //   3. k_profiles: normalised densities, masses and cumulative fractions.
 //   4. k_potential: Psi = G M(<r)/r + G int_r dM/dr' d ln r' (reverse scan),
 //      Psi', Psi'' and d2rho/dPsi2 = (rho'' Psi' - rho' Psi'')/Psi'^3.
@@ -19,8 +20,8 @@
 //   6. k_speed_cdf: per radius, the cumulative distribution of the speed
 //      fraction q = v/v_esc, density q^2 f(Psi_min + (1 - q^2)(Psi - Psi_min)).
 //   7. k_disk_*: the disk's cumulative surface mass, its rotation in the
-//      spheroids' enclosed mass plus Freeman's thin exponential disk
-//      (modified Bessel functions below), the epicyclic frequency, the
+//      spheroids' enclosed mass plus the midplane force of the sech^2
+//      exponential disk (Hankel integral in k), the epicyclic frequency, the
 //      dispersions (sigma_R^2 ~ Sigma with Toomre's Q at R_Q, epicyclic
 //      sigma_phi, isothermal-sheet sigma_z) and the asymmetric-drift
 //      rotation.
@@ -42,12 +43,18 @@ constexpr int KD = BONSAI_ICS_KD;
 constexpr double R_MIN = 1.0e-4;
 constexpr double R_MAX = 600.0;
 constexpr double PI = 3.141592653589793238462643383279502884;
+constexpr int SHELL_N = 2048;   // Simpson intervals of the disk's spherical shell average
+constexpr int VC_NK = 4000;     // Simpson intervals of the disk's Hankel integral in k
+constexpr double VC_KMAX = 40.0;  // k range, in units of 1 / R_d
+constexpr int IZ_NT = 4096;     // Simpson intervals of the vertical factor in t = z / z0
+constexpr double IZ_TMAX = 40.0;
 
 // rows of the radial table
 enum {
     RR = 0, RPSI, RMT, RMH, RMB, RPH, RPB, RG2H, RG2B, RFH, RFB, RVNH, RVNB, RRHOH, RRHOB,
     RLOGR, RS1H, RS2H, RS1B, RS2B, RFH_INT, RFB_INT, RSH, RSB, RDMT, RMD, RDMD, RS0H, RS0B,
     RSLH, RSLB,  // d2rho/dPsi2 slope of segment [Psi_{k+1}, Psi_k]
+    RFD_INT,     // r dM/dr of the disk (integrand in ln r)
     NRAD
 };
 static_assert(BONSAI_ICS_NRAD_OUT <= NRAD, "exported radial rows");
@@ -59,7 +66,16 @@ struct IcsTables {
     double *rad;   // [NRAD][K]
     double *vcdf;  // [2][K][V]
     double *disk;  // [NDISK][KD]
+    double *iz;    // [VC_NK + 1]: the disk's vertical factor I(k z0) on the k grid
 };
+
+// Simpson weight of node j of n intervals (n even), without the h/3
+__device__ __forceinline__ double simpson_w(int j, int n) {
+    return (j == 0 || j == n) ? 1.0 : ((j & 1) ? 4.0 : 2.0);
+}
+
+// Central surface density of the truncated disk (total mass M_disk)
+__device__ double disk_sigma0(const bonsai_galaxy &g);
 
 __device__ __forceinline__ double *row(double *t, int r) { return t + (size_t)r * K; }
 __device__ __forceinline__ const double *row(const double *t, int r) { return t + (size_t)r * K; }
@@ -75,6 +91,10 @@ __device__ double disk_fraction(double x) {
         t = t * x / (k + 1);
     }
     return s;
+}
+
+__device__ double disk_sigma0(const bonsai_galaxy &g) {
+    return g.M_disk / (2.0 * PI * g.R_d * g.R_d * disk_fraction(g.R_max / g.R_d));
 }
 
 // ---------------------------------------------------------------- step 1
@@ -104,9 +124,27 @@ __global__ void k_shapes(bonsai_galaxy g, double *rad) {
         row(rad, c == 0 ? RS2H : RS2B)[k] = h2 * C + 2.0 * h1 * C1 + h * C2;
         row(rad, c == 0 ? RFH_INT : RFB_INT)[k] = 4.0 * PI * r * r * r * s0;
     }
-    const double xd = r / g.R_d;
-    row(rad, RMD)[k] = g.M_disk * disk_fraction(xd);
-    row(rad, RDMD)[k] = g.M_disk * xd * exp(-xd) / g.R_d;
+    // the disk: 4 pi r^2 times its density averaged over the sphere, rho =
+    // Sigma0 e^{-R/R_d} sech^2(z/z0) / (2 z0) for R <= R_max, by Simpson's
+    // rule in the polar angle phi (R = r cos phi, z = r sin phi) on
+    // [acos(min(1, R_max/r)), asin(min(1, 40 z0/r))]
+    const double sig0 = disk_sigma0(g);
+    const double hi = asin(fmin(1.0, IZ_TMAX * g.z0 / r));
+    const double lo = acos(fmin(1.0, g.R_max / r));
+    double dM = 0.0;
+    if (hi > lo) {
+        const double hp = (hi - lo) / SHELL_N;
+        double acc = 0.0;
+        for (int j = 0; j <= SHELL_N; ++j) {
+            const double phi = lo + (hi - lo) * j / SHELL_N;
+            const double cph = cos(phi);
+            const double ch = cosh(r * sin(phi) / g.z0);
+            acc += simpson_w(j, SHELL_N) * (sig0 * exp(-r * cph / g.R_d) / (2.0 * g.z0) / (ch * ch)) * cph;
+        }
+        dM = 4.0 * PI * r * r * (hp / 3.0 * acc);
+    }
+    row(rad, RDMD)[k] = dM;
+    row(rad, RFD_INT)[k] = r * dM;
 }
 
 // Exclusive scan of one double per thread over a block of 1024 threads.
@@ -142,19 +180,25 @@ static_assert(KD % 256 == 0 && KD % 64 == 0, "disk launch shapes");
 
 // ---------------------------------------------------------------- step 2
 // S[k] = S0 + sum_{j<k} (F_j + F_{j+1}) dl / 2, S0 the closed-form mass of
-// the untapered cusp below r_0 times C(r_0).  Block 0: halo, block 1: bulge.
+// the untapered cusp below r_0 times C(r_0).  Block 0: halo, block 1: bulge,
+// block 2: the disk (S0: the central density times the volume below r_0).
 __global__ void __launch_bounds__(SCAN_T) k_cumulative(bonsai_galaxy g, double *rad) {
     __shared__ double sh[32];
     const int c = blockIdx.x;
     const double dl = log(R_MAX / R_MIN) / (K - 1);
-    const double *F = row(rad, c == 0 ? RFH_INT : RFB_INT);
-    double *S = row(rad, c == 0 ? RSH : RSB);
-    const double a = c == 0 ? g.a_halo : g.a_bulge;
+    const double *F = row(rad, c == 0 ? RFH_INT : (c == 1 ? RFB_INT : RFD_INT));
+    double *S = row(rad, c == 0 ? RSH : (c == 1 ? RSB : RMD));
     const double r0 = R_MIN;
-    const double x0 = r0 / a;
-    const double C0 = 0.5 * erfc((r0 - g.r_t) / (sqrt(2.0) * g.dr_t));
-    const double I = c == 0 ? log1p(x0) - x0 / (1.0 + x0) : x0 * x0 / (2.0 * (1.0 + x0) * (1.0 + x0));
-    const double S0 = 4.0 * PI * a * a * a * C0 * I;
+    double S0;
+    if (c == 2) {
+        S0 = 4.0 / 3.0 * PI * r0 * r0 * r0 * disk_sigma0(g) / (2.0 * g.z0);
+    } else {
+        const double a = c == 0 ? g.a_halo : g.a_bulge;
+        const double x0 = r0 / a;
+        const double C0 = 0.5 * erfc((r0 - g.r_t) / (sqrt(2.0) * g.dr_t));
+        const double I = c == 0 ? log1p(x0) - x0 / (1.0 + x0) : x0 * x0 / (2.0 * (1.0 + x0) * (1.0 + x0));
+        S0 = 4.0 * PI * a * a * a * C0 * I;
+    }
     const int j0 = threadIdx.x * PER_T;
     double seg[PER_T], tot = 0.0;
 #pragma unroll
@@ -352,34 +396,22 @@ __global__ void __launch_bounds__(EDD_WARPS * 32) k_speed_cdf(double *rad, doubl
 }
 
 // ---------------------------------------------------------------- step 7
-// Modified Bessel functions of order 0 and 1.  I_nu by the power series
-// sum_k (y^2/4)^k (y/2)^nu / (k! (k+nu)!) (positive terms, no cancellation);
-// K_nu by the trapezoid rule on K_nu(y) = int_0^inf exp(-y cosh t) cosh(nu t)
-// dt, whose integrand is analytic in the strip |Im t| < pi/2, so that the
-// rule with step h errs by about exp(-pi^2 / h) (h = 1/8: 1e-34).
-__device__ void bessel01(double y, double &i0, double &i1, double &k0, double &k1) {
-    const double q = 0.25 * y * y;
-    double t0 = 1.0, t1 = 1.0, s0 = 1.0, s1 = 1.0;
-    for (int k = 1; k < 80; ++k) {
-        t0 *= q / ((double)k * k);
-        t1 *= q / ((double)k * (k + 1));
-        s0 += t0;
-        s1 += t1;
+// The disk's vertical factor on the k grid k_j = j (40 / R_d) / VC_NK:
+// I(k z0) = int_0^inf sech^2(t) e^{-k z0 t} dt (the sech^2 layer's weight of
+// e^{-k|z|}; 1 for a thin disk), Simpson's rule on t in [0, 40].
+__global__ void k_disk_vertical(bonsai_galaxy g, double *iz) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j > VC_NK) return;
+    const double hk = VC_KMAX / g.R_d / VC_NK;
+    const double kz = hk * j * g.z0;
+    const double ht = IZ_TMAX / IZ_NT;
+    double acc = 0.0;
+    for (int i = 0; i <= IZ_NT; ++i) {
+        const double t = IZ_TMAX * i / IZ_NT;
+        const double ch = cosh(t);
+        acc += simpson_w(i, IZ_NT) * (exp(-kz * t) / (ch * ch));
     }
-    i0 = s0;
-    i1 = 0.5 * y * s1;
-    const double h = 0.125;
-    double a0 = 0.5 * exp(-y), a1 = a0;
-    for (int m = 1; m < 1024; ++m) {
-        const double ch = cosh(m * h);
-        const double ex = -y * ch;
-        if (ex < -745.0) break;
-        const double e = exp(ex);
-        a0 += e;
-        a1 += e * ch;
-    }
-    k0 = h * a0;
-    k1 = h * a1;
+    iz[j] = ht / 3.0 * acc;
 }
 
 __device__ __forceinline__ double central(const double *y, int j, double h) {
@@ -410,8 +442,13 @@ __device__ __forceinline__ DiskRows disk_rows(double *disk) {
                     disk + (size_t)DVPHI * KD, disk + (size_t)DOM2 * KD, disk + (size_t)DKAP2 * KD};
 }
 
-// 7a: cumulative surface mass on R_j = j h, v_c^2 and Omega^2 on (j + 1/2) h
-__global__ void k_disk_rotation(bonsai_galaxy g, const double *rad, double *disk) {
+// 7a: cumulative surface mass on R_j = j h, v_c^2 and Omega^2 on (j + 1/2) h.
+// The disk's part of v_c^2 in the midplane of the sech^2 exponential disk:
+// 2 pi G Sigma0 R_d^2 R int_0^inf k J1(kR) I(k z0) (1 + k^2 R_d^2)^{-3/2} dk
+// (the thin disk's Hankel form with e^{-k|z|} averaged over the layer),
+// Simpson's rule on k in [0, 40 / R_d].
+__global__ void k_disk_rotation(bonsai_galaxy g, const double *rad, const double *iz,
+                                double *disk) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= KD) return;
     const DiskRows D = disk_rows(disk);
@@ -420,10 +457,15 @@ __global__ void k_disk_rotation(bonsai_galaxy g, const double *rad, double *disk
     D.cdf[j] = j == KD - 1 ? 1.0 : disk_fraction(j * h / g.R_d) / disk_fraction(g.R_max / g.R_d);
     const double R = (j + 0.5) * h;
     const double ms = sph_mass_at(rad, RMH, R) + sph_mass_at(rad, RMB, R);
-    const double y = R / (2.0 * g.R_d);
-    double i0, i1, k0, k1;
-    bessel01(y, i0, i1, k0, k1);
-    const double v2 = g.G * ms / R + 4.0 * PI * g.G * s0 * g.R_d * y * y * (i0 * k0 - i1 * k1);
+    const double hk = VC_KMAX / g.R_d / VC_NK;
+    double acc = 0.0;
+    for (int i = 0; i <= VC_NK; ++i) {
+        const double k = hk * i;
+        const double q = 1.0 + (k * g.R_d) * (k * g.R_d);
+        acc += simpson_w(i, VC_NK) * (j1(R * k) * (k * iz[i] * (1.0 / (q * sqrt(q)))));
+    }
+    const double vd2 = 2.0 * PI * g.G * s0 * g.R_d * g.R_d * R * (hk / 3.0 * acc);
+    const double v2 = g.G * ms / R + vd2;
     D.vc2[j] = v2;
     D.om2[j] = v2 / (R * R);
 }
@@ -687,18 +729,19 @@ int check(const bonsai_galaxy *g) {
         if (Ns[c] > 0 && !(Ms[c] > 0.0)) return BONSAI_EINVAL;
     }
     if (!(g->M_halo + g->M_disk + g->M_bulge > 0.0)) return BONSAI_EINVAL;
-    if (g->R_max > 200.0 * g->R_d) return BONSAI_EINVAL;  // Bessel arguments up to 100
+    if (g->R_max > 200.0 * g->R_d) return BONSAI_EINVAL;  // the disk tables' range
     return BONSAI_OK;
 }
 
 int build_tables(const bonsai_galaxy &g, IcsTables &t, cudaStream_t s) {
     k_shapes<<<(K + 255) / 256, 256, 0, s>>>(g, t.rad);
-    k_cumulative<<<2, SCAN_T, 0, s>>>(g, t.rad);
+    k_cumulative<<<3, SCAN_T, 0, s>>>(g, t.rad);
     k_profiles<<<(K + 255) / 256, 256, 0, s>>>(g, t.rad);
     k_potential<<<1, SCAN_T, 0, s>>>(g, t.rad);
     k_eddington<<<(2 * K + EDD_WARPS - 1) / EDD_WARPS, EDD_WARPS * 32, 0, s>>>(t.rad);
     k_speed_cdf<<<(2 * K + EDD_WARPS - 1) / EDD_WARPS, EDD_WARPS * 32, 0, s>>>(t.rad, t.vcdf);
-    k_disk_rotation<<<KD / 64, 64, 0, s>>>(g, t.rad, t.disk);
+    k_disk_vertical<<<(VC_NK + 1 + 127) / 128, 128, 0, s>>>(g, t.iz);
+    k_disk_rotation<<<KD / 64, 64, 0, s>>>(g, t.rad, t.iz, t.disk);
     k_disk_kappa<<<KD / 256, 256, 0, s>>>(g, t.disk);
     k_disk_kinematics<<<KD / 256, 256, 0, s>>>(g, t.disk);
     return cudaGetLastError() == cudaSuccess ? BONSAI_OK : BONSAI_ECUDA;
@@ -707,6 +750,7 @@ int build_tables(const bonsai_galaxy &g, IcsTables &t, cudaStream_t s) {
 constexpr size_t RAD_BYTES = sizeof(double) * (size_t)NRAD * K;
 constexpr size_t VCDF_BYTES = sizeof(double) * (size_t)2 * K * V;
 constexpr size_t DISK_BYTES = sizeof(double) * (size_t)NDISK * KD;
+constexpr size_t IZ_BYTES = sizeof(double) * (size_t)(VC_NK + 2);
 
 struct Scratch {
     unsigned char *p = nullptr;
@@ -751,12 +795,14 @@ extern "C" int bonsai_galaxy_tables(const bonsai_galaxy *g, double *radial, doub
     if (!radial || !disk) return BONSAI_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     Scratch sc(s);
-    if (cudaMallocAsync((void **)&sc.p, RAD_BYTES + VCDF_BYTES + DISK_BYTES, s) != cudaSuccess) {
+    if (cudaMallocAsync((void **)&sc.p, RAD_BYTES + VCDF_BYTES + DISK_BYTES + IZ_BYTES, s) !=
+        cudaSuccess) {
         cudaGetLastError();
         return BONSAI_ENOMEM;
     }
     IcsTables t{reinterpret_cast<double *>(sc.p), reinterpret_cast<double *>(sc.p + RAD_BYTES),
-                reinterpret_cast<double *>(sc.p + RAD_BYTES + VCDF_BYTES)};
+                reinterpret_cast<double *>(sc.p + RAD_BYTES + VCDF_BYTES),
+                reinterpret_cast<double *>(sc.p + RAD_BYTES + VCDF_BYTES + DISK_BYTES)};
     rc = build_tables(*g, t, s);
     if (rc != BONSAI_OK) return rc;
     if (cudaMemcpyAsync(radial, t.rad, sizeof(double) * (size_t)BONSAI_ICS_NRAD_OUT * K,
@@ -784,14 +830,16 @@ extern "C" int bonsai_galaxy_generate(const bonsai_galaxy *g, double *pos, doubl
     const int nparts = sms * 4;
     Scratch sc(s);
     const size_t part_bytes = sizeof(double) * 7 * (size_t)nparts;
-    if (cudaMallocAsync((void **)&sc.p, RAD_BYTES + VCDF_BYTES + DISK_BYTES + part_bytes, s) !=
-        cudaSuccess) {
+    if (cudaMallocAsync((void **)&sc.p, RAD_BYTES + VCDF_BYTES + DISK_BYTES + IZ_BYTES + part_bytes,
+                        s) != cudaSuccess) {
         cudaGetLastError();
         return BONSAI_ENOMEM;
     }
     IcsTables t{reinterpret_cast<double *>(sc.p), reinterpret_cast<double *>(sc.p + RAD_BYTES),
-                reinterpret_cast<double *>(sc.p + RAD_BYTES + VCDF_BYTES)};
-    double *part = reinterpret_cast<double *>(sc.p + RAD_BYTES + VCDF_BYTES + DISK_BYTES);
+                reinterpret_cast<double *>(sc.p + RAD_BYTES + VCDF_BYTES),
+                reinterpret_cast<double *>(sc.p + RAD_BYTES + VCDF_BYTES + DISK_BYTES)};
+    double *part =
+        reinterpret_cast<double *>(sc.p + RAD_BYTES + VCDF_BYTES + DISK_BYTES + IZ_BYTES);
     rc = build_tables(*g, t, s);
     if (rc != BONSAI_OK) return rc;
     SampleArgs A{*g, t.rad, t.vcdf, t.disk, pos, vel, mass, n};
