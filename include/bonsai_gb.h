@@ -48,7 +48,9 @@ extern "C" {
 #define BONSAI_EIO (-6)       /* a snapshot file could not be opened, read or written, or
                                  is not a snapshot of this format (size, magic, version) */
 #define BONSAI_ETIMEOUT (-7)  /* a host wait on the device exceeded the wait limit
-                                 (bonsai_set_wait_timeout); the work stays queued */
+                                 (bonsai_set_wait_timeout); the work stays queued.
+                                 Also: a grid-wide barrier of the octree build gave
+                                 up after about a second (the tree is not built) */
 
 typedef struct bonsai_ctx bonsai_ctx;
 typedef struct bonsai_let bonsai_let;
@@ -96,14 +98,15 @@ int bonsai_set_stream(bonsai_ctx *ctx, void *stream);
  * moments" (with the keys and sort of Sec. III.B.1 / Table 2):
  *   bounding cube -> 21-bit Peano-Hilbert keys -> stable radix sort by
  *   (key, index) -> gather to key order -> octree (leaf <= 16 particles,
- *   children in key order, breadth-first numbering) -> walk groups (nodes
- *   of <= 64 particles whose parent has more) -> FP64 mass, centre of mass
- *   and non-traceless quadrupole per node.
+ *   children in key order, breadth-first numbering, built in one
+ *   cooperative launch) -> walk groups (runs of consecutive sibling cells of
+ *   <= 64 particles in all, under a parent with more) -> FP64 mass, centre
+ *   of mass and non-traceless quadrupole per node.
  * pos: device [3][n] float64; mass: device [n] float64 (> 0, finite);
  * n >= 1.  The context copies what it needs; the caller's buffers are only
  * read during the call.  Velocities are reset to zero.
  * Errors: EINVAL (null pointer, n < 1 or > 2^31 - 1, non-finite position,
- * mass <= 0), ENOMEM, ECUDA. */
+ * mass <= 0), ENOMEM, ECUDA, ETIMEOUT (see its definition). */
 int tree_build(bonsai_ctx *ctx, const double *pos, const double *mass, int64_t n);
 
 /* tree_forces -- Sec. III.A "tree-walk in which inter-particle gravitational
@@ -457,9 +460,10 @@ const char *bonsai_strerror(int code);
  * given buffers but no right to allocate.  It creates no context and calls
  * no cudaMalloc, cudaFree or allocating library routine.
  *
- * Scratch: a fixed static device array of about 12.3 MB (two ping-pong
- * halves of the sort for up to BONSAI_NOALLOC_MAX_N pairs, the histograms,
- * the bounding-box partials and a status word), part of the library's
+ * Scratch: a fixed static device array of about 13.2 MB (two ping-pong
+ * halves of the sort for up to BONSAI_NOALLOC_MAX_N pairs, the sort's digit
+ * counts and look-back descriptors, the bounding-box partials and a status
+ * word), part of the library's
  * device code.  The CUDA runtime places it on a device when it loads that
  * code there: with the default lazy module loading at the first call on
  * the device, with CUDA_MODULE_LOADING=EAGER when the library is loaded.
@@ -479,7 +483,8 @@ const char *bonsai_strerror(int code);
  * cudaStream_t (NULL = legacy default stream).  The call returns after the
  * work is complete.
  * Errors: EINVAL (a null pointer, n < 1, n > BONSAI_NOALLOC_MAX_N, a
- * non-finite position or a mass <= 0), ECUDA. */
+ * non-finite position or a mass <= 0), ECUDA, ETIMEOUT (a bounded wait of
+ * the sort's look-back gave up; the output is then not sorted). */
 int bonsai_sfc_order_noalloc(const double *pos, const double *mass, int64_t n, uint64_t *keys,
                              uint32_t *perm, double cube[4], void *stream);
 

@@ -122,8 +122,8 @@ int particle_buffers(bonsai_ctx *c, int64_t n) {
     if (ensure(c->pos, n3) || ensure(c->pos2, n3) || ensure(c->vel, n3) || ensure(c->vel2, n3) ||
         ensure(c->mass, n) || ensure(c->mass2, n) || ensure(c->id, n) || ensure(c->id2, n) ||
         ensure(c->acc, n3) || ensure(c->pot, n) || ensure(c->key, n) || ensure(c->key2, n) ||
-        ensure(c->val, n) || ensure(c->val2, n) || ensure(c->hist, sort_hist_elems(n)) ||
-        ensure(c->scan_tmp, scan_tmp_elems(std::max<int64_t>(n, sort_hist_elems(n)))) ||
+        ensure(c->val, n) || ensure(c->val2, n) || ensure(c->hist, sort_scratch_elems(n)) ||
+        ensure(c->scan_tmp, scan_tmp_elems(n)) ||
         ensure(c->box_part, (size_t)c->sm_count * 4 + 8) || ensure(c->body_hi, n) ||
         ensure(c->body_lo, n) || ensure(c->grp_flag, 2 * (size_t)n + 2) ||
         ensure(c->diag_part, (size_t)diag_blocks(c) * 10 + 16))
@@ -168,11 +168,12 @@ int rebuild(bonsai_ctx *c, const double *pos, const double *mass, bool from_call
     if (from_caller) launch_gather_build(c, pos, mass, n); else launch_gather_step(c, n);
     BGB_CUDA(cudaEventRecord(c->ev[1], c->stream));
     BGB_CUDA(cudaGetLastError());
+    c->have_tree = false;
     int rc = build_octree(c);
     if (rc) return rc;
     if ((rc = node_buffers(c))) return rc;
     if ((rc = build_groups(c))) return rc;
-    launch_multipoles(c);
+    if ((rc = launch_multipoles(c))) return rc;
     launch_body_pack(c);
     BGB_CUDA(cudaEventRecord(c->ev[2], c->stream));
     BGB_CUDA(cudaGetLastError());
@@ -180,6 +181,10 @@ int rebuild(bonsai_ctx *c, const double *pos, const double *mass, bool from_call
     if (c->hsc->status & ST_BAD_INPUT) {
         c->have_tree = false;
         return BONSAI_EINVAL;
+    }
+    if (c->hsc->status & ST_TIMEOUT) {  // a bounded device-side wait gave up
+        c->have_tree = false;
+        return BONSAI_ETIMEOUT;
     }
     if (!c->fixed_cube) {
         for (int d = 0; d < 3; ++d) c->cube[d] = c->hsc->lo[d];

@@ -25,7 +25,7 @@ namespace bgb {
 namespace {
 
 constexpr int DB = 128;     // threads per block
-constexpr int DP = 4;       // target pairs per thread
+constexpr int DP = 3;       // target pairs per thread (6 blocks of 80 registers per SM)
 constexpr int DTG = 2 * DP; // targets per thread
 constexpr int DTILE = 256;  // source records per shared-memory tile
 constexpr int MAX_CHUNKS = 64;
@@ -86,7 +86,7 @@ __device__ __forceinline__ void tile_pairs(const float4 *sr, int cnt, const int 
 // with eps = 0, ALL_MASK, in every tile), and the other tiles run without
 // the per-pair test.
 template <bool ALL_MASK>
-__global__ void __launch_bounds__(DB, 5) k_direct(const float4 *__restrict__ hi,
+__global__ void __launch_bounds__(DB, 6) k_direct(const float4 *__restrict__ hi,
                                                   const float4 *__restrict__ lo, int64_t n,
                                                   const int64_t *__restrict__ targets,
                                                   const uint32_t *__restrict__ inv, int64_t nt,

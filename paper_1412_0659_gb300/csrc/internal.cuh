@@ -20,6 +20,23 @@ constexpr uint32_t LEAF_FLAG = 0x80000000u;  // topo.y: leaf marker, low bits = 
 constexpr int ST_BAD_INPUT = 1;      // non-finite position or mass <= 0
 constexpr int ST_OVERFLOW = 2;       // a walk frontier overflowed
 constexpr int ST_NODE_OVERFLOW = 4;  // node storage too small (host regrows)
+constexpr int ST_TIMEOUT = 8;        // a bounded grid-barrier wait gave up
+
+// Order-preserving integer image of a double: for finite values (the input
+// check rejects the others) a < b exactly when key(a) < key(b), with -0 just
+// below +0.  Minima and maxima taken on the keys are therefore exact, and
+// run on the integer pipes instead of the FP64 one.
+__device__ __forceinline__ long long order_key(double v) {
+    const long long b = __double_as_longlong(v);
+    return b ^ ((b >> 63) & 0x7fffffffffffffffll);
+}
+__device__ __forceinline__ double from_order_key(long long k) {
+    return __longlong_as_double(k ^ ((k >> 63) & 0x7fffffffffffffffll));
+}
+
+// cooperative octree build: threads per block, polls of a barrier wait
+constexpr int OCT_BLOCK = 256;
+constexpr uint32_t OCT_SPINS = 1u << 22;
 
 // Device scalars written by kernels and read back in one copy.
 struct DevScalars {
@@ -28,13 +45,17 @@ struct DevScalars {
     double scale;     // 2^21 / L
     uint64_t n_pp;    // interaction counters of the last walk
     uint64_t n_pc;
-    uint32_t level_count;  // children produced by the last split level
     int32_t status;        // ST_* bits
     int32_t max_frontier;
     uint32_t group_counter;  // dynamic scheduling of the walk
     uint32_t n_groups;
     int32_t pad;
     double mn[3], mx[3];  // componentwise bounds of the last bounding-box reduction
+    // octree build: level starts, node count, depth, nodes needed after an
+    // overflow, and the grid barrier's arrival counter and generation
+    uint32_t oct_level[MAX_LEVEL + 2];
+    uint32_t oct_nodes, oct_depth, oct_need;
+    uint32_t bar_count, bar_gen;
 };
 
 // Bounding-cube reduction partials (per block)
@@ -90,7 +111,7 @@ struct bonsai_ctx {
 
     // nodes (breadth-first)
     bgb::DBuf<uint32_t> nd_first, nd_count, nd_child, nd_nchild, nd_level, nd_parent;
-    bgb::DBuf<uint32_t> nd_scan;     // per-level scan scratch
+    bgb::DBuf<uint32_t> nd_scan;     // octree build: per-block child counts
     bgb::DBuf<double> nd_M;          // [nn]
     bgb::DBuf<double> nd_com;        // [3][nn]
     bgb::DBuf<double> nd_Q;          // [6][nn]
@@ -184,7 +205,7 @@ void launch_gather_step(bonsai_ctx *c, int64_t n);
 // tree.cu
 int build_octree(bonsai_ctx *c);
 int build_groups(bonsai_ctx *c);
-void launch_multipoles(bonsai_ctx *c);
+int launch_multipoles(bonsai_ctx *c);
 void launch_body_pack(bonsai_ctx *c);
 void launch_cell_pack(bonsai_ctx *c, float theta);
 // walk.cu
@@ -230,9 +251,11 @@ constexpr size_t scan_tmp_elems(int64_t n) {
     }
     return t + 64;
 }
-// entries of the per-tile digit histograms of a sort of n pairs
-constexpr size_t sort_hist_elems(int64_t n) {
-    return 256 * (size_t)((n + SORT_TILE - 1) / SORT_TILE) + 64;
+// uint32 entries of the scratch of a sort of n pairs: one 64-bit look-back
+// descriptor per tile and digit, then the 8 x 256 digit counts and the 8
+// passes' tile counters
+constexpr size_t sort_scratch_elems(int64_t n) {
+    return 2 * 256 * (size_t)((n + SORT_TILE - 1) / SORT_TILE) + 8 * 256 + 64;
 }
 void launch_unpermute_state(bonsai_ctx *c, double *pos, double *vel, double *mass);
 void launch_unpermute_forces(bonsai_ctx *c, float *acc, float *pot);
@@ -248,8 +271,8 @@ void launch_rev_accum(bonsai_ctx *c, double *xbar, double *mbar);
 int launch_cube_keys_into(cudaStream_t s, int sm_count, const double *pos, const double *mass,
                           int64_t n, BoxPartial *part, int max_part, DevScalars *dsc,
                           uint64_t *key, uint32_t *val);
-int radix_sort_pairs_into(cudaStream_t s, int64_t n, uint64_t *ka, uint64_t *kb, uint32_t *va,
-                          uint32_t *vb, uint32_t *hist, uint32_t *tmp);
+int radix_sort_pairs_into(cudaStream_t s, int sm_count, int64_t n, uint64_t *ka, uint64_t *kb,
+                          uint32_t *va, uint32_t *vb, uint32_t *scratch, int32_t *status);
 
 // Exclusive scan on explicit buffers (in and out must not alias; tmp holds
 // scan_tmp_elems(n) entries); *total_dev receives the sum.  Returns the

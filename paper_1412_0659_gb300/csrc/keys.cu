@@ -6,6 +6,7 @@
 // the keys are bit-identical to any IEEE implementation of the same formula.
 #include <math.h>
 
+#include <climits>
 #include <cmath>
 
 #include "internal.cuh"
@@ -26,32 +27,46 @@ __device__ inline double warp_max(double v) {
 }
 
 // Per-block min/max of x, y, z plus an input check (finite positions,
-// finite positive masses).
+// finite positive masses).  The minima and maxima are taken on the
+// order-preserving integer images of the doubles and the checks on their
+// bit patterns, so the loop uses no FP64 instruction.
+__device__ inline long long warp_min_k(long long v) {
+    for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_down_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ inline long long warp_max_k(long long v) {
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_down_sync(0xffffffffu, v, o));
+    return v;
+}
+
 __global__ void __launch_bounds__(BOX_BLOCK) k_box_partial(const double *__restrict__ pos,
                                                            const double *__restrict__ mass,
                                                            int64_t n, BoxPartial *part) {
-    double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    constexpr long long EXP = 0x7ff0000000000000ll;  // exponent field: all ones = inf / NaN
+    long long mn[3] = {LLONG_MAX, LLONG_MAX, LLONG_MAX}, mx[3] = {LLONG_MIN, LLONG_MIN, LLONG_MIN};
     int bad = 0;
     for (int64_t i = blockIdx.x * (int64_t)BOX_BLOCK + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * BOX_BLOCK) {
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            double v = pos[d * n + i];
-            bad |= !isfinite(v);
-            mn[d] = fmin(mn[d], v);
-            mx[d] = fmax(mx[d], v);
+            const double v = pos[d * n + i];
+            bad |= (__double_as_longlong(v) & EXP) == EXP;
+            const long long k = order_key(v);
+            mn[d] = min(mn[d], k);
+            mx[d] = max(mx[d], k);
         }
-        double m = mass[i];
-        bad |= !(m > 0.0) || !isfinite(m);
+        // positive, finite and not zero: the bit pattern lies in (0, +inf)
+        const long long mb = __double_as_longlong(mass[i]);
+        bad |= !(mb > 0ll && mb < EXP);
     }
-    __shared__ double smn[3][BOX_BLOCK / 32], smx[3][BOX_BLOCK / 32];
+    __shared__ long long smn[3][BOX_BLOCK / 32], smx[3][BOX_BLOCK / 32];
     __shared__ int sbad;
     if (threadIdx.x == 0) sbad = 0;
     __syncthreads();
     int w = threadIdx.x >> 5, l = threadIdx.x & 31;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-        double a = warp_min(mn[d]), b = warp_max(mx[d]);
+        long long a = warp_min_k(mn[d]), b = warp_max_k(mx[d]);
         if (l == 0) { smn[d][w] = a; smx[d][w] = b; }
     }
     if (bad) atomicOr(&sbad, 1);
@@ -59,11 +74,14 @@ __global__ void __launch_bounds__(BOX_BLOCK) k_box_partial(const double *__restr
     if (threadIdx.x < 32) {
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            double a = l < BOX_BLOCK / 32 ? smn[d][l] : INFINITY;
-            double b = l < BOX_BLOCK / 32 ? smx[d][l] : -INFINITY;
-            a = warp_min(a);
-            b = warp_max(b);
-            if (l == 0) { part[blockIdx.x].mn[d] = a; part[blockIdx.x].mx[d] = b; }
+            long long a = l < BOX_BLOCK / 32 ? smn[d][l] : LLONG_MAX;
+            long long b = l < BOX_BLOCK / 32 ? smx[d][l] : LLONG_MIN;
+            a = warp_min_k(a);
+            b = warp_max_k(b);
+            if (l == 0) {
+                part[blockIdx.x].mn[d] = from_order_key(a);
+                part[blockIdx.x].mx[d] = from_order_key(b);
+            }
         }
         if (l == 0) part[blockIdx.x].bad = sbad;
     }
@@ -125,11 +143,13 @@ __global__ void __launch_bounds__(BOX_BLOCK) k_box_final(const BoxPartial *part,
     }
 }
 
+// floor((x - lo) * scale) clamped to [0, 2^21 - 1], each FP64 step rounded
+// to nearest.  The conversion truncates toward zero and saturates (NaN gives
+// 0), which equals floor followed by the clamp: a negative product becomes
+// 0 or less either way, and a non-negative one truncates to its floor.
 __device__ inline uint32_t quantise(double x, double lo, double scale) {
-    double f = floor(__dmul_rn(__dsub_rn(x, lo), scale));
-    if (!(f >= 0.0)) return 0u;
-    if (f > (double)((1u << KEY_BITS) - 1u)) return (1u << KEY_BITS) - 1u;
-    return (uint32_t)f;
+    const int f = __double2int_rz(__dmul_rn(__dsub_rn(x, lo), scale));
+    return (uint32_t)min(max(f, 0), (int)((1u << KEY_BITS) - 1u));
 }
 
 // Spread the low 21 bits of v to every third bit of a 64-bit word.

@@ -21,19 +21,15 @@ constexpr size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 // byte offsets of the regions of the scratch array
 constexpr size_t OFF_KEY2 = 0;
 constexpr size_t OFF_VAL2 = OFF_KEY2 + align256(sizeof(uint64_t) * MAX_N);
-constexpr size_t HIST_ELEMS = bgb::sort_hist_elems(MAX_N);
-// the sort scans its 256 x tiles histogram entries
-constexpr size_t SCAN_ELEMS = bgb::scan_tmp_elems((int64_t)(HIST_ELEMS - 64));
-constexpr size_t OFF_HIST = OFF_VAL2 + align256(sizeof(uint32_t) * MAX_N);
-constexpr size_t OFF_SCAN = OFF_HIST + align256(sizeof(uint32_t) * HIST_ELEMS);
-constexpr size_t OFF_PART = OFF_SCAN + align256(sizeof(uint32_t) * SCAN_ELEMS);
+constexpr size_t SORT_ELEMS = bgb::sort_scratch_elems(MAX_N);
+constexpr size_t OFF_SORT = OFF_VAL2 + align256(sizeof(uint32_t) * MAX_N);
+constexpr size_t OFF_PART = OFF_SORT + align256(sizeof(uint32_t) * SORT_ELEMS);
 constexpr size_t OFF_DSC = OFF_PART + align256(sizeof(BoxPartial) * MAX_PART);
 constexpr size_t SCRATCH_BYTES = OFF_DSC + align256(sizeof(DevScalars));
-// the regions are sized from the sort's own tile constants, so a retuned sort
-// cannot write past its region; the total stays modest
-static_assert(OFF_SCAN - OFF_HIST >= sizeof(uint32_t) * bgb::sort_hist_elems(MAX_N), "histogram region");
-static_assert(OFF_PART - OFF_SCAN >= sizeof(uint32_t) * bgb::scan_tmp_elems(256 * ((MAX_N + bgb::SORT_TILE - 1) / bgb::SORT_TILE)),
-              "scan region");
+// the sort's region is sized from its own tile constants, so a retuned sort
+// cannot write past it; the total stays modest
+static_assert(OFF_PART - OFF_SORT >= sizeof(uint32_t) * bgb::sort_scratch_elems(MAX_N), "sort region");
+static_assert(OFF_SORT % 8 == 0, "the sort's descriptors are 64-bit words");
 static_assert(SCRATCH_BYTES < (16u << 20), "scratch array above 16 MB");
 
 // The scratch of every call on this device.  Host code must not use its name
@@ -81,20 +77,20 @@ extern "C" int bonsai_sfc_order_noalloc(const double *pos, const double *mass, i
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     uint64_t *key2 = reinterpret_cast<uint64_t *>(base + OFF_KEY2);
     uint32_t *val2 = reinterpret_cast<uint32_t *>(base + OFF_VAL2);
-    uint32_t *hist = reinterpret_cast<uint32_t *>(base + OFF_HIST);
-    uint32_t *tmp = reinterpret_cast<uint32_t *>(base + OFF_SCAN);
+    uint32_t *sort_scratch = reinterpret_cast<uint32_t *>(base + OFF_SORT);
     BoxPartial *part = reinterpret_cast<BoxPartial *>(base + OFF_PART);
     DevScalars *dsc = reinterpret_cast<DevScalars *>(base + OFF_DSC);
     // the status word and cube of the previous call are still there: clear them
     BGB_CUDA(cudaMemsetAsync(dsc, 0, sizeof(DevScalars), s));
     bgb::launch_cube_keys_into(s, sms, pos, mass, n, part, MAX_PART, dsc, keys, perm);
     // eight passes ping-pong between the caller's buffers and the scratch halves
-    bgb::radix_sort_pairs_into(s, n, keys, key2, perm, val2, hist, tmp);
+    bgb::radix_sort_pairs_into(s, sms, n, keys, key2, perm, val2, sort_scratch, &dsc->status);
     BGB_CUDA(cudaGetLastError());
     DevScalars h;
     BGB_CUDA(cudaMemcpyAsync(&h, dsc, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
     BGB_WAIT(s);
     if (h.status & bgb::ST_BAD_INPUT) return BONSAI_EINVAL;
+    if (h.status & bgb::ST_TIMEOUT) return BONSAI_ETIMEOUT;
     if (cube) {
         cube[0] = h.lo[0];
         cube[1] = h.lo[1];

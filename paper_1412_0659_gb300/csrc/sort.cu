@@ -2,11 +2,10 @@
 // scan, and the gathers that move particle state into key order
 // (Table 2 "Sorting SFC").
 //
-// The sort is 8 passes of 8 bits.  Each pass is a per-tile histogram, an
-// exclusive scan of the digit-major histogram table (which yields every
-// tile's output offset per digit), and a stable scatter that ranks the
-// tile's keys with warp match/popc and writes them digit by digit.  Stability plus the index payload
-// starting at 0..n-1 makes the order identical to sorting by (key, index).
+// The sort is 8 passes of 8 bits after one count of all digits; each pass
+// is one kernel (a one-sweep pass with decoupled look-back, below).
+// Stability plus the index payload starting at 0..n-1 makes the order
+// identical to sorting by (key, index).
 #include <utility>
 
 #include "internal.cuh"
@@ -17,7 +16,29 @@ namespace {
 
 // SORT_BLOCK, SORT_IPT, SORT_TILE, SCAN_BLOCK, SCAN_IPT and SCAN_TILE are
 // in internal.cuh: the scratch sizes of every caller derive from them.
+// ---- one-sweep LSD radix sort ----
+// Digit d of pass p is bits [8p, 8p + 8) of the key.  k_sort_counts counts
+// every pass's digits in one read of the keys.  Each pass is then a single
+// kernel over tiles of SORT_TILE pairs, taken in launch order from a
+// counter: a tile ranks its pairs by digit (warp match/popc against
+// warp-private counts, so equal digits keep their input order), publishes
+// its per-digit counts, and finds its global offset per digit by a
+// decoupled look-back over the descriptors of the tiles before it (the
+// exclusive sum of their counts), stopping at the first tile that already
+// published its inclusive prefix.  A descriptor is one 64-bit word: the pass
+// (plus one) in bits 56-63, the kind (1 = this tile's count, 2 = inclusive
+// prefix) in bits 54-55, the value below; words of another pass read as not
+// yet published, and the whole array is cleared once per sort.  A tile
+// waits only on tiles that started before it, so the look-back always
+// ends; its polling is bounded all the same, and a wait that gives up sets
+// ST_TIMEOUT.
 constexpr int SORT_WARPS = SORT_BLOCK / 32;
+constexpr int PER_WARP = SORT_TILE / SORT_WARPS;  // contiguous pairs of one warp
+constexpr int ROUNDS = PER_WARP / 32;
+constexpr uint64_t DESC_VALUE = (1ull << 54) - 1ull;
+constexpr uint64_t DESC_COUNT = 1ull << 54, DESC_PREFIX = 2ull << 54;
+constexpr uint32_t LOOKBACK_SPINS = 1u << 22;
+constexpr int LOOKBACK_W = 8;  // predecessors read per look-back round trip
 
 __device__ inline uint32_t lanemask_lt() {
     uint32_t m;
@@ -25,112 +46,187 @@ __device__ inline uint32_t lanemask_lt() {
     return m;
 }
 
-__global__ void __launch_bounds__(SORT_BLOCK) k_hist(const uint64_t *__restrict__ kin, int64_t n,
-                                                     int shift, uint32_t *__restrict__ hist,
-                                                     int nb) {
-    __shared__ uint32_t cnt[256];
-    cnt[threadIdx.x] = 0;
+// The digit counts of all eight passes: cnt[p * 256 + d] (zeroed by the
+// caller), from block-private shared counters.  Per warp and pass, a digit
+// shared by all 32 lanes (the usual case for the high digits of nearly
+// sorted keys) is one add; otherwise every lane adds its own.
+__global__ void __launch_bounds__(SORT_BLOCK) k_sort_counts(const uint64_t *__restrict__ kin,
+                                                            int64_t n, uint32_t *__restrict__ cnt) {
+    __shared__ uint32_t sc[8][256];
+    for (int k = threadIdx.x; k < 8 * 256; k += SORT_BLOCK) (&sc[0][0])[k] = 0u;
     __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * SORT_TILE;
-    for (int r = 0; r < SORT_IPT; ++r) {
-        int64_t i = base + r * SORT_BLOCK + threadIdx.x;
-        uint32_t d = i < n ? (uint32_t)(kin[i] >> shift) & 255u : 256u;
-        uint32_t peers = __match_any_sync(0xffffffffu, d);
-        if (d < 256u && (peers & lanemask_lt()) == 0u) atomicAdd(&cnt[d], __popc(peers));
-    }
-    __syncthreads();
-    hist[(int64_t)threadIdx.x * nb + blockIdx.x] = cnt[threadIdx.x];
-}
-
-// Stable scatter of one tile, in two halves of 2048 pairs.  Each warp owns
-// a contiguous run of 256 pairs of the half and ranks them by digit with
-// match_any against warp-private digit counts; a scan over the digits then
-// gives every pair its place in a digit-sorted copy of the half in shared
-// memory, from which the pairs of each digit are written to global memory
-// as one contiguous run (instead of one scattered store per pair).  Warps
-// own consecutive positions, so the order within a digit is the input order.
-__global__ void __launch_bounds__(SORT_BLOCK) k_scatter(const uint64_t *__restrict__ kin,
-                                                        const uint32_t *__restrict__ vin,
-                                                        uint64_t *__restrict__ kout,
-                                                        uint32_t *__restrict__ vout, int64_t n,
-                                                        int shift,
-                                                        const uint32_t *__restrict__ offs,
-                                                        int nb) {
-    constexpr int HALF = SORT_TILE / 2;
-    constexpr int PER_WARP = HALF / SORT_WARPS;
-    constexpr int ROUNDS = PER_WARP / 32;
-    __shared__ uint64_t sk[HALF];
-    __shared__ uint32_t sv[HALF];
-    __shared__ uint32_t wh[SORT_WARPS][256];
-    __shared__ uint32_t gbase[256], lstart[256], wsum[SORT_WARPS];
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const uint32_t lt = lanemask_lt();
-    gbase[tid] = offs[(int64_t)tid * nb + blockIdx.x];
-    for (int h = 0; h < 2; ++h) {
-        const int64_t h0 = (int64_t)blockIdx.x * SORT_TILE + (int64_t)h * HALF;
+    const int64_t stride = (int64_t)gridDim.x * SORT_BLOCK;
+    const int64_t end = (n + 31) / 32 * 32;  // whole warps take part in the votes
+    for (int64_t i = (int64_t)blockIdx.x * SORT_BLOCK + threadIdx.x; i < end; i += stride) {
+        const bool valid = i < n;
+        const uint64_t k = valid ? kin[i] : 0ull;
 #pragma unroll
-        for (int w = 0; w < SORT_WARPS; ++w) wh[w][tid] = 0u;
-        __syncthreads();
-        uint64_t key[ROUNDS];
-        uint32_t val[ROUNDS], dg[ROUNDS], rk[ROUNDS];
-#pragma unroll
-        for (int r = 0; r < ROUNDS; ++r) {
-            const int64_t i = h0 + warp * PER_WARP + r * 32 + lane;
-            const bool valid = i < n;
-            key[r] = valid ? kin[i] : 0ull;
-            val[r] = valid ? vin[i] : 0u;
-            const uint32_t d = valid ? (uint32_t)(key[r] >> shift) & 255u : 256u;
-            dg[r] = d;
-            const uint32_t peers = __match_any_sync(0xffffffffu, d);
-            const uint32_t prev = d < 256u ? wh[warp][d] : 0u;
-            rk[r] = prev + __popc(peers & lt);
-            __syncwarp();
-            if (d < 256u && (peers & lt) == 0u) wh[warp][d] = prev + __popc(peers);
-            __syncwarp();
-        }
-        __syncthreads();
-        // digit tid: offsets of the warps' runs, and the half's count
-        uint32_t cnt = 0;
-#pragma unroll
-        for (int w = 0; w < SORT_WARPS; ++w) {
-            const uint32_t c = wh[w][tid];
-            wh[w][tid] = cnt;
-            cnt += c;
-        }
-        // exclusive scan of the counts over the 256 digits
-        uint32_t inc = cnt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += t;
-        }
-        if (lane == 31) wsum[warp] = inc;
-        __syncthreads();
-        uint32_t add = 0;
-        for (int w = 0; w < warp; ++w) add += wsum[w];
-        lstart[tid] = add + inc - cnt;
-        __syncthreads();
-#pragma unroll
-        for (int r = 0; r < ROUNDS; ++r) {
-            const uint32_t d = dg[r];
-            if (d < 256u) {
-                const uint32_t p = lstart[d] + wh[warp][d] + rk[r];
-                sk[p] = key[r];
-                sv[p] = val[r];
+        for (int p = 0; p < 8; ++p) {
+            const uint32_t d = valid ? (uint32_t)(k >> (8 * p)) & 255u : 256u;
+            const uint32_t d0 = __shfl_sync(0xffffffffu, d, 0);
+            if (__all_sync(0xffffffffu, d == d0)) {
+                if ((threadIdx.x & 31) == 0 && d0 < 256u) atomicAdd(&sc[p][d0], 32u);
+            } else if (d < 256u) {
+                atomicAdd(&sc[p][d], 1u);
             }
         }
-        __syncthreads();
-        const int64_t left = n - h0;
-        const int nh = left <= 0 ? 0 : (left < HALF ? (int)left : HALF);
-        for (int p = tid; p < nh; p += SORT_BLOCK) {
-            const uint64_t k = sk[p];
-            const uint32_t d = (uint32_t)(k >> shift) & 255u;
-            const uint32_t dst = gbase[d] + ((uint32_t)p - lstart[d]);
-            kout[dst] = k;
-            vout[dst] = sv[p];
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < 8 * 256; k += SORT_BLOCK) {
+        const uint32_t v = (&sc[0][0])[k];
+        if (v) atomicAdd(cnt + k, v);
+    }
+}
+
+// One pass (digit shift 8 * pass) over one tile per block.  Shared memory:
+// the tile's pairs in digit order (sk, sv), the warps' digit counts, and per
+// digit the tile's local start and global base.
+struct SweepShared {
+    uint64_t sk[SORT_TILE];
+    uint32_t sv[SORT_TILE];
+    uint32_t wh[SORT_WARPS][256];
+    uint32_t lstart[256], gbase[256], wsum[SORT_WARPS];
+    uint32_t tile;
+};
+
+__global__ void __launch_bounds__(SORT_BLOCK, 3) k_sort_pass(const uint64_t *__restrict__ kin,
+                                                          const uint32_t *__restrict__ vin,
+                                                          uint64_t *__restrict__ kout,
+                                                          uint32_t *__restrict__ vout, int64_t n,
+                                                          int pass, uint64_t *desc,
+                                                          const uint32_t *__restrict__ cnt,
+                                                          uint32_t *tile_counter,
+                                                          int32_t *status) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SweepShared &S = *reinterpret_cast<SweepShared *>(smem_raw);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int shift = 8 * pass;
+    const uint32_t lt = lanemask_lt();
+    if (tid == 0) S.tile = atomicAdd(tile_counter + pass, 1u);
+#pragma unroll
+    for (int w = 0; w < SORT_WARPS; ++w) S.wh[w][tid] = 0u;
+    __syncthreads();
+    const uint32_t tile = S.tile;
+    const int64_t t0 = (int64_t)tile * SORT_TILE;
+    // 1. ranks within the warp's contiguous run (the keys are read again in
+    // step 3, from L2, rather than held in registers through the look-back)
+    uint32_t dr[ROUNDS];  // digit (bits 0-8, 256 = past the end) | rank in warp << 9
+#pragma unroll
+    for (int r = 0; r < ROUNDS; ++r) {
+        const int64_t i = t0 + warp * PER_WARP + r * 32 + lane;
+        const bool valid = i < n;
+        const uint32_t d = valid ? (uint32_t)(kin[i] >> shift) & 255u : 256u;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t prev = d < 256u ? S.wh[warp][d] : 0u;
+        dr[r] = d | ((prev + __popc(peers & lt)) << 9);
+        __syncwarp();
+        if (d < 256u && (peers & lt) == 0u) S.wh[warp][d] = prev + __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    // 2. digit tid: the warps' offsets within the digit and the tile's count
+    uint32_t c = 0;
+#pragma unroll
+    for (int w = 0; w < SORT_WARPS; ++w) {
+        const uint32_t x = S.wh[w][tid];
+        S.wh[w][tid] = c;
+        c += x;
+    }
+    // publish this tile's count, then look back for the exclusive prefix
+    const uint64_t epoch = (uint64_t)(pass + 1) << 56;
+    uint64_t *my = desc + (int64_t)tile * 256 + tid;
+    volatile uint64_t *vmy = my;
+    uint64_t excl = 0;
+    if (tile == 0) {
+        *vmy = epoch | DESC_PREFIX | (uint64_t)c;
+    } else {
+        *vmy = epoch | DESC_COUNT | (uint64_t)c;
+        // LOOKBACK_W predecessors per round trip (independent loads), taken
+        // nearest first; an unpublished one is polled again from there
+        int64_t t = (int64_t)tile - 1;
+        uint32_t spins = 0;
+        while (t >= 0) {
+            uint64_t v[LOOKBACK_W];
+#pragma unroll
+            for (int w = 0; w < LOOKBACK_W; ++w)  // before tile 0: a zero prefix
+                v[w] = t - w >= 0 ? *(volatile uint64_t *)(desc + (t - w) * 256 + tid)
+                                  : (epoch | DESC_PREFIX);
+            int used = LOOKBACK_W;
+            bool done = false;
+#pragma unroll
+            for (int w = 0; w < LOOKBACK_W; ++w) {
+                if ((v[w] & (255ull << 56)) != epoch) {
+                    used = w;
+                    break;
+                }
+                excl += v[w] & DESC_VALUE;
+                if ((v[w] & (3ull << 54)) == DESC_PREFIX) {
+                    done = true;
+                    break;
+                }
+            }
+            if (done) break;
+            t -= used;
+            if (used < LOOKBACK_W) {
+                if (++spins > LOOKBACK_SPINS || (*(volatile int32_t *)status & ST_TIMEOUT)) {
+                    atomicOr(status, ST_TIMEOUT);
+                    break;
+                }
+                __nanosleep(32);
+            }
         }
-        __syncthreads();
-        gbase[tid] += cnt;
+        *vmy = epoch | DESC_PREFIX | (excl + c);
+    }
+    // global base of digit tid: pairs of smaller digits in all tiles, plus
+    // pairs of this digit in the tiles before this one
+    uint32_t inc = __ldg(cnt + pass * 256 + tid), lc = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t a = __shfl_up_sync(0xffffffffu, inc, o);
+        const uint32_t b = __shfl_up_sync(0xffffffffu, lc, o);
+        if (lane >= o) {
+            inc += a;
+            lc += b;
+        }
+    }
+    // inc: inclusive scan of the global counts over this warp's digits; lc:
+    // the same for the tile's counts
+    __shared__ uint32_t gsum[SORT_WARPS];
+    if (lane == 31) {
+        gsum[warp] = inc;
+        S.wsum[warp] = lc;
+    }
+    __syncthreads();
+    uint32_t gadd = 0, ladd = 0;
+    for (int w = 0; w < warp; ++w) {
+        gadd += gsum[w];
+        ladd += S.wsum[w];
+    }
+    const uint32_t gcount = __ldg(cnt + pass * 256 + tid);
+    S.gbase[tid] = (gadd + inc - gcount) + (uint32_t)excl;
+    S.lstart[tid] = ladd + lc - c;
+    __syncthreads();
+    // 3. the tile's pairs in digit order in shared memory (values read now)
+#pragma unroll
+    for (int r = 0; r < ROUNDS; ++r) {
+        const uint32_t d = dr[r] & 511u;
+        if (d < 256u) {
+            const int64_t i = t0 + warp * PER_WARP + r * 32 + lane;
+            const uint32_t p = S.lstart[d] + S.wh[warp][d] + (dr[r] >> 9);
+            S.sk[p] = kin[i];
+            S.sv[p] = vin[i];
+        }
+    }
+    __syncthreads();
+    // 4. each digit's pairs as one contiguous run of the output
+    const int64_t left = n - t0;
+    const int nt = left < SORT_TILE ? (int)left : SORT_TILE;
+    for (int p = tid; p < nt; p += SORT_BLOCK) {
+        const uint64_t k = S.sk[p];
+        const uint32_t d = (uint32_t)(k >> shift) & 255u;
+        const int64_t dst = (int64_t)S.gbase[d] + (p - (int64_t)S.lstart[d]);
+        kout[dst] = k;
+        vout[dst] = S.sv[p];
     }
 }
 
@@ -262,38 +358,34 @@ int exclusive_scan_into(cudaStream_t s, const uint32_t *in, uint32_t *out, int64
     return launches;
 }
 
-// The same eight passes on explicit buffers: (ka, va) hold the input and the
-// result, (kb, vb) are the second ping-pong half, hist holds
-// sort_hist_elems(n) entries and tmp scan_tmp_elems(256 * tiles) entries.
-// Returns the number of kernels launched.
-int radix_sort_pairs_into(cudaStream_t s, int64_t n, uint64_t *ka, uint64_t *kb, uint32_t *va,
-                          uint32_t *vb, uint32_t *hist, uint32_t *tmp) {
-    const int nb = (int)((n + SORT_TILE - 1) / SORT_TILE);
-    const int64_t nh = 256ll * nb;
-    int launches = 0;
-    for (int shift = 0; shift < 64; shift += 8) {
-        k_hist<<<nb, SORT_BLOCK, 0, s>>>(ka, n, shift, hist, nb);
-        launches += scan_rec(s, hist, hist, nh, tmp) + 2;
-        k_scatter<<<nb, SORT_BLOCK, 0, s>>>(ka, va, kb, vb, n, shift, hist, nb);
+// The sort on explicit buffers: (ka, va) hold the input and the result,
+// (kb, vb) are the second ping-pong half, scratch holds
+// sort_scratch_elems(n) entries (cleared here; 8-byte aligned), status
+// receives ST_TIMEOUT if a look-back wait gave up.  Returns the number of
+// kernels launched.
+int radix_sort_pairs_into(cudaStream_t s, int sm_count, int64_t n, uint64_t *ka, uint64_t *kb,
+                          uint32_t *va, uint32_t *vb, uint32_t *scratch, int32_t *status) {
+    const int64_t tiles = (n + SORT_TILE - 1) / SORT_TILE;
+    uint64_t *desc = reinterpret_cast<uint64_t *>(scratch);
+    uint32_t *cnt = scratch + 2 * 256 * tiles;
+    uint32_t *tile_counter = cnt + 8 * 256;
+    cudaMemsetAsync(scratch, 0, sort_scratch_elems(n) * sizeof(uint32_t), s);
+    k_sort_counts<<<grid_for(n, SORT_BLOCK * 16, sm_count * 2), SORT_BLOCK, 0, s>>>(ka, n, cnt);
+    cudaFuncSetAttribute(k_sort_pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(SweepShared));
+    for (int pass = 0; pass < 8; ++pass) {
+        k_sort_pass<<<(unsigned)tiles, SORT_BLOCK, sizeof(SweepShared), s>>>(
+            ka, va, kb, vb, n, pass, desc, cnt, tile_counter, status);
         uint64_t *tk = ka; ka = kb; kb = tk;
         uint32_t *tv = va; va = vb; vb = tv;
     }
-    return launches;
+    // eight passes: the result is back in (ka, va)
+    return 9;
 }
 
 void radix_sort_pairs(bonsai_ctx *c, int64_t n) {
-    const int nb = (int)((n + SORT_TILE - 1) / SORT_TILE);
-    const int64_t nh = 256ll * nb;
-    uint64_t *ka = c->key.p, *kb = c->key2.p;
-    uint32_t *va = c->val.p, *vb = c->val2.p;
-    for (int shift = 0; shift < 64; shift += 8) {
-        k_hist<<<nb, SORT_BLOCK, 0, c->stream>>>(ka, n, shift, c->hist.p, nb);
-        c->launches += scan_rec(c->stream, c->hist.p, c->hist.p, nh, c->scan_tmp.p) + 2;
-        k_scatter<<<nb, SORT_BLOCK, 0, c->stream>>>(ka, va, kb, vb, n, shift, c->hist.p, nb);
-        uint64_t *tk = ka; ka = kb; kb = tk;
-        uint32_t *tv = va; va = vb; vb = tv;
-    }
-    // eight passes: the result is back in key/val
+    c->launches += radix_sort_pairs_into(c->stream, c->sm_count, n, c->key.p, c->key2.p, c->val.p,
+                                         c->val2.p, c->hist.p, &c->dsc->status);
 }
 
 void launch_gather_build(bonsai_ctx *c, const double *pos, const double *mass, int64_t n) {

@@ -3,17 +3,18 @@
 // and "computation of multipole moments"; Sec. I.A leaf size 16; Sec. VI.A
 // mass, centre of mass and 3x3 symmetric quadrupole per cell).
 //
-// The octree is built level by level: a node of level l holding more than
-// 16 particles is cut into the runs of equal key digit l+1 (8 binary
-// searches on its sorted key range); an exclusive scan over the level's
-// child counts numbers the children breadth-first, so the numbering is a
-// pure function of the sorted keys.  The host reads one count per level to
-// size the next launch.
+// The octree is built level by level in one cooperative launch: a node of
+// level l holding more than 16 particles is cut into the runs of equal key
+// digit l+1 (8 binary searches on its sorted key range); an exclusive scan
+// over the level's child counts numbers the children breadth-first, so the
+// numbering is a pure function of the sorted keys.  Grid-wide barriers
+// separate the counting and writing phases of each level, and the host
+// reads the level table once at the end.
 //
-// The upward pass computes every leaf in one launch (a leaf needs only its
-// particles), then visits the levels bottom-up, where internal nodes
-// combine their children by the parallel-axis rule; every FP64 operation is
-// an explicit round-to-nearest intrinsic in a fixed order.
+// The upward pass is one cooperative launch: leaves from their particles,
+// then internal nodes level by level from their children by the
+// parallel-axis rule; every FP64 operation is an explicit round-to-nearest
+// intrinsic in a fixed order.
 #include <math.h>
 
 #include <algorithm>
@@ -24,14 +25,6 @@ namespace bgb {
 
 
 namespace {
-
-__global__ void k_root(uint32_t *first, uint32_t *count, uint32_t *level, uint32_t *parent,
-                       uint32_t n) {
-    first[0] = 0;
-    count[0] = n;
-    level[0] = 0;
-    parent[0] = 0;
-}
 
 // Child boundaries of a node at level l: b[d] = first slot of [f, f + c)
 // whose digit l+1 is >= d.  The seven lower bounds share the range, so they
@@ -60,212 +53,324 @@ __device__ inline void child_bounds(const uint64_t *__restrict__ key, uint32_t f
         b[d + 1] = lo[d] + (key[lo[d]] < (base | ((uint64_t)(d + 1) << shift)) ? 1u : 0u);
 }
 
-__global__ void __launch_bounds__(256) k_split_count(const uint64_t *__restrict__ key,
-                                                     const uint32_t *__restrict__ first,
-                                                     const uint32_t *__restrict__ count,
-                                                     uint32_t *__restrict__ nchild,
-                                                     uint32_t *__restrict__ scan_in, int64_t s,
-                                                     int64_t m, int l) {
-    int64_t t = blockIdx.x * 256ll + threadIdx.x;
-    if (t >= m) return;
-    int64_t i = s + t;
-    uint32_t f = first[i], c = count[i], nc = 0;
-    if (c > (uint32_t)NLEAF && l < MAX_LEVEL) {
-        uint32_t b[9];
-        child_bounds(key, f, c, l, b);
-#pragma unroll
-        for (int d = 0; d < 8; ++d) nc += b[d + 1] > b[d];
-    }
-    nchild[i] = nc;
-    scan_in[t] = nc;
-}
-
-__global__ void __launch_bounds__(256) k_split_write(
-    const uint64_t *__restrict__ key, uint32_t *__restrict__ first, uint32_t *__restrict__ count,
-    uint32_t *__restrict__ child, const uint32_t *__restrict__ nchild, uint32_t *__restrict__ level,
-    uint32_t *__restrict__ parent, uint2 *__restrict__ topo, const uint32_t *__restrict__ off,
-    int64_t s, int64_t m, int64_t e, int l) {
-    int64_t t = blockIdx.x * 256ll + threadIdx.x;
-    if (t >= m) return;
-    int64_t i = s + t;
-    uint32_t f = first[i], c = count[i], nc = nchild[i];
-    if (nc == 0) {
-        child[i] = 0;
-        topo[i] = make_uint2(f, c | LEAF_FLAG);
-        return;
-    }
-    uint32_t ch = (uint32_t)(e + off[t]);
-    child[i] = ch;
-    topo[i] = make_uint2(ch, nc);
-    uint32_t b[9];
-    child_bounds(key, f, c, l, b);
-    uint32_t k = ch;
-#pragma unroll
-    for (int d = 0; d < 8; ++d) {
-        if (b[d + 1] > b[d]) {
-            first[k] = b[d];
-            count[k] = b[d + 1] - b[d];
-            level[k] = (uint32_t)(l + 1);
-            parent[k] = (uint32_t)i;
-            ++k;
+// Grid-wide barrier of a cooperative launch (every block resident).  Each
+// thread fences its own writes, the block meets, and one thread arrives on
+// the counter; the last arrival resets it and advances the generation.  The
+// wait is bounded: after OCT_SPINS polls (a second or so), or as soon as
+// another block has given up, the block records ST_TIMEOUT and reports
+// failure, so every block's later barriers end too and the kernel returns.
+__device__ bool grid_barrier(DevScalars *sc) {
+    __shared__ int ok;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int good = 1;
+        volatile uint32_t *gen = &sc->bar_gen;
+        volatile int32_t *status = &sc->status;
+        const uint32_t g = *gen;  // read before arriving: it cannot advance before we do
+        if (atomicAdd(&sc->bar_count, 1u) == gridDim.x - 1u) {
+            atomicExch(&sc->bar_count, 0u);
+            __threadfence();
+            atomicAdd(&sc->bar_gen, 1u);
+        } else {
+            uint32_t it = 0;
+            while (*gen == g) {
+                if (++it > OCT_SPINS || (*status & ST_TIMEOUT)) {
+                    atomicOr(&sc->status, ST_TIMEOUT);
+                    good = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
         }
+        __threadfence();
+        ok = good;
     }
+    __syncthreads();
+    return ok != 0;
 }
 
-// Leaves of the deepest level never reach k_split_write: mark them here.
-__global__ void k_mark_leaves(const uint32_t *__restrict__ first, const uint32_t *__restrict__ count,
-                              uint32_t *__restrict__ child, uint32_t *__restrict__ nchild,
-                              uint2 *__restrict__ topo, int64_t s, int64_t m) {
-    int64_t t = blockIdx.x * 256ll + threadIdx.x;
-    if (t >= m) return;
-    int64_t i = s + t;
-    child[i] = 0;
-    nchild[i] = 0;
-    topo[i] = make_uint2(first[i], count[i] | LEAF_FLAG);
+// Block-wide exclusive sum of v over OCT_BLOCK threads; *total gets the sum.
+__device__ __forceinline__ uint32_t block_excl_sum(uint32_t v, uint32_t *total) {
+    __shared__ uint32_t wsum[OCT_BLOCK / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    __syncthreads();  // wsum is reused from the previous call
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();
+    uint32_t before = 0, all = 0;
+#pragma unroll
+    for (int w = 0; w < OCT_BLOCK / 32; ++w) {
+        const uint32_t x = wsum[w];
+        before += w < warp ? x : 0u;
+        all += x;
+    }
+    *total = all;
+    return before + inc - v;
+}
+
+// The whole octree in one cooperative launch, level by level.  At level l
+// (nodes [s, e)), every block takes a contiguous chunk of the level:
+//   A. each node of more than NLEAF particles (and l < MAX_LEVEL) counts
+//      its non-empty children from the boundaries of digit l+1; the block
+//      sums its counts;
+//   -- barrier --
+//   B. a block's children start after those of all lower blocks (a sum of
+//      the per-block counts) and, within the block, after those of its
+//      lower nodes (a block scan in node order), so the numbering is
+//      breadth-first and a pure function of the sorted keys.  Each node
+//      writes its children (first, count, level, parent) and its topology
+//      record, and flags the walk groups it starts: the runs of its
+//      children of at most NCRIT particles, gathered greedily in key order
+//      up to NCRIT particles, a child of more than NCRIT ending the run
+//      (its own children are grouped by its thread); the root when it
+//      holds at most NCRIT; NCRIT-particle runs of a max-depth leaf that
+//      holds more;
+//   -- barrier --
+// until a level has no children.  Nodes written by other blocks are read
+// through L2 (ld.cg).  If the next level would pass cap nodes, nothing of it
+// is written: ST_NODE_OVERFLOW and the node count needed so far are
+// reported and the host grows the arrays and launches again.
+__global__ void __launch_bounds__(OCT_BLOCK) k_octree(
+    const uint64_t *__restrict__ key, uint32_t n, uint32_t *first, uint32_t *count,
+    uint32_t *child, uint32_t *nchild, uint32_t *level, uint32_t *parent, uint2 *topo,
+    uint32_t *__restrict__ flag, uint32_t cap, uint32_t *bsum, DevScalars *sc) {
+    const uint32_t nb = gridDim.x, blk = blockIdx.x, tid = threadIdx.x;
+    if (blk == 0 && tid == 0) {
+        first[0] = 0;
+        count[0] = n;
+        level[0] = 0;
+        parent[0] = 0;
+        sc->oct_level[0] = 0;
+        sc->oct_level[1] = 1;
+    }
+    __syncthreads();  // block 0 owns the root's chunk of level 0
+    uint32_t s = 0, e = 1;
+    for (int l = 0; l <= MAX_LEVEL; ++l) {
+        const uint32_t m = e - s;
+        const uint32_t per = (m + nb - 1u) / nb;
+        const uint32_t c0 = min(m, blk * per), c1 = min(m, c0 + per);
+        // A: child counts
+        uint32_t mine = 0;
+        for (uint32_t t = c0 + tid; t < c1; t += OCT_BLOCK) {
+            const uint32_t i = s + t;
+            const uint32_t f = __ldcg(first + i), c = __ldcg(count + i);
+            uint32_t nc = 0;
+            if (c > (uint32_t)NLEAF && l < MAX_LEVEL) {
+                uint32_t b[9];
+                child_bounds(key, f, c, l, b);
+#pragma unroll
+                for (int d = 0; d < 8; ++d) nc += b[d + 1] > b[d];
+            }
+            nchild[i] = nc;
+            mine += nc;
+        }
+        uint32_t block_total;
+        block_excl_sum(mine, &block_total);
+        if (tid == 0) bsum[blk] = block_total;
+        if (!grid_barrier(sc)) return;
+        // B: this block's offset and the level's total
+        uint32_t lower = 0, all = 0;
+        for (uint32_t k = tid; k < nb; k += OCT_BLOCK) {
+            const uint32_t v = __ldcg(bsum + k);
+            all += v;
+            lower += k < blk ? v : 0u;
+        }
+        uint32_t lower_sum, all_sum;
+        block_excl_sum(lower, &lower_sum);
+        block_excl_sum(all, &all_sum);
+        const uint32_t ne = e + all_sum;
+        if (ne > cap || ne < e) {  // the next level does not fit: write nothing
+            if (blk == 0 && tid == 0) {
+                atomicOr(&sc->status, ST_NODE_OVERFLOW);
+                sc->oct_need = ne < e ? 0xffffffffu : ne;
+            }
+            return;
+        }
+        uint32_t carry = e + lower_sum;
+        for (uint32_t base = c0; base < c1; base += OCT_BLOCK) {
+            const uint32_t t = base + tid;
+            const bool valid = t < c1;
+            const uint32_t i = s + t;
+            const uint32_t nc = valid ? nchild[i] : 0u;
+            uint32_t round;
+            const uint32_t off = block_excl_sum(nc, &round);
+            if (valid) {
+                const uint32_t f = __ldcg(first + i), c = __ldcg(count + i);
+                if (i == 0 && c <= (uint32_t)NCRIT) flag[f] = 1u;
+                if (nc == 0) {
+                    child[i] = 0;
+                    topo[i] = make_uint2(f, c | LEAF_FLAG);
+                    if (c > (uint32_t)NCRIT)
+                        for (uint32_t r = 0; r < c; r += NCRIT) flag[f + r] = 1u;
+                } else {
+                    const uint32_t ch = carry + off;
+                    child[i] = ch;
+                    topo[i] = make_uint2(ch, nc);
+                    uint32_t b[9];
+                    child_bounds(key, f, c, l, b);
+                    uint32_t k = ch, run = 0;
+                    bool open = false;
+#pragma unroll
+                    for (int d = 0; d < 8; ++d) {
+                        if (b[d + 1] > b[d]) {
+                            const uint32_t cj = b[d + 1] - b[d];
+                            first[k] = b[d];
+                            count[k] = cj;
+                            level[k] = (uint32_t)(l + 1);
+                            parent[k] = i;
+                            ++k;
+                            if (c > (uint32_t)NCRIT) {
+                                if (cj > (uint32_t)NCRIT) {
+                                    open = false;
+                                } else if (!open || run + cj > (uint32_t)NCRIT) {
+                                    flag[b[d]] = 1u;
+                                    run = cj;
+                                    open = true;
+                                } else {
+                                    run += cj;
+                                }
+                            }
+                        }
+                    }
+                }
+            }
+            carry += round;
+        }
+        if (blk == 0 && tid == 0 && l + 2 <= MAX_LEVEL + 1) sc->oct_level[l + 2] = ne;
+        if (ne == e) {  // no children: level l is the deepest
+            if (blk == 0 && tid == 0) {
+                sc->oct_depth = (uint32_t)l;
+                sc->oct_nodes = e;
+            }
+            return;
+        }
+        if (!grid_barrier(sc)) return;
+        s = e;
+        e = ne;
+    }
 }
 
 // ---- upward pass (FP64) ----
-// Q order: xx, yy, zz, xy, xz, yz.  LEAVES: one launch over all nodes that
-// computes the leaves (they depend on nothing); otherwise one launch per
-// level, bottom-up, that combines the children of the level's internal
-// nodes.
-template <bool LEAVES>
-__global__ void __launch_bounds__(128) k_multipoles(
-    const double *__restrict__ pos, const double *__restrict__ mass, int64_t n,
-    const uint32_t *__restrict__ first, const uint32_t *__restrict__ count,
-    const uint32_t *__restrict__ child, const uint32_t *__restrict__ nchild, double *__restrict__ M,
-    double *__restrict__ com, double *__restrict__ Q, int64_t nn, int64_t s, int64_t m) {
-    int64_t t = blockIdx.x * 128ll + threadIdx.x;
-    if (t >= m) return;
-    int64_t i = s + t;
-    if ((nchild[i] == 0) != LEAVES) return;
-    double Ms = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
-    double q0 = 0.0, q1 = 0.0, q2 = 0.0, q3 = 0.0, q4 = 0.0, q5 = 0.0;
-    double cx, cy, cz;
-    uint32_t nc = nchild[i];
-    if (nc == 0) {
-        uint32_t f = first[i], c = count[i];
-        for (uint32_t j = f; j < f + c; ++j) {
-            double mj = mass[j];
-            Ms = __dadd_rn(Ms, mj);
-            sx = __dadd_rn(sx, __dmul_rn(mj, pos[j]));
-            sy = __dadd_rn(sy, __dmul_rn(mj, pos[n + j]));
-            sz = __dadd_rn(sz, __dmul_rn(mj, pos[2 * n + j]));
-        }
-        cx = __ddiv_rn(sx, Ms);
-        cy = __ddiv_rn(sy, Ms);
-        cz = __ddiv_rn(sz, Ms);
-        for (uint32_t j = f; j < f + c; ++j) {
-            double mj = mass[j];
-            double dx = __dsub_rn(pos[j], cx), dy = __dsub_rn(pos[n + j], cy),
-                   dz = __dsub_rn(pos[2 * n + j], cz);
-            double mx = __dmul_rn(mj, dx), my = __dmul_rn(mj, dy);
-            q0 = __dadd_rn(q0, __dmul_rn(mx, dx));
-            q1 = __dadd_rn(q1, __dmul_rn(my, dy));
-            q2 = __dadd_rn(q2, __dmul_rn(__dmul_rn(mj, dz), dz));
-            q3 = __dadd_rn(q3, __dmul_rn(mx, dy));
-            q4 = __dadd_rn(q4, __dmul_rn(mx, dz));
-            q5 = __dadd_rn(q5, __dmul_rn(my, dz));
-        }
-    } else {
-        uint32_t c0 = child[i];
-        for (uint32_t k = c0; k < c0 + nc; ++k) {
-            double Mk = M[k];
-            Ms = __dadd_rn(Ms, Mk);
-            sx = __dadd_rn(sx, __dmul_rn(Mk, com[k]));
-            sy = __dadd_rn(sy, __dmul_rn(Mk, com[nn + k]));
-            sz = __dadd_rn(sz, __dmul_rn(Mk, com[2 * nn + k]));
-        }
-        cx = __ddiv_rn(sx, Ms);
-        cy = __ddiv_rn(sy, Ms);
-        cz = __ddiv_rn(sz, Ms);
-        for (uint32_t k = c0; k < c0 + nc; ++k) {
-            double Mk = M[k];
-            double dx = __dsub_rn(com[k], cx), dy = __dsub_rn(com[nn + k], cy),
-                   dz = __dsub_rn(com[2 * nn + k], cz);
-            double mx = __dmul_rn(Mk, dx), my = __dmul_rn(Mk, dy);
-            q0 = __dadd_rn(q0, __dadd_rn(Q[k], __dmul_rn(mx, dx)));
-            q1 = __dadd_rn(q1, __dadd_rn(Q[nn + k], __dmul_rn(my, dy)));
-            q2 = __dadd_rn(q2, __dadd_rn(Q[2 * nn + k], __dmul_rn(__dmul_rn(Mk, dz), dz)));
-            q3 = __dadd_rn(q3, __dadd_rn(Q[3 * nn + k], __dmul_rn(mx, dy)));
-            q4 = __dadd_rn(q4, __dadd_rn(Q[4 * nn + k], __dmul_rn(mx, dz)));
-            q5 = __dadd_rn(q5, __dadd_rn(Q[5 * nn + k], __dmul_rn(my, dz)));
-        }
-    }
+// Q order: xx, yy, zz, xy, xz, yz.  Every FP64 operation is an explicit
+// round-to-nearest intrinsic in a fixed order, so the moments do not depend
+// on which thread computes a node or when.
+__device__ __forceinline__ void store_moments(double *__restrict__ M, double *__restrict__ com,
+                                              double *__restrict__ Q, int64_t nn, int64_t i,
+                                              double Ms, double cx, double cy, double cz,
+                                              const double q[6]) {
     M[i] = Ms;
     com[i] = cx;
     com[nn + i] = cy;
     com[2 * nn + i] = cz;
-    Q[i] = q0;
-    Q[nn + i] = q1;
-    Q[2 * nn + i] = q2;
-    Q[3 * nn + i] = q3;
-    Q[4 * nn + i] = q4;
-    Q[5 * nn + i] = q5;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) Q[k * nn + i] = q[k];
+}
+
+// A leaf from its particles: mass, centre of mass, and the second moment
+// about the centre of mass.
+__device__ void leaf_moments(const double *__restrict__ pos, const double *__restrict__ mass,
+                             int64_t n, uint32_t f, uint32_t c, double *__restrict__ M,
+                             double *__restrict__ com, double *__restrict__ Q, int64_t nn,
+                             int64_t i) {
+    double Ms = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
+    for (uint32_t j = f; j < f + c; ++j) {
+        const double mj = mass[j];
+        Ms = __dadd_rn(Ms, mj);
+        sx = __dadd_rn(sx, __dmul_rn(mj, pos[j]));
+        sy = __dadd_rn(sy, __dmul_rn(mj, pos[n + j]));
+        sz = __dadd_rn(sz, __dmul_rn(mj, pos[2 * n + j]));
+    }
+    const double cx = __ddiv_rn(sx, Ms), cy = __ddiv_rn(sy, Ms), cz = __ddiv_rn(sz, Ms);
+    double q[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (uint32_t j = f; j < f + c; ++j) {
+        const double mj = mass[j];
+        const double dx = __dsub_rn(pos[j], cx), dy = __dsub_rn(pos[n + j], cy),
+                     dz = __dsub_rn(pos[2 * n + j], cz);
+        const double mx = __dmul_rn(mj, dx), my = __dmul_rn(mj, dy);
+        q[0] = __dadd_rn(q[0], __dmul_rn(mx, dx));
+        q[1] = __dadd_rn(q[1], __dmul_rn(my, dy));
+        q[2] = __dadd_rn(q[2], __dmul_rn(__dmul_rn(mj, dz), dz));
+        q[3] = __dadd_rn(q[3], __dmul_rn(mx, dy));
+        q[4] = __dadd_rn(q[4], __dmul_rn(mx, dz));
+        q[5] = __dadd_rn(q[5], __dmul_rn(my, dz));
+    }
+    store_moments(M, com, Q, nn, i, Ms, cx, cy, cz, q);
+}
+
+// An internal node from its children by the parallel-axis rule.  The
+// children were written by other threads of this launch: read through L2.
+__device__ void internal_moments(uint32_t c0, uint32_t nc, double *__restrict__ M,
+                                 double *__restrict__ com, double *__restrict__ Q, int64_t nn,
+                                 int64_t i) {
+    double Ms = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
+    for (uint32_t k = c0; k < c0 + nc; ++k) {
+        const double Mk = __ldcg(M + k);
+        Ms = __dadd_rn(Ms, Mk);
+        sx = __dadd_rn(sx, __dmul_rn(Mk, __ldcg(com + k)));
+        sy = __dadd_rn(sy, __dmul_rn(Mk, __ldcg(com + nn + k)));
+        sz = __dadd_rn(sz, __dmul_rn(Mk, __ldcg(com + 2 * nn + k)));
+    }
+    const double cx = __ddiv_rn(sx, Ms), cy = __ddiv_rn(sy, Ms), cz = __ddiv_rn(sz, Ms);
+    double q[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (uint32_t k = c0; k < c0 + nc; ++k) {
+        const double Mk = __ldcg(M + k);
+        const double dx = __dsub_rn(__ldcg(com + k), cx), dy = __dsub_rn(__ldcg(com + nn + k), cy),
+                     dz = __dsub_rn(__ldcg(com + 2 * nn + k), cz);
+        const double mx = __dmul_rn(Mk, dx), my = __dmul_rn(Mk, dy);
+        q[0] = __dadd_rn(q[0], __dadd_rn(__ldcg(Q + k), __dmul_rn(mx, dx)));
+        q[1] = __dadd_rn(q[1], __dadd_rn(__ldcg(Q + nn + k), __dmul_rn(my, dy)));
+        q[2] = __dadd_rn(q[2], __dadd_rn(__ldcg(Q + 2 * nn + k), __dmul_rn(__dmul_rn(Mk, dz), dz)));
+        q[3] = __dadd_rn(q[3], __dadd_rn(__ldcg(Q + 3 * nn + k), __dmul_rn(mx, dy)));
+        q[4] = __dadd_rn(q[4], __dadd_rn(__ldcg(Q + 4 * nn + k), __dmul_rn(mx, dz)));
+        q[5] = __dadd_rn(q[5], __dadd_rn(__ldcg(Q + 5 * nn + k), __dmul_rn(my, dz)));
+    }
+    store_moments(M, com, Q, nn, i, Ms, cx, cy, cz, q);
+}
+
+// Level starts of the octree, passed by value to the upward pass.
+struct LevelTable {
+    int64_t start[MAX_LEVEL + 2];
+};
+
+// The whole upward pass in one cooperative launch: every leaf (grid-stride
+// over all nodes), then the internal nodes level by level from the deepest
+// up, a grid-wide barrier (bounded, see grid_barrier) between levels so
+// that a node's children are final when it combines them.  All threads of
+// a level work on its nodes side by side.
+__global__ void __launch_bounds__(128) k_upward(
+    const double *__restrict__ pos, const double *__restrict__ mass, int64_t n,
+    const uint32_t *__restrict__ first, const uint32_t *__restrict__ count,
+    const uint32_t *__restrict__ child, const uint32_t *__restrict__ nchild,
+    double *__restrict__ M, double *__restrict__ com, double *__restrict__ Q, int64_t nn,
+    LevelTable lv, int depth, DevScalars *sc) {
+    const int64_t stride = (int64_t)gridDim.x * 128;
+    for (int64_t i = blockIdx.x * 128ll + threadIdx.x; i < nn; i += stride)
+        if (nchild[i] == 0) leaf_moments(pos, mass, n, first[i], count[i], M, com, Q, nn, i);
+    for (int l = depth - 1; l >= 0; --l) {  // the deepest level holds leaves only
+        if (!grid_barrier(sc)) return;
+        for (int64_t i = lv.start[l] + blockIdx.x * 128ll + threadIdx.x; i < lv.start[l + 1];
+             i += stride) {
+            const uint32_t nc = nchild[i];
+            if (nc != 0) internal_moments(child[i], nc, M, com, Q, nn, i);
+        }
+    }
 }
 
 // ---- groups: runs of consecutive sibling cells of at most NCRIT particles
-// in all.  Each group start is flagged in a per-particle array, a scan
-// numbers them in particle order.
-// Group starts (flags at the first particle of each group).  A thread per
-// node; only nodes with more than NCRIT particles act.  Their children of at
-// most NCRIT particles are taken in key order and gathered greedily into runs
-// of at most NCRIT particles, a child with more than NCRIT ending the run
-// (its own children are grouped by its thread): each run is one group.  The
-// root is the one group when it holds at most NCRIT; a max-depth leaf with
-// more than NCRIT is cut into runs of NCRIT.
-__global__ void __launch_bounds__(256) k_group_flags(const uint32_t *__restrict__ first,
-                                                           const uint32_t *__restrict__ count,
-                                                           const uint32_t *__restrict__ nchild,
-                                                           const uint32_t *__restrict__ child,
-                                                           uint32_t *__restrict__ flag, int64_t nn) {
-    int64_t i = blockIdx.x * 256ll + threadIdx.x;
-    if (i >= nn) return;
-    const uint32_t c = count[i];
-    if (c <= (uint32_t)NCRIT) {
-        if (i == 0) flag[first[0]] = 1u;
-        return;
-    }
-    if (nchild[i] == 0) {
-        for (uint32_t s = 0; s < c; s += NCRIT) flag[first[i] + s] = 1u;
-        return;
-    }
-    uint32_t run = 0;
-    bool open = false;
-    for (uint32_t k = 0; k < nchild[i]; ++k) {
-        const uint32_t j = child[i] + k, cj = count[j];
-        if (cj > (uint32_t)NCRIT) {
-            open = false;
-            continue;
-        }
-        if (!open || run + cj > (uint32_t)NCRIT) {
-            flag[first[j]] = 1u;
-            run = cj;
-            open = true;
-        } else {
-            run += cj;
-        }
-    }
-}
-
+// in all, flagged at their first particle by k_octree; a scan numbers them
+// in particle order.
 __global__ void __launch_bounds__(256) k_group_write(const uint32_t *__restrict__ flag,
                                                      const uint32_t *__restrict__ gid, int64_t n,
                                                      uint32_t *__restrict__ gfirst) {
     int64_t i = blockIdx.x * 256ll + threadIdx.x;
     if (i >= n) return;
     if (flag[i]) gfirst[gid[i]] = (uint32_t)i;
-}
-
-// Order-preserving integer image of a double: for finite values (the input
-// check rejects the others) a < b exactly when key(a) < key(b), with -0 just
-// below +0.  Minima and maxima taken on the keys are therefore exact, and
-// run on the integer pipes instead of the FP64 one.
-__device__ __forceinline__ long long order_key(double v) {
-    const long long b = __double_as_longlong(v);
-    return b ^ ((b >> 63) & 0x7fffffffffffffffll);
-}
-__device__ __forceinline__ double from_order_key(long long k) {
-    return __longlong_as_double(k ^ ((k >> 63) & 0x7fffffffffffffffll));
 }
 
 // Per group: the FP64 box of the members, its FP32 centre (nearest), the
@@ -395,104 +500,103 @@ __global__ void __launch_bounds__(256) k_cell_pack(
 
 }  // namespace
 
-// Grow the node arrays to hold at least need nodes, keeping [0, keep).
-static int grow_nodes(bonsai_ctx *c, int64_t need, int64_t keep) {
+// Grow the node arrays to hold at least need nodes (contents not kept).
+static int grow_nodes(bonsai_ctx *c, int64_t need) {
     if ((size_t)need <= c->nd_first.cap) return BONSAI_OK;
-    size_t cap = std::max((size_t)need, c->nd_first.cap + c->nd_first.cap / 2);
+    const size_t cap = std::max((size_t)need, c->nd_first.cap + c->nd_first.cap / 2);
+    BGB_WAIT(c->stream);  // earlier work may still read the old arrays
     DBuf<uint32_t> *u32s[] = {&c->nd_first, &c->nd_count, &c->nd_child, &c->nd_nchild,
                               &c->nd_level, &c->nd_parent};
     for (DBuf<uint32_t> *b : u32s) {
-        uint32_t *p = nullptr;
-        if (cudaMalloc(&p, cap * sizeof(uint32_t)) != cudaSuccess) return BONSAI_ENOMEM;
-        if (keep > 0 && b->p)
-            cudaMemcpyAsync(p, b->p, keep * sizeof(uint32_t), cudaMemcpyDeviceToDevice, c->stream);
-        BGB_WAIT(c->stream);
         cudaFree(b->p);
-        b->p = p;
+        b->p = nullptr;
+        b->cap = 0;
+        if (cudaMalloc(&b->p, cap * sizeof(uint32_t)) != cudaSuccess) {
+            b->p = nullptr;
+            return BONSAI_ENOMEM;
+        }
         b->cap = cap;
     }
-    {
-        uint2 *p = nullptr;
-        if (cudaMalloc(&p, cap * sizeof(uint2)) != cudaSuccess) return BONSAI_ENOMEM;
-        if (keep > 0 && c->cell_topo.p)
-            cudaMemcpyAsync(p, c->cell_topo.p, keep * sizeof(uint2), cudaMemcpyDeviceToDevice,
-                            c->stream);
-        BGB_WAIT(c->stream);
-        cudaFree(c->cell_topo.p);
-        c->cell_topo.p = p;
-        c->cell_topo.cap = cap;
-    }
-    if (ensure(c->nd_scan, cap) || ensure(c->scan_tmp, scan_tmp_elems((int64_t)cap)))
+    cudaFree(c->cell_topo.p);
+    c->cell_topo.p = nullptr;
+    c->cell_topo.cap = 0;
+    if (cudaMalloc(&c->cell_topo.p, cap * sizeof(uint2)) != cudaSuccess) {
+        c->cell_topo.p = nullptr;
         return BONSAI_ENOMEM;
+    }
+    c->cell_topo.cap = cap;
     return BONSAI_OK;
 }
 
+// The octree and the walk-group starts (k_octree, one cooperative launch),
+// then the group numbering (a scan of the flags); one readback gives the
+// level table, the node count and the group count.  A launch that runs out
+// of node storage writes nothing past it and is repeated with larger
+// arrays.
 int build_octree(bonsai_ctx *c) {
     const int64_t n = c->n;
-    int rc = grow_nodes(c, std::max<int64_t>(1024, n / 2 + 64), 0);
+    int rc = grow_nodes(c, std::max<int64_t>(1024, n / 2 + 64));
     if (rc) return rc;
-    k_root<<<1, 1, 0, c->stream>>>(c->nd_first.p, c->nd_count.p, c->nd_level.p, c->nd_parent.p,
-                                   (uint32_t)n);
-    c->launches += 1;
-    c->level_start[0] = 0;
-    c->level_start[1] = 1;
-    int depth = 0;
-    for (int l = 0; l <= MAX_LEVEL; ++l) {
-        const int64_t s = c->level_start[l], e = c->level_start[l + 1], m = e - s;
-        if (m == 0) {
-            for (int k = l + 1; k <= MAX_LEVEL + 1; ++k) c->level_start[k] = e;
-            break;
-        }
-        depth = l;
-        if (l == MAX_LEVEL) {
-            k_mark_leaves<<<grid_for(m, 256), 256, 0, c->stream>>>(
-                c->nd_first.p, c->nd_count.p, c->nd_child.p, c->nd_nchild.p, c->cell_topo.p, s, m);
-            c->launches += 1;
-            c->level_start[l + 2 > MAX_LEVEL + 1 ? MAX_LEVEL + 1 : l + 2] = e;
-            break;
-        }
-        k_split_count<<<grid_for(m, 256), 256, 0, c->stream>>>(c->key.p, c->nd_first.p,
-                                                                 c->nd_count.p, c->nd_nchild.p,
-                                                                 c->nd_scan.p, s, m, l);
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_octree, OCT_BLOCK, 0) !=
+            cudaSuccess ||
+        per_sm < 1)
+        return BONSAI_ECUDA;
+    // enough blocks for the widest possible level (8 children per node of
+    // more than NLEAF particles), at most all resident ones
+    const int64_t widest = 8 * (n / (NLEAF + 1)) + 1;
+    const int64_t blocks =
+        std::min<int64_t>((int64_t)per_sm * c->sm_count, (widest + OCT_BLOCK - 1) / OCT_BLOCK);
+    if (ensure(c->nd_scan, (size_t)blocks)) return BONSAI_ENOMEM;
+    for (int attempt = 0;; ++attempt) {
+        BGB_CUDA(cudaMemsetAsync(c->grp_flag.p, 0, (n + 1) * sizeof(uint32_t), c->stream));
+        // the status word may carry the input check's bit: cleared only
+        // for a repeat, when it is known to be clean but for the overflow
+        if (attempt > 0) BGB_CUDA(cudaMemsetAsync(&c->dsc->status, 0, sizeof(int32_t), c->stream));
+        BGB_CUDA(cudaMemsetAsync(&c->dsc->bar_count, 0, 2 * sizeof(uint32_t), c->stream));
+        BGB_CUDA(cudaMemsetAsync(&c->dsc->oct_nodes, 0, 3 * sizeof(uint32_t), c->stream));
+        const uint64_t *key = c->key.p;
+        uint32_t nn32 = (uint32_t)n, cap = (uint32_t)std::min<size_t>(c->nd_first.cap, 0xffffffffu);
+        uint32_t *first = c->nd_first.p, *count = c->nd_count.p, *child = c->nd_child.p;
+        uint32_t *nchild = c->nd_nchild.p, *level = c->nd_level.p, *parent = c->nd_parent.p;
+        uint2 *topo = c->cell_topo.p;
+        uint32_t *flag = c->grp_flag.p, *bsum = c->nd_scan.p;
+        DevScalars *sc = c->dsc;
+        void *args[] = {&key, &nn32, &first, &count, &child, &nchild, &level, &parent,
+                        &topo, &flag, &cap, &bsum, &sc};
+        BGB_CUDA(cudaLaunchCooperativeKernel((const void *)k_octree, dim3((unsigned)blocks),
+                                             dim3(OCT_BLOCK), args, 0, c->stream));
         c->launches += 1;
-        // scan the child counts in place of a separate buffer: grp_flag is free here
-        exclusive_scan_u32(c, c->nd_scan.p, c->grp_flag.p, m, &c->dsc->level_count);
-        BGB_CUDA(cudaMemcpyAsync(&c->hsc->level_count, &c->dsc->level_count, sizeof(uint32_t),
-                                 cudaMemcpyDeviceToHost, c->stream));
+        uint32_t *gid = c->grp_flag.p + (n + 1);
+        exclusive_scan_u32(c, c->grp_flag.p, gid, n, &c->dsc->n_groups);
+        BGB_CUDA(cudaMemcpyAsync(c->hsc, c->dsc, sizeof(DevScalars), cudaMemcpyDeviceToHost,
+                                 c->stream));
         BGB_WAIT(c->stream);
-        const int64_t tot = c->hsc->level_count;
-        rc = grow_nodes(c, e + tot, e);
+        const int32_t st = c->hsc->status;
+        if (st & ST_BAD_INPUT) return BONSAI_EINVAL;
+        if (st & ST_TIMEOUT) return BONSAI_ETIMEOUT;
+        if (!(st & ST_NODE_OVERFLOW)) break;
+        const uint64_t need = c->hsc->oct_need;
+        if (need >= 0xffffffffull || attempt > 8) return BONSAI_ENOMEM;
+        rc = grow_nodes(c, (int64_t)std::max<uint64_t>(need + need / 2, 2 * c->nd_first.cap));
         if (rc) return rc;
-        k_split_write<<<grid_for(m, 256), 256, 0, c->stream>>>(
-            c->key.p, c->nd_first.p, c->nd_count.p, c->nd_child.p, c->nd_nchild.p, c->nd_level.p,
-            c->nd_parent.p, c->cell_topo.p, c->grp_flag.p, s, m, e, l);
-        c->launches += 1;
-        c->level_start[l + 2] = e + tot;
     }
-    c->depth = depth;
-    c->n_nodes = c->level_start[depth + 1];
-    for (int k = depth + 2; k <= MAX_LEVEL + 1; ++k) c->level_start[k] = c->n_nodes;
+    const DevScalars &h = *c->hsc;
+    c->depth = (int)h.oct_depth;
+    c->n_nodes = h.oct_nodes;
+    for (int k = 0; k <= c->depth + 1; ++k) c->level_start[k] = h.oct_level[k];
+    for (int k = c->depth + 2; k <= MAX_LEVEL + 1; ++k) c->level_start[k] = c->n_nodes;
+    c->n_groups = h.n_groups;
     return BONSAI_OK;
 }
 
 int build_groups(bonsai_ctx *c) {
-    const int64_t n = c->n, nn = c->n_nodes;
-    BGB_CUDA(cudaMemsetAsync(c->grp_flag.p, 0, (n + 1) * sizeof(uint32_t), c->stream));
-    k_group_flags<<<grid_for(nn, 256), 256, 0, c->stream>>>(c->nd_first.p, c->nd_count.p,
-                                                             c->nd_nchild.p, c->nd_child.p,
-                                                             c->grp_flag.p, nn);
-    c->launches += 1;
-    uint32_t *gid = c->grp_flag.p + (n + 1);
-    exclusive_scan_u32(c, c->grp_flag.p, gid, n, &c->dsc->n_groups);
-    BGB_CUDA(cudaMemcpyAsync(&c->hsc->n_groups, &c->dsc->n_groups, sizeof(uint32_t),
-                             cudaMemcpyDeviceToHost, c->stream));
-    BGB_WAIT(c->stream);
-    const int64_t ng = c->hsc->n_groups;
-    c->n_groups = ng;
+    const int64_t n = c->n, ng = c->n_groups;
     if (ensure(c->grp_first, ng) || ensure(c->grp_count, ng) || ensure(c->grp_centre, 3 * ng) ||
         ensure(c->grp_box, ng) || ensure(c->grp_half, ng) || ensure(c->grp_lo, ng) ||
         ensure(c->grp_npp, ng) || ensure(c->grp_npc, ng))
         return BONSAI_ENOMEM;
+    const uint32_t *gid = c->grp_flag.p + (n + 1);
     k_group_write<<<grid_for(n, 256), 256, 0, c->stream>>>(c->grp_flag.p, gid, n, c->grp_first.p);
     k_group_box<<<grid_for((ng + 31) / 32 * 32, 256), 256, 0, c->stream>>>(
         c->pos.p, n, c->grp_first.p, c->grp_count.p, ng, c->grp_centre.p, c->grp_box.p,
@@ -501,20 +605,29 @@ int build_groups(bonsai_ctx *c) {
     return BONSAI_OK;
 }
 
-void launch_multipoles(bonsai_ctx *c) {
-    const int64_t nn = c->n_nodes;
-    k_multipoles<true><<<grid_for(nn, 128), 128, 0, c->stream>>>(
-        c->pos.p, c->mass.p, c->n, c->nd_first.p, c->nd_count.p, c->nd_child.p, c->nd_nchild.p,
-        c->nd_M.p, c->nd_com.p, c->nd_Q.p, nn, 0, nn);
+int launch_multipoles(bonsai_ctx *c) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_upward, 128, 0) != cudaSuccess ||
+        per_sm < 1)
+        return BONSAI_ECUDA;
+    int64_t nn = c->n_nodes;
+    const int64_t blocks = std::min<int64_t>((int64_t)per_sm * c->sm_count, (nn + 127) / 128);
+    const double *pos = c->pos.p, *mass = c->mass.p;
+    int64_t n = c->n;
+    const uint32_t *first = c->nd_first.p, *count = c->nd_count.p, *child = c->nd_child.p,
+                   *nchild = c->nd_nchild.p;
+    double *M = c->nd_M.p, *com = c->nd_com.p, *Q = c->nd_Q.p;
+    LevelTable lv;
+    for (int k = 0; k <= MAX_LEVEL + 1; ++k) lv.start[k] = c->level_start[k];
+    int depth = c->depth;
+    DevScalars *sc = c->dsc;
+    BGB_CUDA(cudaMemsetAsync(&c->dsc->bar_count, 0, sizeof(uint32_t), c->stream));
+    void *args[] = {&pos, &mass, &n, &first, &count, &child, &nchild, &M, &com, &Q, &nn,
+                    &lv, &depth, &sc};
+    BGB_CUDA(cudaLaunchCooperativeKernel((const void *)k_upward, dim3((unsigned)blocks), dim3(128),
+                                         args, 0, c->stream));
     c->launches += 1;
-    for (int l = c->depth - 1; l >= 0; --l) {  // the deepest level holds leaves only
-        const int64_t s = c->level_start[l], m = c->level_start[l + 1] - s;
-        if (m <= 0) continue;
-        k_multipoles<false><<<grid_for(m, 128), 128, 0, c->stream>>>(
-            c->pos.p, c->mass.p, c->n, c->nd_first.p, c->nd_count.p, c->nd_child.p,
-            c->nd_nchild.p, c->nd_M.p, c->nd_com.p, c->nd_Q.p, nn, s, m);
-        c->launches += 1;
-    }
+    return BONSAI_OK;
 }
 
 void launch_body_pack(bonsai_ctx *c) {

@@ -42,6 +42,7 @@ struct __align__(16) WarpLists {
     int pid[RING];    // sorted index of the particle
     int cid[RING];    // node index of the cell
     float4 gbox, ghalf, glo;  // the group's box, read from here rather than kept in registers
+    uint2 tsel;               // first target and target count of the walk
 };
 
 // Targets of one group for the adjoint policy, two per record (targets 2p
@@ -73,6 +74,7 @@ struct WalkArgs {
     float *acc_c;  // caller order [3][n] or null
     float *pot_c;  // caller order [n] or null
     int accumulate;  // add to acc/pot instead of writing them
+    int parts;       // forward walk: pieces each group's targets are split into (1-8)
     const uint32_t *id;
     int32_t *gnpp, *gnpc;
     // adjoint inputs / outputs (sorted order)
@@ -106,6 +108,14 @@ __device__ __forceinline__ float4 lds_f4(const float4 *p) {
     float4 v;
     asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
                  : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"((unsigned)__cvta_generic_to_shared(p)));
+    return v;
+}
+
+__device__ __forceinline__ uint2 lds_u2(const uint2 *p) {
+    uint2 v;
+    asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];"
+                 : "=r"(v.x), "=r"(v.y)
                  : "r"((unsigned)__cvta_generic_to_shared(p)));
     return v;
 }
@@ -800,6 +810,7 @@ struct __align__(16) WarpLists64 {
     double px[RING], py[RING], pz[RING], pm[RING];
     int pid[RING];
     float4 gbox, ghalf, glo;
+    uint2 tsel;
 };
 
 __device__ __forceinline__ void pc_one64(double rx, double ry, double rz, double M, double qxx,
@@ -970,17 +981,21 @@ __device__ __forceinline__ void do_flush_pp(ListPolicy &pol, const WarpLists &L,
 // The traversal
 // ---------------------------------------------------------------------------
 
+// The walk of group g's box, evaluated on tcnt of its targets starting at
+// its target toff (the whole group, or one piece of it when the forward
+// walk splits small workloads over more warps).
 template <class P, class LT>
 __device__ __forceinline__ void walk_group(const WalkArgs &A, LT &L, WarpTargets *tgt, P &pol,
-                                           uint32_t g, uint32_t *fa, uint32_t *fb, int lane,
-                                           uint32_t lt) {
-    const uint32_t gf = A.gfirst[g], gc = A.gcount[g];
+                                           uint32_t g, uint32_t toff, uint32_t tcnt, uint32_t *fa,
+                                           uint32_t *fb, int lane, uint32_t lt) {
+    const uint32_t gf = A.gfirst[g] + toff, gc = tcnt;
     {
         const float4 box = A.gbox[g], clo = A.glo[g];
         if (lane == 0) {
             L.gbox = box;
             L.ghalf = A.ghalf[g];
             L.glo = clo;
+            L.tsel = make_uint2(gf, gc);
         }
         pol.begin(A, tgt, g, gf, gc, box, clo, lane);
     }
@@ -1084,12 +1099,13 @@ __device__ __forceinline__ void walk_group(const WalkArgs &A, LT &L, WarpTargets
     do_flush_pc(pol, L, (int)(pc_head & (RING - 1)), (int)(pc_tail - pc_head), lane);
     do_flush_pp(pol, L, (int)(pp_head & (RING - 1)), (int)(pp_tail - pp_head), lane);
     __syncwarp();
-    pol.finish(A, gf, gc, lane);
+    const uint2 ts = lds_u2(&L.tsel);  // (gf, gc), not kept in registers through the walk
+    pol.finish(A, ts.x, ts.y, lane);
     if (lane == 0) {
         if (A.gnpp) A.gnpp[g] = (int32_t)pp_tail;
         if (A.gnpc) A.gnpc[g] = (int32_t)pc_tail;
-        atomicAdd((unsigned long long *)&A.sc->n_pp, (unsigned long long)gc * pp_tail);
-        atomicAdd((unsigned long long *)&A.sc->n_pc, (unsigned long long)gc * pc_tail);
+        atomicAdd((unsigned long long *)&A.sc->n_pp, (unsigned long long)ts.y * pp_tail);
+        atomicAdd((unsigned long long *)&A.sc->n_pc, (unsigned long long)ts.y * pc_tail);
         atomicMax(&A.sc->max_frontier, (int)maxf);
         if (overflow) atomicOr(&A.sc->status, ST_OVERFLOW);
     }
@@ -1105,13 +1121,18 @@ __global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(const WalkArgs A) {
     const int64_t gw = (int64_t)blockIdx.x * WALK_WARPS + wib;
     uint32_t *fa = A.frontier + gw * 2 * FCAP;
     uint32_t *fb = fa + FCAP;
+    // work item w: piece w % parts of group w / parts
     while (true) {
-        uint32_t g = 0;
-        if (lane == 0) g = atomicAdd(&A.sc->group_counter, 1u);
-        g = __shfl_sync(0xffffffffu, g, 0);
-        if (g >= A.ngroups) break;
+        uint32_t w = 0;
+        if (lane == 0) w = atomicAdd(&A.sc->group_counter, 1u);
+        w = __shfl_sync(0xffffffffu, w, 0);
+        const uint32_t parts = (uint32_t)A.parts;
+        if (w >= (uint32_t)A.ngroups * parts) break;
+        const uint32_t g = w / parts, piece = w - g * parts;
+        const uint32_t gc = A.gcount[g], per = (gc + parts - 1u) / parts, tf = piece * per;
+        if (tf >= gc) continue;
         ForwardPolicy<SELF> pol;
-        walk_group(A, lists[wib], nullptr, pol, g, fa, fb, lane, lt);
+        walk_group(A, lists[wib], nullptr, pol, g, tf, min(per, gc - tf), fa, fb, lane, lt);
     }
 }
 
@@ -1135,7 +1156,7 @@ __global__ void __launch_bounds__(WALK_WARPS * 32, 4) k_walk_adjoint(const WalkA
         pol.part_adj = A.part_adj;
         pol.nn = A.nn;
         pol.W = &scratch[wib];
-        walk_group(A, lists[wib], &targets[wib], pol, g, fa, fb, lane, lt);
+        walk_group(A, lists[wib], &targets[wib], pol, g, 0u, A.gcount[g], fa, fb, lane, lt);
     }
 }
 
@@ -1153,7 +1174,7 @@ __global__ void __launch_bounds__(WALK_WARPS * 32) k_walk_lists(const WalkArgs A
         g = __shfl_sync(0xffffffffu, g, 0);
         if (g >= A.ngroups) break;
         ListPolicy pol;
-        walk_group(A, lists[wib], nullptr, pol, g, fa, fb, lane, lt);
+        walk_group(A, lists[wib], nullptr, pol, g, 0u, A.gcount[g], fa, fb, lane, lt);
     }
 }
 
@@ -1171,7 +1192,7 @@ __global__ void __launch_bounds__(WALK_WARPS * 32) k_walk_fp64(const WalkArgs A)
         g = __shfl_sync(0xffffffffu, g, 0);
         if (g >= A.ngroups) break;
         Fp64Policy pol;
-        walk_group(A, lists[wib], nullptr, pol, g, fa, fb, lane, lt);
+        walk_group(A, lists[wib], nullptr, pol, g, 0u, A.gcount[g], fa, fb, lane, lt);
     }
 }
 
@@ -1186,6 +1207,7 @@ void fill_args(bonsai_ctx *c, float eps, WalkArgs &a) {
     a.src_hi = c->body_hi.p;
     a.src_lo = c->body_lo.p;
     a.accumulate = 0;
+    a.parts = 1;
     a.gfirst = c->grp_first.p;
     a.gcount = c->grp_count.p;
     a.gbox = c->grp_box.p;
@@ -1256,19 +1278,31 @@ static int launch_blocks(const void *fn, bonsai_ctx *c) {
     return blocks < cap ? blocks : cap;
 }
 
+// Pieces per group for the forward walk: when the groups are fewer than the
+// resident warps (small N), each group's targets are split over up to
+// MAX_PIECES warps that walk the same box (the same lists), so more warps
+// share the evaluation; every target still sums its list in one warp.
+constexpr int MAX_PIECES = 8;
+static int walk_parts(int64_t ngroups, int blocks) {
+    const int64_t warps = (int64_t)blocks * WALK_WARPS;
+    const int64_t p = ngroups > 0 ? warps / ngroups : 1;
+    return p >= MAX_PIECES ? MAX_PIECES : (p >= 1 ? (int)p : 1);
+}
+
 int walk_force(bonsai_ctx *c, float theta, float eps, float *acc_c, float *pot_c) {
     const bool mask_self = !(eps > 0.0f) || !(theta < 0.57f);
     WalkArgs a;
     fill_args(c, eps, a);
     a.acc_c = acc_c;
     a.pot_c = pot_c;
+    const void *fn = mask_self ? (const void *)k_walk<SELF_MASK> : (const void *)k_walk<SELF_SUB>;
+    const int blocks = launch_blocks(fn, c);
+    a.parts = walk_parts(c->n_groups, blocks);
     cudaEventRecord(c->ev[8], c->stream);
     if (mask_self)
-        k_walk<SELF_MASK><<<launch_blocks((const void *)k_walk<SELF_MASK>, c), WALK_WARPS * 32, 0,
-                            c->stream>>>(a);
+        k_walk<SELF_MASK><<<blocks, WALK_WARPS * 32, 0, c->stream>>>(a);
     else
-        k_walk<SELF_SUB><<<launch_blocks((const void *)k_walk<SELF_SUB>, c), WALK_WARPS * 32, 0,
-                           c->stream>>>(a);
+        k_walk<SELF_SUB><<<blocks, WALK_WARPS * 32, 0, c->stream>>>(a);
     cudaEventRecord(c->ev[9], c->stream);
     c->launches += 1;
     return cudaPeekAtLastError() == cudaSuccess ? BONSAI_OK : BONSAI_ECUDA;
@@ -1288,9 +1322,10 @@ int walk_let(bonsai_ctx *dst, const LetTree &t, float eps) {
     a.src_lo = t.lo;
     a.nn = t.nn;
     a.accumulate = 1;
+    const int blocks = launch_blocks((const void *)k_walk<SELF_NONE>, dst);
+    a.parts = walk_parts(dst->n_groups, blocks);
     cudaEventRecord(dst->ev[8], dst->stream);
-    k_walk<SELF_NONE><<<launch_blocks((const void *)k_walk<SELF_NONE>, dst), WALK_WARPS * 32, 0,
-                        dst->stream>>>(a);
+    k_walk<SELF_NONE><<<blocks, WALK_WARPS * 32, 0, dst->stream>>>(a);
     cudaEventRecord(dst->ev[9], dst->stream);
     dst->launches += 1;
     return cudaPeekAtLastError() == cudaSuccess ? BONSAI_OK : BONSAI_ECUDA;
