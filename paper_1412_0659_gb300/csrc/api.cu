@@ -149,8 +149,20 @@ int read_scalars(bonsai_ctx *c) {
 
 // Keys, sort, gather, octree, groups, multipoles, particle records.
 // from_caller: pos/mass are the caller's (caller order); otherwise the
-// context's own state is re-sorted in place (tree_step).
+// context's own state is re-sorted in place (tree_step): by default its keys
+// are written in slot order and equal-key runs put in caller order after the
+// sort; exact_ties writes each key at its caller index instead (taken when a
+// run of equal keys is too long for the fix-up), and both give the (key,
+// caller index) order.
+static int rebuild_impl(bonsai_ctx *c, const double *pos, const double *mass, bool from_caller,
+                        bool exact_ties);
+
 int rebuild(bonsai_ctx *c, const double *pos, const double *mass, bool from_caller) {
+    return rebuild_impl(c, pos, mass, from_caller, false);
+}
+
+static int rebuild_impl(bonsai_ctx *c, const double *pos, const double *mass, bool from_caller,
+                        bool exact_ties) {
     const int64_t n = c->n;
     BGB_CUDA(cudaMemsetAsync(c->dsc, 0, sizeof(DevScalars), c->stream));
     BGB_CUDA(cudaEventRecord(c->ev[0], c->stream));
@@ -158,18 +170,26 @@ int rebuild(bonsai_ctx *c, const double *pos, const double *mass, bool from_call
     const double *m = from_caller ? mass : c->mass.p;
     launch_bbox(c, p, m, n);  // also checks the input
     if (c->fixed_cube) launch_set_cube(c);
-    if (from_caller) {
-        launch_keys(c, p, n);
-    } else {
+    const bool scatter = !from_caller && exact_ties;
+    if (scatter) {
         if (ensure(c->inv_id, (size_t)n)) return BONSAI_ENOMEM;
         launch_keys(c, p, n, c->id.p, c->inv_id.p);
+    } else {
+        launch_keys(c, p, n);
     }
     radix_sort_pairs(c, n);
-    if (from_caller) launch_gather_build(c, pos, mass, n); else launch_gather_step(c, n);
+    if (from_caller) {
+        launch_gather_build(c, pos, mass, n);
+    } else {
+        if (!scatter) launch_fix_ties(c, n);
+        launch_gather_step(c, n, scatter);
+    }
     BGB_CUDA(cudaEventRecord(c->ev[1], c->stream));
     BGB_CUDA(cudaGetLastError());
     c->have_tree = false;
     int rc = build_octree(c);
+    if (rc == BUILD_RETRY_EXACT && !from_caller && !exact_ties)
+        return rebuild_impl(c, nullptr, nullptr, false, true);
     if (rc) return rc;
     if ((rc = node_buffers(c))) return rc;
     if ((rc = build_groups(c))) return rc;
@@ -289,7 +309,7 @@ void bonsai_destroy(bonsai_ctx *c) {
     for (int k = 0; k < 2; ++k)
         if (c->stage[k]) cudaFreeHost(c->stage[k]);
     release(c->nd_first); release(c->nd_count); release(c->nd_child); release(c->nd_nchild);
-    release(c->nd_level); release(c->nd_parent); release(c->nd_scan);
+    release(c->nd_level); release(c->nd_parent); release(c->nd_scan); release(c->nd_arrive);
     release(c->nd_M); release(c->nd_com); release(c->nd_Q);
     release(c->cell_mac); release(c->cell_topo); release(c->cell_a); release(c->cell_b);
     release(c->cell_c);

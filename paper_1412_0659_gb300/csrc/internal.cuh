@@ -21,6 +21,8 @@ constexpr int ST_BAD_INPUT = 1;      // non-finite position or mass <= 0
 constexpr int ST_OVERFLOW = 2;       // a walk frontier overflowed
 constexpr int ST_NODE_OVERFLOW = 4;  // node storage too small (host regrows)
 constexpr int ST_TIMEOUT = 8;        // a bounded grid-barrier wait gave up
+constexpr int ST_LONG_TIES = 16;     // a run of equal keys too long to fix in place
+constexpr int BUILD_RETRY_EXACT = 1; // build_octree: sort again by the exact path
 
 // Order-preserving integer image of a double: for finite values (the input
 // check rejects the others) a < b exactly when key(a) < key(b), with -0 just
@@ -112,6 +114,7 @@ struct bonsai_ctx {
     // nodes (breadth-first)
     bgb::DBuf<uint32_t> nd_first, nd_count, nd_child, nd_nchild, nd_level, nd_parent;
     bgb::DBuf<uint32_t> nd_scan;     // octree build: per-block child counts
+    bgb::DBuf<uint32_t> nd_arrive;   // one-launch upward pass: finished children per node
     bgb::DBuf<double> nd_M;          // [nn]
     bgb::DBuf<double> nd_com;        // [3][nn]
     bgb::DBuf<double> nd_Q;          // [6][nn]
@@ -201,7 +204,8 @@ void radix_sort_pairs(bonsai_ctx *c, int64_t n);  // sorts key/val in place (pin
 void exclusive_scan_u32(bonsai_ctx *c, const uint32_t *in, uint32_t *out, int64_t n,
                         uint32_t *total_dev);
 void launch_gather_build(bonsai_ctx *c, const double *pos, const double *mass, int64_t n);
-void launch_gather_step(bonsai_ctx *c, int64_t n);
+void launch_gather_step(bonsai_ctx *c, int64_t n, bool exact);
+void launch_fix_ties(bonsai_ctx *c, int64_t n);
 // tree.cu
 int build_octree(bonsai_ctx *c);
 int build_groups(bonsai_ctx *c);

@@ -317,16 +317,25 @@ __global__ void __launch_bounds__(256) k_gather_build(const double *__restrict__
     }
 }
 
-// Re-sort of the context's state: perm holds the caller index of each new
-// slot, inv the old slot of each caller index.
+// Re-sort of the context's state.  With inv (the exact path), perm holds the
+// caller index of each new slot and inv the old slot of each caller index;
+// without it, perm holds the old slot of each new slot and id_o the caller
+// index of each old slot.
 __global__ void __launch_bounds__(256) k_gather_step(
     const double *__restrict__ pos_o, const double *__restrict__ vel_o,
     const double *__restrict__ mass_o, const uint32_t *__restrict__ inv,
-    const uint32_t *__restrict__ perm, int64_t n, double *__restrict__ pos,
-    double *__restrict__ vel, double *__restrict__ mass, uint32_t *__restrict__ id) {
+    const uint32_t *__restrict__ id_o, const uint32_t *__restrict__ perm, int64_t n,
+    double *__restrict__ pos, double *__restrict__ vel, double *__restrict__ mass,
+    uint32_t *__restrict__ id) {
     for (int64_t i = blockIdx.x * 256ll + threadIdx.x; i < n; i += (int64_t)gridDim.x * 256) {
-        const uint32_t c = perm[i];
-        const uint32_t j = inv[c];
+        uint32_t c, j;
+        if (inv) {
+            c = perm[i];
+            j = inv[c];
+        } else {
+            j = perm[i];
+            c = id_o[j];
+        }
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             pos[d * n + i] = pos_o[d * n + j];
@@ -334,6 +343,38 @@ __global__ void __launch_bounds__(256) k_gather_step(
         }
         mass[i] = mass_o[j];
         id[i] = c;
+    }
+}
+
+// Ties of the slot-order sort: the sort ran on (key, old slot) pairs in
+// old-slot order, so equal keys came out in old-slot order; each run of
+// equal keys is put in caller-index order (id: caller index of each old
+// slot), which makes the result the (key, caller index) order.  A run of
+// more than TIE_RUN_MAX pairs is left alone and reported (ST_LONG_TIES):
+// the caller then sorts again by the exact path.
+constexpr int TIE_RUN_MAX = 32;
+__global__ void __launch_bounds__(256) k_fix_ties(const uint64_t *__restrict__ key,
+                                                  uint32_t *__restrict__ val,
+                                                  const uint32_t *__restrict__ id, int64_t n,
+                                                  int32_t *status) {
+    for (int64_t i = blockIdx.x * 256ll + threadIdx.x; i < n; i += (int64_t)gridDim.x * 256) {
+        const uint64_t k = key[i];
+        if ((i > 0 && key[i - 1] == k) || i + 1 >= n || key[i + 1] != k) continue;
+        int64_t e = i + 2;  // [i, e): the run starting at i
+        while (e < n && e - i <= TIE_RUN_MAX && key[e] == k) ++e;
+        if (e - i > TIE_RUN_MAX) {
+            atomicOr(status, ST_LONG_TIES);
+            continue;
+        }
+        for (int64_t a = i + 1; a < e; ++a) {  // insertion sort by caller index
+            const uint32_t v = val[a], cv = id[v];
+            int64_t b = a - 1;
+            while (b >= i && id[val[b]] > cv) {
+                val[b + 1] = val[b];
+                --b;
+            }
+            val[b + 1] = v;
+        }
     }
 }
 
@@ -394,10 +435,17 @@ void launch_gather_build(bonsai_ctx *c, const double *pos, const double *mass, i
     c->launches += 1;
 }
 
-void launch_gather_step(bonsai_ctx *c, int64_t n) {
+void launch_fix_ties(bonsai_ctx *c, int64_t n) {
+    k_fix_ties<<<grid_for(n, 256, c->sm_count * 16), 256, 0, c->stream>>>(c->key.p, c->val.p,
+                                                                         c->id.p, n,
+                                                                         &c->dsc->status);
+    c->launches += 1;
+}
+
+void launch_gather_step(bonsai_ctx *c, int64_t n, bool exact) {
     k_gather_step<<<grid_for(n, 256, c->sm_count * 16), 256, 0, c->stream>>>(
-        c->pos.p, c->vel.p, c->mass.p, c->inv_id.p, c->val.p, n, c->pos2.p, c->vel2.p, c->mass2.p,
-        c->id2.p);
+        c->pos.p, c->vel.p, c->mass.p, exact ? c->inv_id.p : nullptr, c->id.p, c->val.p, n,
+        c->pos2.p, c->vel2.p, c->mass2.p, c->id2.p);
     c->launches += 1;
     std::swap(c->pos, c->pos2);
     std::swap(c->vel, c->vel2);

@@ -11,10 +11,12 @@
 // separate the counting and writing phases of each level, and the host
 // reads the level table once at the end.
 //
-// The upward pass is one cooperative launch: leaves from their particles,
-// then internal nodes level by level from their children by the
-// parallel-axis rule; every FP64 operation is an explicit round-to-nearest
-// intrinsic in a fixed order.
+// The upward pass computes every leaf in one launch (a leaf needs only its
+// particles), then visits the levels bottom-up, where internal nodes
+// combine their children by the parallel-axis rule; small trees take it in
+// one launch instead (each internal node computed by the thread of its last
+// finished child).  Every FP64 operation is an explicit round-to-nearest
+// intrinsic in a fixed order, so both give the same moments.
 #include <math.h>
 
 #include <algorithm>
@@ -257,9 +259,87 @@ __global__ void __launch_bounds__(OCT_BLOCK) k_octree(
 }
 
 // ---- upward pass (FP64) ----
-// Q order: xx, yy, zz, xy, xz, yz.  Every FP64 operation is an explicit
-// round-to-nearest intrinsic in a fixed order, so the moments do not depend
-// on which thread computes a node or when.
+// Q order: xx, yy, zz, xy, xz, yz.  LEAVES: one launch over all nodes that
+// computes the leaves (they depend on nothing); otherwise one launch per
+// level, bottom-up, that combines the children of the level's internal
+// nodes.
+template <bool LEAVES>
+__global__ void __launch_bounds__(128) k_multipoles(
+    const double *__restrict__ pos, const double *__restrict__ mass, int64_t n,
+    const uint32_t *__restrict__ first, const uint32_t *__restrict__ count,
+    const uint32_t *__restrict__ child, const uint32_t *__restrict__ nchild, double *__restrict__ M,
+    double *__restrict__ com, double *__restrict__ Q, int64_t nn, int64_t s, int64_t m) {
+    int64_t t = blockIdx.x * 128ll + threadIdx.x;
+    if (t >= m) return;
+    int64_t i = s + t;
+    if ((nchild[i] == 0) != LEAVES) return;
+    double Ms = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
+    double q0 = 0.0, q1 = 0.0, q2 = 0.0, q3 = 0.0, q4 = 0.0, q5 = 0.0;
+    double cx, cy, cz;
+    uint32_t nc = nchild[i];
+    if (nc == 0) {
+        uint32_t f = first[i], c = count[i];
+        for (uint32_t j = f; j < f + c; ++j) {
+            double mj = mass[j];
+            Ms = __dadd_rn(Ms, mj);
+            sx = __dadd_rn(sx, __dmul_rn(mj, pos[j]));
+            sy = __dadd_rn(sy, __dmul_rn(mj, pos[n + j]));
+            sz = __dadd_rn(sz, __dmul_rn(mj, pos[2 * n + j]));
+        }
+        cx = __ddiv_rn(sx, Ms);
+        cy = __ddiv_rn(sy, Ms);
+        cz = __ddiv_rn(sz, Ms);
+        for (uint32_t j = f; j < f + c; ++j) {
+            double mj = mass[j];
+            double dx = __dsub_rn(pos[j], cx), dy = __dsub_rn(pos[n + j], cy),
+                   dz = __dsub_rn(pos[2 * n + j], cz);
+            double mx = __dmul_rn(mj, dx), my = __dmul_rn(mj, dy);
+            q0 = __dadd_rn(q0, __dmul_rn(mx, dx));
+            q1 = __dadd_rn(q1, __dmul_rn(my, dy));
+            q2 = __dadd_rn(q2, __dmul_rn(__dmul_rn(mj, dz), dz));
+            q3 = __dadd_rn(q3, __dmul_rn(mx, dy));
+            q4 = __dadd_rn(q4, __dmul_rn(mx, dz));
+            q5 = __dadd_rn(q5, __dmul_rn(my, dz));
+        }
+    } else {
+        uint32_t c0 = child[i];
+        for (uint32_t k = c0; k < c0 + nc; ++k) {
+            double Mk = M[k];
+            Ms = __dadd_rn(Ms, Mk);
+            sx = __dadd_rn(sx, __dmul_rn(Mk, com[k]));
+            sy = __dadd_rn(sy, __dmul_rn(Mk, com[nn + k]));
+            sz = __dadd_rn(sz, __dmul_rn(Mk, com[2 * nn + k]));
+        }
+        cx = __ddiv_rn(sx, Ms);
+        cy = __ddiv_rn(sy, Ms);
+        cz = __ddiv_rn(sz, Ms);
+        for (uint32_t k = c0; k < c0 + nc; ++k) {
+            double Mk = M[k];
+            double dx = __dsub_rn(com[k], cx), dy = __dsub_rn(com[nn + k], cy),
+                   dz = __dsub_rn(com[2 * nn + k], cz);
+            double mx = __dmul_rn(Mk, dx), my = __dmul_rn(Mk, dy);
+            q0 = __dadd_rn(q0, __dadd_rn(Q[k], __dmul_rn(mx, dx)));
+            q1 = __dadd_rn(q1, __dadd_rn(Q[nn + k], __dmul_rn(my, dy)));
+            q2 = __dadd_rn(q2, __dadd_rn(Q[2 * nn + k], __dmul_rn(__dmul_rn(Mk, dz), dz)));
+            q3 = __dadd_rn(q3, __dadd_rn(Q[3 * nn + k], __dmul_rn(mx, dy)));
+            q4 = __dadd_rn(q4, __dadd_rn(Q[4 * nn + k], __dmul_rn(mx, dz)));
+            q5 = __dadd_rn(q5, __dadd_rn(Q[5 * nn + k], __dmul_rn(my, dz)));
+        }
+    }
+    M[i] = Ms;
+    com[i] = cx;
+    com[nn + i] = cy;
+    com[2 * nn + i] = cz;
+    Q[i] = q0;
+    Q[nn + i] = q1;
+    Q[2 * nn + i] = q2;
+    Q[3 * nn + i] = q3;
+    Q[4 * nn + i] = q4;
+    Q[5 * nn + i] = q5;
+}
+
+// Small trees: the whole upward pass in one launch, with the same FP64
+// operations in the same order as k_multipoles.
 __device__ __forceinline__ void store_moments(double *__restrict__ M, double *__restrict__ com,
                                               double *__restrict__ Q, int64_t nn, int64_t i,
                                               double Ms, double cx, double cy, double cz,
@@ -333,32 +413,28 @@ __device__ void internal_moments(uint32_t c0, uint32_t nc, double *__restrict__ 
     store_moments(M, com, Q, nn, i, Ms, cx, cy, cz, q);
 }
 
-// Level starts of the octree, passed by value to the upward pass.
-struct LevelTable {
-    int64_t start[MAX_LEVEL + 2];
-};
-
-// The whole upward pass in one cooperative launch: every leaf (grid-stride
-// over all nodes), then the internal nodes level by level from the deepest
-// up, a grid-wide barrier (bounded, see grid_barrier) between levels so
-// that a node's children are final when it combines them.  All threads of
-// a level work on its nodes side by side.
+// A thread per node: a leaf's thread computes the leaf, then climbs.  At
+// each parent it counts itself in (arrive, zeroed by the caller); the child
+// that arrives last, which finds every sibling finished, computes the parent
+// and climbs on; the others stop.  Nothing waits, and each node is computed
+// once, after all its children.
 __global__ void __launch_bounds__(128) k_upward(
     const double *__restrict__ pos, const double *__restrict__ mass, int64_t n,
     const uint32_t *__restrict__ first, const uint32_t *__restrict__ count,
     const uint32_t *__restrict__ child, const uint32_t *__restrict__ nchild,
-    double *__restrict__ M, double *__restrict__ com, double *__restrict__ Q, int64_t nn,
-    LevelTable lv, int depth, DevScalars *sc) {
-    const int64_t stride = (int64_t)gridDim.x * 128;
-    for (int64_t i = blockIdx.x * 128ll + threadIdx.x; i < nn; i += stride)
-        if (nchild[i] == 0) leaf_moments(pos, mass, n, first[i], count[i], M, com, Q, nn, i);
-    for (int l = depth - 1; l >= 0; --l) {  // the deepest level holds leaves only
-        if (!grid_barrier(sc)) return;
-        for (int64_t i = lv.start[l] + blockIdx.x * 128ll + threadIdx.x; i < lv.start[l + 1];
-             i += stride) {
-            const uint32_t nc = nchild[i];
-            if (nc != 0) internal_moments(child[i], nc, M, com, Q, nn, i);
-        }
+    const uint32_t *__restrict__ parent, double *__restrict__ M, double *__restrict__ com,
+    double *__restrict__ Q, int64_t nn, uint32_t *__restrict__ arrive) {
+    const int64_t i = blockIdx.x * 128ll + threadIdx.x;
+    if (i >= nn || nchild[i] != 0) return;
+    leaf_moments(pos, mass, n, first[i], count[i], M, com, Q, nn, i);
+    uint32_t node = (uint32_t)i;
+    while (node != 0u) {
+        const uint32_t p = parent[node];
+        __threadfence();  // this node's moments before the arrival
+        if (atomicAdd(arrive + p, 1u) != nchild[p] - 1u) break;
+        __threadfence();  // the siblings' moments after it
+        internal_moments(child[p], nchild[p], M, com, Q, nn, p);
+        node = p;
     }
 }
 
@@ -575,6 +651,7 @@ int build_octree(bonsai_ctx *c) {
         const int32_t st = c->hsc->status;
         if (st & ST_BAD_INPUT) return BONSAI_EINVAL;
         if (st & ST_TIMEOUT) return BONSAI_ETIMEOUT;
+        if (st & ST_LONG_TIES) return BUILD_RETRY_EXACT;  // the order is not final
         if (!(st & ST_NODE_OVERFLOW)) break;
         const uint64_t need = c->hsc->oct_need;
         if (need >= 0xffffffffull || attempt > 8) return BONSAI_ENOMEM;
@@ -605,28 +682,36 @@ int build_groups(bonsai_ctx *c) {
     return BONSAI_OK;
 }
 
+// Below UPWARD_ONE_LAUNCH nodes the one-launch pass (k_upward) is used:
+// there launch latency dominates.  Above, its climbing threads would run
+// alone in their warps on the scarce FP64 pipe, and a launch per level,
+// with every lane of a warp on its own node, is faster.
+constexpr int64_t UPWARD_ONE_LAUNCH = 1 << 16;
+
 int launch_multipoles(bonsai_ctx *c) {
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_upward, 128, 0) != cudaSuccess ||
-        per_sm < 1)
-        return BONSAI_ECUDA;
-    int64_t nn = c->n_nodes;
-    const int64_t blocks = std::min<int64_t>((int64_t)per_sm * c->sm_count, (nn + 127) / 128);
-    const double *pos = c->pos.p, *mass = c->mass.p;
-    int64_t n = c->n;
-    const uint32_t *first = c->nd_first.p, *count = c->nd_count.p, *child = c->nd_child.p,
-                   *nchild = c->nd_nchild.p;
-    double *M = c->nd_M.p, *com = c->nd_com.p, *Q = c->nd_Q.p;
-    LevelTable lv;
-    for (int k = 0; k <= MAX_LEVEL + 1; ++k) lv.start[k] = c->level_start[k];
-    int depth = c->depth;
-    DevScalars *sc = c->dsc;
-    BGB_CUDA(cudaMemsetAsync(&c->dsc->bar_count, 0, sizeof(uint32_t), c->stream));
-    void *args[] = {&pos, &mass, &n, &first, &count, &child, &nchild, &M, &com, &Q, &nn,
-                    &lv, &depth, &sc};
-    BGB_CUDA(cudaLaunchCooperativeKernel((const void *)k_upward, dim3((unsigned)blocks), dim3(128),
-                                         args, 0, c->stream));
+    const int64_t nn = c->n_nodes;
+    if (nn <= UPWARD_ONE_LAUNCH) {
+        if (ensure(c->nd_arrive, (size_t)nn)) return BONSAI_ENOMEM;
+        BGB_CUDA(cudaMemsetAsync(c->nd_arrive.p, 0, nn * sizeof(uint32_t), c->stream));
+        k_upward<<<grid_for(nn, 128), 128, 0, c->stream>>>(
+            c->pos.p, c->mass.p, c->n, c->nd_first.p, c->nd_count.p, c->nd_child.p,
+            c->nd_nchild.p, c->nd_parent.p, c->nd_M.p, c->nd_com.p, c->nd_Q.p, nn,
+            c->nd_arrive.p);
+        c->launches += 1;
+        return BONSAI_OK;
+    }
+    k_multipoles<true><<<grid_for(nn, 128), 128, 0, c->stream>>>(
+        c->pos.p, c->mass.p, c->n, c->nd_first.p, c->nd_count.p, c->nd_child.p, c->nd_nchild.p,
+        c->nd_M.p, c->nd_com.p, c->nd_Q.p, nn, 0, nn);
     c->launches += 1;
+    for (int l = c->depth - 1; l >= 0; --l) {  // the deepest level holds leaves only
+        const int64_t s = c->level_start[l], m = c->level_start[l + 1] - s;
+        if (m <= 0) continue;
+        k_multipoles<false><<<grid_for(m, 128), 128, 0, c->stream>>>(
+            c->pos.p, c->mass.p, c->n, c->nd_first.p, c->nd_count.p, c->nd_child.p,
+            c->nd_nchild.p, c->nd_M.p, c->nd_com.p, c->nd_Q.p, nn, s, m);
+        c->launches += 1;
+    }
     return BONSAI_OK;
 }
 

@@ -77,3 +77,43 @@ def test_free_drift_and_single_particle():
     g.close()
     assert torch.equal(pos.cpu(), torch.tensor([[1.0], [2.0], [3.0]], dtype=torch.float64) + 2.0 * v0.cpu())
     assert torch.equal(vel.cpu(), v0.cpu())
+
+
+@pytest.mark.parametrize("copies", [3, 40])
+def test_a_step_orders_equal_keys_by_caller_index_like_a_fresh_build(copies):
+    """Coincident copies share a key.  After a step (which sorts the
+    key-ordered state: runs of at most 32 equal keys are put in caller
+    order after the sort, longer runs take the path that writes each key at
+    its caller index), the order must be the (key, caller index) order that
+    a fresh build of the same state gives, and every later tree with it.
+    Copies of one particle get the same velocity and feel the same force,
+    so they stay coincident."""
+    from gpu_helpers import DEV
+    from paper_1412_0659_gb300 import TreeGravity
+    m = workloads.plummer(4096, seed=31)
+    rng = np.random.default_rng(32)
+    src = rng.choice(m.n, 12, replace=False)
+    pos = np.concatenate([m.pos] + [m.pos[:, src]] * copies, axis=1)
+    vel = np.concatenate([m.vel] + [m.vel[:, src]] * copies, axis=1)
+    mass = np.concatenate([m.mass] + [m.mass[src]] * copies)
+    shuffle = rng.permutation(pos.shape[1])  # copies spread over the caller indices
+    pos, vel, mass = pos[:, shuffle], vel[:, shuffle], mass[shuffle]
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+    with TreeGravity(G=1.0, theta=0.4, eps=0.01) as g:
+        g.build(t(pos), t(mass))
+        g.set_velocities(t(vel))
+        g.step(1.0 / 64)
+        g.step(1.0 / 64)
+        d_step = g.debug()
+        p1, v1, m1 = g.state()
+        keys = d_step["keys"].cpu().numpy().view(np.uint64)
+        perm = d_step["perm"].cpu().numpy()
+        edges = np.concatenate([[0], np.flatnonzero(np.diff(keys)) + 1, [keys.size]])
+        assert np.diff(edges).max() >= copies + 1  # the copies did tie
+        with TreeGravity(G=1.0, theta=0.4, eps=0.01) as f:
+            f.build(p1, m1)
+            d_build = f.debug()
+    assert np.array_equal(keys, d_build["keys"].cpu().numpy().view(np.uint64))
+    assert np.array_equal(perm, d_build["perm"].cpu().numpy())
+    for k in ("first", "count", "child", "nchild"):
+        assert torch.equal(d_step["nodes"][k], d_build["nodes"][k]), k
