@@ -411,7 +411,7 @@ int radix_sort_pairs_into(cudaStream_t s, int sm_count, int64_t n, uint64_t *ka,
     uint32_t *cnt = scratch + 2 * 256 * tiles;
     uint32_t *tile_counter = cnt + 8 * 256;
     cudaMemsetAsync(scratch, 0, sort_scratch_elems(n) * sizeof(uint32_t), s);
-    k_sort_counts<<<grid_for(n, SORT_BLOCK * 16, sm_count * 2), SORT_BLOCK, 0, s>>>(ka, n, cnt);
+    k_sort_counts<<<grid_for(n, SORT_BLOCK * 4, sm_count * 8), SORT_BLOCK, 0, s>>>(ka, n, cnt);
     cudaFuncSetAttribute(k_sort_pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sizeof(SweepShared));
     for (int pass = 0; pass < 8; ++pass) {

@@ -2,8 +2,9 @@
 // walk and the force computation in one kernel, interaction lists kept on
 // chip and evaluated on the fly; Eq. 1-2 of Sec. VI.A), and its adjoint.
 //
-// One warp owns one group of <= 64 targets.  Warps fetch groups from a
-// global counter, so the grid is persistent: one wave of resident warps.
+// One warp owns one group of <= 64 targets (or, at small N, one piece of a
+// group's targets).  Warps fetch groups from a global counter, so the grid
+// is persistent: one wave of resident warps.
 // The walk is breadth-first: each lane tests one cell of the current
 // frontier against the group's box (ballot + popc compaction replaces
 // Bonsai's shared-memory stacks):
@@ -21,8 +22,10 @@
 //
 // The traversal is one template (walk_group) shared by two evaluation
 // policies: the forward one (targets in lanes, list entries broadcast from
-// shared memory) and the adjoint one (list entries in lanes, targets
-// broadcast), which recomputes exactly the same lists.
+// shared memory; a lane's first two targets evaluated as one packed FP32
+// pair, bit-identical to the scalar arithmetic) and the adjoint one (list
+// entries in lanes, targets broadcast), which recomputes exactly the same
+// lists.
 #include "internal.cuh"
 #include "packed.cuh"
 
@@ -190,6 +193,66 @@ __device__ __forceinline__ void pp_one(const float4 s, int sid, int tid, float t
     az = fmaf(mr3, dz, az);
 }
 
+// pc_one and pp_one on the two targets of a packed pair: every packed
+// operation is the scalar one on each half, in the same order, so the two
+// targets get bit-identical results to the scalar code.  The potential is
+// accumulated negated (phn = -phi): phn + u tp and phn + m/r round exactly as
+// phi - u tp and phi - m/r do.
+__device__ __forceinline__ void pc_two(const float4 a, const float4 b, const float4 c, f32x2 tx,
+                                       f32x2 ty, f32x2 tz, f32x2 e2, f32x2 &ax, f32x2 &ay,
+                                       f32x2 &az, f32x2 &phn) {
+    const f32x2 rx = sub2(dup2(a.x), tx), ry = sub2(dup2(a.y), ty), rz = sub2(dup2(a.z), tz);
+    f32x2 s2 = fma2(rx, rx, e2);
+    s2 = fma2(ry, ry, s2);
+    s2 = fma2(rz, rz, s2);
+    float s0, s1;
+    u2(s2, s0, s1);
+    const f32x2 u = p2(rsqrtf(s0), rsqrtf(s1));
+    const f32x2 w = mul2(u, u);
+    const f32x2 bx = dup2(b.x), by = dup2(b.y), bz = dup2(b.z), bw = dup2(b.w);
+    const f32x2 cx = dup2(c.x), cy = dup2(c.y);
+    const f32x2 qx = fma2(bx, rx, fma2(bw, ry, mul2(cx, rz)));
+    const f32x2 qy = fma2(bw, rx, fma2(by, ry, mul2(cy, rz)));
+    const f32x2 qz = fma2(cx, rx, fma2(cy, ry, mul2(bz, rz)));
+    const f32x2 q = mul2(fma2(rx, qx, fma2(ry, qy, mul2(rz, qz))), w);
+    const f32x2 M = dup2(a.w);
+    const f32x2 tp = fma2(w, fma2(dup2(-0.5f), q, dup2(c.z)), M);
+    phn = fma2(u, tp, phn);
+    const f32x2 uw = mul2(u, w);
+    const f32x2 A = mul2(uw, fma2(w, fma2(dup2(-2.5f), q, dup2(c.w)), M));
+    const f32x2 B = mul2(uw, w);
+    ax = fma2(A, rx, ax);
+    ay = fma2(A, ry, ay);
+    az = fma2(A, rz, az);
+    ax = fma2(B, qx, ax);
+    ay = fma2(B, qy, ay);
+    az = fma2(B, qz, az);
+}
+
+template <bool MASK>
+__device__ __forceinline__ void pp_two(const float4 s, int sid, int id0, int id1, f32x2 tx,
+                                       f32x2 ty, f32x2 tz, f32x2 e2, f32x2 &ax, f32x2 &ay,
+                                       f32x2 &az, f32x2 &phn) {
+    const f32x2 dx = sub2(dup2(s.x), tx), dy = sub2(dup2(s.y), ty), dz = sub2(dup2(s.z), tz);
+    f32x2 r2 = fma2(dx, dx, e2);
+    r2 = fma2(dy, dy, r2);
+    r2 = fma2(dz, dz, r2);
+    float r0, r1;
+    u2(r2, r0, r1);
+    float i0 = rsqrtf(r0), i1 = rsqrtf(r1);
+    if (MASK) {
+        i0 = (sid == id0) ? 0.0f : i0;
+        i1 = (sid == id1) ? 0.0f : i1;
+    }
+    const f32x2 rinv = p2(i0, i1);
+    const f32x2 mr = mul2(dup2(s.w), rinv);
+    const f32x2 mr3 = mul2(mul2(mr, rinv), rinv);
+    phn = add2(phn, mr);
+    ax = fma2(mr3, dx, ax);
+    ay = fma2(mr3, dy, ay);
+    az = fma2(mr3, dz, az);
+}
+
 // Targets of one lane: K = 2 or 3 slots, chosen per group.  A group of c
 // targets is spread over T = ceil(c/K) lanes (slot k of lane tl holds
 // target tl + k*T), and the S = floor(32/T) copies of that layout each
@@ -253,7 +316,8 @@ struct Fp32Rings {
 template <int SELF>
 struct ForwardPolicy : Fp32Rings {
     int K, T, S, cp, tl, j0;
-    Targets t;
+    Targets t;  // slots 0 and 1 live packed in the pair below during the walk
+    f32x2 x01, y01, z01, ax01, ay01, az01, phn01, e2;
     float self[KMAX];
     float eps2;
 
@@ -280,6 +344,11 @@ struct ForwardPolicy : Fp32Rings {
             self[k] = h.w;
         }
         j0 = active ? cp : 1 << 30;  // first ring entry of this lane
+        x01 = p2(t.x[0], t.x[1]);
+        y01 = p2(t.y[0], t.y[1]);
+        z01 = p2(t.z[0], t.z[1]);
+        ax01 = ay01 = az01 = phn01 = 0ull;
+        e2 = dup2(eps2);
     }
 
     // entries [hb, hb + cnt) of the p-c ring (hb a multiple of 32, cnt <= 32)
@@ -289,17 +358,14 @@ struct ForwardPolicy : Fp32Rings {
 #pragma unroll 1
             for (int j = hb + j0; j < end; j += S) {
                 const float4 a = L.ca[j], b = L.cb[j], c = L.cc[j];
-#pragma unroll
-                for (int k = 0; k < 2; ++k)
-                    pc_one(a, b, c, t.x[k], t.y[k], t.z[k], eps2, t.ax[k], t.ay[k], t.az[k], t.ph[k]);
+                pc_two(a, b, c, x01, y01, z01, e2, ax01, ay01, az01, phn01);
             }
         } else {
 #pragma unroll 1
             for (int j = hb + j0; j < end; j += S) {
                 const float4 a = L.ca[j], b = L.cb[j], c = L.cc[j];
-#pragma unroll
-                for (int k = 0; k < 3; ++k)
-                    pc_one(a, b, c, t.x[k], t.y[k], t.z[k], eps2, t.ax[k], t.ay[k], t.az[k], t.ph[k]);
+                pc_two(a, b, c, x01, y01, z01, e2, ax01, ay01, az01, phn01);
+                pc_one(a, b, c, t.x[2], t.y[2], t.z[2], eps2, t.ax[2], t.ay[2], t.az[2], t.ph[2]);
             }
         }
     }
@@ -311,25 +377,29 @@ struct ForwardPolicy : Fp32Rings {
             for (int j = hb + j0; j < end; j += S) {
                 const float4 p = L.pp[j];
                 const int sid = L.pid[j];
-#pragma unroll
-                for (int k = 0; k < 2; ++k)
-                    pp_one<SELF == SELF_MASK>(p, sid, t.id[k], t.x[k], t.y[k], t.z[k], eps2, t.ax[k],
-                                              t.ay[k], t.az[k], t.ph[k]);
+                pp_two<SELF == SELF_MASK>(p, sid, t.id[0], t.id[1], x01, y01, z01, e2, ax01, ay01,
+                                          az01, phn01);
             }
         } else {
 #pragma unroll 1
             for (int j = hb + j0; j < end; j += S) {
                 const float4 p = L.pp[j];
                 const int sid = L.pid[j];
-#pragma unroll
-                for (int k = 0; k < 3; ++k)
-                    pp_one<SELF == SELF_MASK>(p, sid, t.id[k], t.x[k], t.y[k], t.z[k], eps2, t.ax[k],
-                                              t.ay[k], t.az[k], t.ph[k]);
+                pp_two<SELF == SELF_MASK>(p, sid, t.id[0], t.id[1], x01, y01, z01, e2, ax01, ay01,
+                                          az01, phn01);
+                pp_one<SELF == SELF_MASK>(p, sid, t.id[2], t.x[2], t.y[2], t.z[2], eps2, t.ax[2],
+                                          t.ay[2], t.az[2], t.ph[2]);
             }
         }
     }
 
     __device__ __forceinline__ void finish(const WalkArgs &A, uint32_t gf, uint32_t gc, int lane) {
+        u2(ax01, t.ax[0], t.ax[1]);
+        u2(ay01, t.ay[0], t.ay[1]);
+        u2(az01, t.az[0], t.az[1]);
+        u2(phn01, t.ph[0], t.ph[1]);
+        t.ph[0] = -t.ph[0];
+        t.ph[1] = -t.ph[1];
 #pragma unroll
         for (int k = 0; k < KMAX; ++k) {
             if (k >= K) break;
