@@ -45,8 +45,8 @@ if ROOT not in sys.path:
 # DRAM bytes (read + written) of one walk/force launch, from a one-pass ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum) of the benchmark
 # command, valid only for the walk source it was taken on (checked by hash).
-WALK_TRAFFIC = {"walk_cu_sha256": "aa770e6bc2b82ea78e672bc1213a34f8bed451ae4707c43099bff61da3b10f31",
-                "bytes": {"milky-way-2^23": 946.907904e6 + 458.898944e6}}
+WALK_TRAFFIC = {"walk_cu_sha256": "98b2c03c447ab3dc96d498df581b4de1ff729efc032949dce388e6116e0ebf44",
+                "bytes": {"milky-way-2^23": 811.230208e6 + 324.368640e6}}
 
 METRIC = "tree-force Tflop/s (23 flops/p-p + 65 flops/p-c, Sec. VI.A) per full KDK step, theta=0.4"
 UNIT = "Tflop/s"

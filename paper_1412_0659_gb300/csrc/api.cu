@@ -309,7 +309,7 @@ void bonsai_destroy(bonsai_ctx *c) {
     for (int k = 0; k < 2; ++k)
         if (c->stage[k]) cudaFreeHost(c->stage[k]);
     release(c->nd_first); release(c->nd_count); release(c->nd_child); release(c->nd_nchild);
-    release(c->nd_level); release(c->nd_parent); release(c->nd_scan); release(c->nd_arrive);
+    release(c->nd_level); release(c->nd_parent); release(c->nd_scan); release(c->nd_arrive); release(c->nd_bounds);
     release(c->nd_M); release(c->nd_com); release(c->nd_Q);
     release(c->cell_mac); release(c->cell_topo); release(c->cell_a); release(c->cell_b);
     release(c->cell_c);

@@ -38,6 +38,7 @@ __device__ __forceinline__ double from_order_key(long long k) {
 
 // cooperative octree build: threads per block, polls of a barrier wait
 constexpr int OCT_BLOCK = 256;
+constexpr int OCT_KEEP = 1 << 18;  // widest level whose child boundaries are kept between phases
 constexpr uint32_t OCT_SPINS = 1u << 22;
 
 // Device scalars written by kernels and read back in one copy.
@@ -115,6 +116,7 @@ struct bonsai_ctx {
     bgb::DBuf<uint32_t> nd_first, nd_count, nd_child, nd_nchild, nd_level, nd_parent;
     bgb::DBuf<uint32_t> nd_scan;     // octree build: per-block child counts
     bgb::DBuf<uint32_t> nd_arrive;   // one-launch upward pass: finished children per node
+    bgb::DBuf<uint32_t> nd_bounds;   // octree build: [7][OCT_KEEP] child boundaries of a level
     bgb::DBuf<double> nd_M;          // [nn]
     bgb::DBuf<double> nd_com;        // [3][nn]
     bgb::DBuf<double> nd_Q;          // [6][nn]

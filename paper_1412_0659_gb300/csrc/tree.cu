@@ -141,7 +141,7 @@ __device__ __forceinline__ uint32_t block_excl_sum(uint32_t v, uint32_t *total) 
 __global__ void __launch_bounds__(OCT_BLOCK) k_octree(
     const uint64_t *__restrict__ key, uint32_t n, uint32_t *first, uint32_t *count,
     uint32_t *child, uint32_t *nchild, uint32_t *level, uint32_t *parent, uint2 *topo,
-    uint32_t *__restrict__ flag, uint32_t cap, uint32_t *bsum, DevScalars *sc) {
+    uint32_t *__restrict__ flag, uint32_t cap, uint32_t *bsum, uint32_t *bnd, DevScalars *sc) {
     const uint32_t nb = gridDim.x, blk = blockIdx.x, tid = threadIdx.x;
     if (blk == 0 && tid == 0) {
         first[0] = 0;
@@ -157,7 +157,10 @@ __global__ void __launch_bounds__(OCT_BLOCK) k_octree(
         const uint32_t m = e - s;
         const uint32_t per = (m + nb - 1u) / nb;
         const uint32_t c0 = min(m, blk * per), c1 = min(m, c0 + per);
-        // A: child counts
+        // A: child counts (the boundaries kept for B when the level is small
+        // enough for the scratch: the searches' latency is what a small level
+        // costs)
+        const bool keep = m <= (uint32_t)OCT_KEEP;
         uint32_t mine = 0;
         for (uint32_t t = c0 + tid; t < c1; t += OCT_BLOCK) {
             const uint32_t i = s + t;
@@ -168,6 +171,10 @@ __global__ void __launch_bounds__(OCT_BLOCK) k_octree(
                 child_bounds(key, f, c, l, b);
 #pragma unroll
                 for (int d = 0; d < 8; ++d) nc += b[d + 1] > b[d];
+                if (keep) {
+#pragma unroll
+                    for (int d = 1; d < 8; ++d) bnd[(size_t)(d - 1) * OCT_KEEP + t] = b[d];
+                }
             }
             nchild[i] = nc;
             mine += nc;
@@ -215,7 +222,14 @@ __global__ void __launch_bounds__(OCT_BLOCK) k_octree(
                     child[i] = ch;
                     topo[i] = make_uint2(ch, nc);
                     uint32_t b[9];
-                    child_bounds(key, f, c, l, b);
+                    if (keep) {  // written by this thread in A
+                        b[0] = f;
+                        b[8] = f + c;
+#pragma unroll
+                        for (int d = 1; d < 8; ++d) b[d] = bnd[(size_t)(d - 1) * OCT_KEEP + t];
+                    } else {
+                        child_bounds(key, f, c, l, b);
+                    }
                     uint32_t k = ch, run = 0;
                     bool open = false;
 #pragma unroll
@@ -385,30 +399,48 @@ __device__ void leaf_moments(const double *__restrict__ pos, const double *__res
 
 // An internal node from its children by the parallel-axis rule.  The
 // children were written by other threads of this launch: read through L2.
+// The loops run over the eight possible children with the absent ones
+// masked, so that the loads of all children can be in flight at once; the
+// FP64 operations keep their order.
 __device__ void internal_moments(uint32_t c0, uint32_t nc, double *__restrict__ M,
                                  double *__restrict__ com, double *__restrict__ Q, int64_t nn,
                                  int64_t i) {
+    double Mk[8], X[8], Y[8], Z[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const bool h = (uint32_t)k < nc;
+        const uint32_t j = c0 + (h ? (uint32_t)k : 0u);
+        Mk[k] = h ? __ldcg(M + j) : 0.0;
+        X[k] = __ldcg(com + j);
+        Y[k] = __ldcg(com + nn + j);
+        Z[k] = __ldcg(com + 2 * nn + j);
+    }
     double Ms = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
-    for (uint32_t k = c0; k < c0 + nc; ++k) {
-        const double Mk = __ldcg(M + k);
-        Ms = __dadd_rn(Ms, Mk);
-        sx = __dadd_rn(sx, __dmul_rn(Mk, __ldcg(com + k)));
-        sy = __dadd_rn(sy, __dmul_rn(Mk, __ldcg(com + nn + k)));
-        sz = __dadd_rn(sz, __dmul_rn(Mk, __ldcg(com + 2 * nn + k)));
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        if ((uint32_t)k < nc) {
+            Ms = __dadd_rn(Ms, Mk[k]);
+            sx = __dadd_rn(sx, __dmul_rn(Mk[k], X[k]));
+            sy = __dadd_rn(sy, __dmul_rn(Mk[k], Y[k]));
+            sz = __dadd_rn(sz, __dmul_rn(Mk[k], Z[k]));
+        }
     }
     const double cx = __ddiv_rn(sx, Ms), cy = __ddiv_rn(sy, Ms), cz = __ddiv_rn(sz, Ms);
     double q[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    for (uint32_t k = c0; k < c0 + nc; ++k) {
-        const double Mk = __ldcg(M + k);
-        const double dx = __dsub_rn(__ldcg(com + k), cx), dy = __dsub_rn(__ldcg(com + nn + k), cy),
-                     dz = __dsub_rn(__ldcg(com + 2 * nn + k), cz);
-        const double mx = __dmul_rn(Mk, dx), my = __dmul_rn(Mk, dy);
-        q[0] = __dadd_rn(q[0], __dadd_rn(__ldcg(Q + k), __dmul_rn(mx, dx)));
-        q[1] = __dadd_rn(q[1], __dadd_rn(__ldcg(Q + nn + k), __dmul_rn(my, dy)));
-        q[2] = __dadd_rn(q[2], __dadd_rn(__ldcg(Q + 2 * nn + k), __dmul_rn(__dmul_rn(Mk, dz), dz)));
-        q[3] = __dadd_rn(q[3], __dadd_rn(__ldcg(Q + 3 * nn + k), __dmul_rn(mx, dy)));
-        q[4] = __dadd_rn(q[4], __dadd_rn(__ldcg(Q + 4 * nn + k), __dmul_rn(mx, dz)));
-        q[5] = __dadd_rn(q[5], __dadd_rn(__ldcg(Q + 5 * nn + k), __dmul_rn(my, dz)));
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        if ((uint32_t)k < nc) {
+            const uint32_t j = c0 + (uint32_t)k;
+            const double dx = __dsub_rn(X[k], cx), dy = __dsub_rn(Y[k], cy),
+                         dz = __dsub_rn(Z[k], cz);
+            const double mx = __dmul_rn(Mk[k], dx), my = __dmul_rn(Mk[k], dy);
+            q[0] = __dadd_rn(q[0], __dadd_rn(__ldcg(Q + j), __dmul_rn(mx, dx)));
+            q[1] = __dadd_rn(q[1], __dadd_rn(__ldcg(Q + nn + j), __dmul_rn(my, dy)));
+            q[2] = __dadd_rn(q[2], __dadd_rn(__ldcg(Q + 2 * nn + j), __dmul_rn(__dmul_rn(Mk[k], dz), dz)));
+            q[3] = __dadd_rn(q[3], __dadd_rn(__ldcg(Q + 3 * nn + j), __dmul_rn(mx, dy)));
+            q[4] = __dadd_rn(q[4], __dadd_rn(__ldcg(Q + 4 * nn + j), __dmul_rn(mx, dz)));
+            q[5] = __dadd_rn(q[5], __dadd_rn(__ldcg(Q + 5 * nn + j), __dmul_rn(my, dz)));
+        }
     }
     store_moments(M, com, Q, nn, i, Ms, cx, cy, cz, q);
 }
@@ -451,9 +483,10 @@ __global__ void __launch_bounds__(256) k_group_write(const uint32_t *__restrict_
 
 // Per group: the FP64 box of the members, its FP32 centre (nearest), the
 // centre's FP32 remainder, and the half-size rounded up to FP32.  A warp
-// takes 32 consecutive groups: for each, all lanes load its members and
+// takes GPW consecutive groups: for each, all lanes load its members and
 // reduce their minima and maxima; lane k keeps those of group k, and the
-// FP64 epilogue then runs once per lane for the 32 groups at a time.
+// FP64 epilogue then runs once per lane for the GPW groups at a time.
+template <int GPW>  // groups per warp: 32, or 1 when the groups are few (small N)
 __global__ void __launch_bounds__(256) k_group_box(const double *__restrict__ pos, int64_t n,
                                                    const uint32_t *__restrict__ gfirst,
                                                    uint32_t *__restrict__ gcount, int64_t ng,
@@ -461,11 +494,11 @@ __global__ void __launch_bounds__(256) k_group_box(const double *__restrict__ po
                                                    float4 *__restrict__ gbox,
                                                    float4 *__restrict__ ghalf,
                                                    float4 *__restrict__ glo) {
-    const int64_t g0 = ((blockIdx.x * 256ll + threadIdx.x) >> 5) * 32;
+    const int64_t g0 = ((blockIdx.x * 256ll + threadIdx.x) >> 5) * GPW;
     const int lane = threadIdx.x & 31;
     if (g0 >= ng) return;
     long long myn[3] = {0, 0, 0}, myx[3] = {0, 0, 0};
-    const int kend = (int)min((int64_t)32, ng - g0);
+    const int kend = (int)min((int64_t)GPW, ng - g0);
     for (int k = 0; k < kend; ++k) {
         const int64_t g = g0 + k;
         const uint32_t f = gfirst[g];
@@ -623,7 +656,8 @@ int build_octree(bonsai_ctx *c) {
     const int64_t widest = 8 * (n / (NLEAF + 1)) + 1;
     const int64_t blocks =
         std::min<int64_t>((int64_t)per_sm * c->sm_count, (widest + OCT_BLOCK - 1) / OCT_BLOCK);
-    if (ensure(c->nd_scan, (size_t)blocks)) return BONSAI_ENOMEM;
+    if (ensure(c->nd_scan, (size_t)blocks) || ensure(c->nd_bounds, (size_t)7 * OCT_KEEP))
+        return BONSAI_ENOMEM;
     for (int attempt = 0;; ++attempt) {
         BGB_CUDA(cudaMemsetAsync(c->grp_flag.p, 0, (n + 1) * sizeof(uint32_t), c->stream));
         // the status word may carry the input check's bit: cleared only
@@ -636,10 +670,10 @@ int build_octree(bonsai_ctx *c) {
         uint32_t *first = c->nd_first.p, *count = c->nd_count.p, *child = c->nd_child.p;
         uint32_t *nchild = c->nd_nchild.p, *level = c->nd_level.p, *parent = c->nd_parent.p;
         uint2 *topo = c->cell_topo.p;
-        uint32_t *flag = c->grp_flag.p, *bsum = c->nd_scan.p;
+        uint32_t *flag = c->grp_flag.p, *bsum = c->nd_scan.p, *bnd = c->nd_bounds.p;
         DevScalars *sc = c->dsc;
         void *args[] = {&key, &nn32, &first, &count, &child, &nchild, &level, &parent,
-                        &topo, &flag, &cap, &bsum, &sc};
+                        &topo, &flag, &cap, &bsum, &bnd, &sc};
         BGB_CUDA(cudaLaunchCooperativeKernel((const void *)k_octree, dim3((unsigned)blocks),
                                              dim3(OCT_BLOCK), args, 0, c->stream));
         c->launches += 1;
@@ -675,9 +709,14 @@ int build_groups(bonsai_ctx *c) {
         return BONSAI_ENOMEM;
     const uint32_t *gid = c->grp_flag.p + (n + 1);
     k_group_write<<<grid_for(n, 256), 256, 0, c->stream>>>(c->grp_flag.p, gid, n, c->grp_first.p);
-    k_group_box<<<grid_for((ng + 31) / 32 * 32, 256), 256, 0, c->stream>>>(
-        c->pos.p, n, c->grp_first.p, c->grp_count.p, ng, c->grp_centre.p, c->grp_box.p,
-        c->grp_half.p, c->grp_lo.p);
+    if (ng <= 16 * (int64_t)c->sm_count)  // few groups: a warp each
+        k_group_box<1><<<grid_for(ng * 32, 256), 256, 0, c->stream>>>(
+            c->pos.p, n, c->grp_first.p, c->grp_count.p, ng, c->grp_centre.p, c->grp_box.p,
+            c->grp_half.p, c->grp_lo.p);
+    else
+        k_group_box<32><<<grid_for((ng + 31) / 32 * 32, 256), 256, 0, c->stream>>>(
+            c->pos.p, n, c->grp_first.p, c->grp_count.p, ng, c->grp_centre.p, c->grp_box.p,
+            c->grp_half.p, c->grp_lo.p);
     c->launches += 2;
     return BONSAI_OK;
 }
