@@ -55,17 +55,18 @@ __device__ inline void child_bounds(const uint64_t *__restrict__ key, uint32_t f
         b[d + 1] = lo[d] + (key[lo[d]] < (base | ((uint64_t)(d + 1) << shift)) ? 1u : 0u);
 }
 
-// Grid-wide barrier of a cooperative launch (every block resident).  Each
-// thread fences its own writes, the block meets, and one thread arrives on
-// the counter; the last arrival resets it and advances the generation.  The
+// Grid-wide barrier of a cooperative launch (every block resident).  The
+// block meets, then one thread fences (cumulatively: the block's writes that
+// the meeting ordered before it) and arrives on the counter; the last
+// arrival resets it and advances the generation.  The
 // wait is bounded: after OCT_SPINS polls (a second or so), or as soon as
 // another block has given up, the block records ST_TIMEOUT and reports
 // failure, so every block's later barriers end too and the kernel returns.
 __device__ bool grid_barrier(DevScalars *sc) {
     __shared__ int ok;
-    __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
+        __threadfence();
         int good = 1;
         volatile uint32_t *gen = &sc->bar_gen;
         volatile int32_t *status = &sc->status;
@@ -462,9 +463,14 @@ __global__ void __launch_bounds__(128) k_upward(
     uint32_t node = (uint32_t)i;
     while (node != 0u) {
         const uint32_t p = parent[node];
-        __threadfence();  // this node's moments before the arrival
-        if (atomicAdd(arrive + p, 1u) != nchild[p] - 1u) break;
-        __threadfence();  // the siblings' moments after it
+        // one acquire-release arrival: this node's moments are released
+        // with it, and the last arrival acquires every sibling's
+        uint32_t before;
+        asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;"
+                     : "=r"(before)
+                     : "l"(arrive + p)
+                     : "memory");
+        if (before != nchild[p] - 1u) break;
         internal_moments(child[p], nchild[p], M, com, Q, nn, p);
         node = p;
     }
