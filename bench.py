@@ -45,8 +45,8 @@ if ROOT not in sys.path:
 # DRAM bytes (read + written) of one walk/force launch, from a one-pass ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum) of the benchmark
 # command, valid only for the walk source it was taken on (checked by hash).
-WALK_TRAFFIC = {"walk_cu_sha256": "98b2c03c447ab3dc96d498df581b4de1ff729efc032949dce388e6116e0ebf44",
-                "bytes": {"milky-way-2^23": 811.230208e6 + 324.368640e6}}
+WALK_TRAFFIC = {"walk_cu_sha256": "f48b2fd4198c74e17b7022a20c204bbc7592a3fbeceeac026c5794bba611388a",
+                "bytes": {"milky-way-2^23": 819.767040e6 + 327.900160e6}}
 
 METRIC = "tree-force Tflop/s (23 flops/p-p + 65 flops/p-c, Sec. VI.A) per full KDK step, theta=0.4"
 UNIT = "Tflop/s"
@@ -413,7 +413,7 @@ def run_ours(args):
             ts.append(i0.elapsed_time(i1))
         ics = {"model": "Sec. IV Milky Way: NFW halo 6.0e11, exponential disk 5.0e10, Hernquist bulge "
                         f"4.6e9 Msun; {int(gal.n_halo)} + {int(gal.n_disk)} + {int(gal.n_bulge)} particles",
-               "ms": min(ts), "particles_per_s": n / (min(ts) * 1e-3), "launches_per_call": 12,
+               "ms": min(ts), "particles_per_s": n / (min(ts) * 1e-3), "launches_per_call": 14,
                "what": "bonsai_galaxy_generate: Eddington tables, speed and disk tables, Philox sampling, "
                        "centre-of-mass shift; FP64 throughout"}
         del ipos, ivel, imass

@@ -77,7 +77,7 @@ struct WalkArgs {
     float *acc_c;  // caller order [3][n] or null
     float *pot_c;  // caller order [n] or null
     int accumulate;  // add to acc/pot instead of writing them
-    int parts;       // forward walk: pieces each group's targets are split into (1-8)
+    int parts;       // forward and adjoint walks: pieces each group's targets are split into (1-8)
     const uint32_t *id;
     int32_t *gnpp, *gnpc;
     // adjoint inputs / outputs (sorted order)
@@ -1216,17 +1216,22 @@ __global__ void __launch_bounds__(WALK_WARPS * 32, 4) k_walk_adjoint(const WalkA
     const int64_t gw = (int64_t)blockIdx.x * WALK_WARPS + wib;
     uint32_t *fa = A.frontier + gw * 2 * FCAP;
     uint32_t *fb = fa + FCAP;
+    // work item w: piece w % parts of group w / parts (as in k_walk)
     while (true) {
-        uint32_t g = 0;
-        if (lane == 0) g = atomicAdd(&A.sc->group_counter, 1u);
-        g = __shfl_sync(0xffffffffu, g, 0);
-        if (g >= A.ngroups) break;
+        uint32_t w = 0;
+        if (lane == 0) w = atomicAdd(&A.sc->group_counter, 1u);
+        w = __shfl_sync(0xffffffffu, w, 0);
+        const uint32_t parts = (uint32_t)A.parts;
+        if (w >= (uint32_t)A.ngroups * parts) break;
+        const uint32_t g = w / parts, piece = w - g * parts;
+        const uint32_t gc = A.gcount[g], per = (gc + parts - 1u) / parts, tf = piece * per;
+        if (tf >= gc) continue;
         AdjointPolicy pol;
         pol.cell_adj = A.cell_adj;
         pol.part_adj = A.part_adj;
         pol.nn = A.nn;
         pol.W = &scratch[wib];
-        walk_group(A, lists[wib], &targets[wib], pol, g, 0u, A.gcount[g], fa, fb, lane, lt);
+        walk_group(A, lists[wib], &targets[wib], pol, g, tf, min(per, gc - tf), fa, fb, lane, lt);
     }
 }
 
@@ -1416,7 +1421,9 @@ int walk_adjoint(bonsai_ctx *c, float eps, const float *lam, const float *mu, fl
     a.mu = mu;
     a.cell_adj = cell_adj;
     a.part_adj = part_adj;
-    k_walk_adjoint<<<launch_blocks((const void *)k_walk_adjoint, c), WALK_WARPS * 32, 0, c->stream>>>(a);
+    const int blocks = launch_blocks((const void *)k_walk_adjoint, c);
+    a.parts = walk_parts(c->n_groups, blocks);
+    k_walk_adjoint<<<blocks, WALK_WARPS * 32, 0, c->stream>>>(a);
     c->launches += 1;
     return cudaPeekAtLastError() == cudaSuccess ? BONSAI_OK : BONSAI_ECUDA;
 }
