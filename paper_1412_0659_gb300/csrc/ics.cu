@@ -124,10 +124,26 @@ __global__ void k_shapes(bonsai_galaxy g, double *rad) {
         row(rad, c == 0 ? RS2H : RS2B)[k] = h2 * C + 2.0 * h1 * C1 + h * C2;
         row(rad, c == 0 ? RFH_INT : RFB_INT)[k] = 4.0 * PI * r * r * r * s0;
     }
-    // the disk: 4 pi r^2 times its density averaged over the sphere, rho =
-    // Sigma0 e^{-R/R_d} sech^2(z/z0) / (2 z0) for R <= R_max, by Simpson's
-    // rule in the polar angle phi (R = r cos phi, z = r sin phi) on
-    // [acos(min(1, R_max/r)), asin(min(1, 40 z0/r))]
+}
+
+// Sum over the 32 lanes of a warp (every lane gets the total).
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// The disk: 4 pi r^2 times its density averaged over the sphere, rho =
+// Sigma0 e^{-R/R_d} sech^2(z/z0) / (2 z0) for R <= R_max, by Simpson's rule
+// in the polar angle phi (R = r cos phi, z = r sin phi) on
+// [acos(min(1, R_max/r)), asin(min(1, 40 z0/r))].  A warp per radius node,
+// its lanes taking every 32nd term.
+__global__ void k_disk_shell(bonsai_galaxy g, double *rad) {
+    const int k = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (k >= K) return;
+    const double dl = log(R_MAX / R_MIN) / (K - 1);
+    const double r = R_MIN * exp(dl * k);
     const double sig0 = disk_sigma0(g);
     const double hi = asin(fmin(1.0, IZ_TMAX * g.z0 / r));
     const double lo = acos(fmin(1.0, g.R_max / r));
@@ -135,16 +151,18 @@ __global__ void k_shapes(bonsai_galaxy g, double *rad) {
     if (hi > lo) {
         const double hp = (hi - lo) / SHELL_N;
         double acc = 0.0;
-        for (int j = 0; j <= SHELL_N; ++j) {
+        for (int j = lane; j <= SHELL_N; j += 32) {
             const double phi = lo + (hi - lo) * j / SHELL_N;
             const double cph = cos(phi);
             const double ch = cosh(r * sin(phi) / g.z0);
             acc += simpson_w(j, SHELL_N) * (sig0 * exp(-r * cph / g.R_d) / (2.0 * g.z0) / (ch * ch)) * cph;
         }
-        dM = 4.0 * PI * r * r * (hp / 3.0 * acc);
+        dM = 4.0 * PI * r * r * (hp / 3.0 * warp_sum(acc));
     }
-    row(rad, RDMD)[k] = dM;
-    row(rad, RFD_INT)[k] = r * dM;
+    if (lane == 0) {
+        row(rad, RDMD)[k] = dM;
+        row(rad, RFD_INT)[k] = r * dM;
+    }
 }
 
 // Exclusive scan of one double per thread over a block of 1024 threads.
@@ -399,19 +417,22 @@ __global__ void __launch_bounds__(EDD_WARPS * 32) k_speed_cdf(double *rad, doubl
 // The disk's vertical factor on the k grid k_j = j (40 / R_d) / VC_NK:
 // I(k z0) = int_0^inf sech^2(t) e^{-k z0 t} dt (the sech^2 layer's weight of
 // e^{-k|z|}; 1 for a thin disk), Simpson's rule on t in [0, 40].
+// A warp per k node, its lanes taking every 32nd term.
 __global__ void k_disk_vertical(bonsai_galaxy g, double *iz) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
     if (j > VC_NK) return;
     const double hk = VC_KMAX / g.R_d / VC_NK;
     const double kz = hk * j * g.z0;
     const double ht = IZ_TMAX / IZ_NT;
     double acc = 0.0;
-    for (int i = 0; i <= IZ_NT; ++i) {
+    for (int i = lane; i <= IZ_NT; i += 32) {
         const double t = IZ_TMAX * i / IZ_NT;
         const double ch = cosh(t);
         acc += simpson_w(i, IZ_NT) * (exp(-kz * t) / (ch * ch));
     }
-    iz[j] = ht / 3.0 * acc;
+    acc = warp_sum(acc);
+    if (lane == 0) iz[j] = ht / 3.0 * acc;
 }
 
 __device__ __forceinline__ double central(const double *y, int j, double h) {
@@ -447,23 +468,27 @@ __device__ __forceinline__ DiskRows disk_rows(double *disk) {
 // 2 pi G Sigma0 R_d^2 R int_0^inf k J1(kR) I(k z0) (1 + k^2 R_d^2)^{-3/2} dk
 // (the thin disk's Hankel form with e^{-k|z|} averaged over the layer),
 // Simpson's rule on k in [0, 40 / R_d].
+// A warp per radius, its lanes taking every 32nd term of the k integral.
 __global__ void k_disk_rotation(bonsai_galaxy g, const double *rad, const double *iz,
                                 double *disk) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
     if (j >= KD) return;
     const DiskRows D = disk_rows(disk);
     const double h = g.R_max / (KD - 1);
     const double s0 = g.M_disk / (2.0 * PI * g.R_d * g.R_d);
-    D.cdf[j] = j == KD - 1 ? 1.0 : disk_fraction(j * h / g.R_d) / disk_fraction(g.R_max / g.R_d);
     const double R = (j + 0.5) * h;
-    const double ms = sph_mass_at(rad, RMH, R) + sph_mass_at(rad, RMB, R);
     const double hk = VC_KMAX / g.R_d / VC_NK;
     double acc = 0.0;
-    for (int i = 0; i <= VC_NK; ++i) {
+    for (int i = lane; i <= VC_NK; i += 32) {
         const double k = hk * i;
         const double q = 1.0 + (k * g.R_d) * (k * g.R_d);
         acc += simpson_w(i, VC_NK) * (j1(R * k) * (k * iz[i] * (1.0 / (q * sqrt(q)))));
     }
+    acc = warp_sum(acc);
+    if (lane != 0) return;
+    D.cdf[j] = j == KD - 1 ? 1.0 : disk_fraction(j * h / g.R_d) / disk_fraction(g.R_max / g.R_d);
+    const double ms = sph_mass_at(rad, RMH, R) + sph_mass_at(rad, RMB, R);
     const double vd2 = 2.0 * PI * g.G * s0 * g.R_d * g.R_d * R * (hk / 3.0 * acc);
     const double v2 = g.G * ms / R + vd2;
     D.vc2[j] = v2;
@@ -735,13 +760,14 @@ int check(const bonsai_galaxy *g) {
 
 int build_tables(const bonsai_galaxy &g, IcsTables &t, cudaStream_t s) {
     k_shapes<<<(K + 255) / 256, 256, 0, s>>>(g, t.rad);
+    k_disk_shell<<<(K * 32 + 255) / 256, 256, 0, s>>>(g, t.rad);
     k_cumulative<<<3, SCAN_T, 0, s>>>(g, t.rad);
     k_profiles<<<(K + 255) / 256, 256, 0, s>>>(g, t.rad);
     k_potential<<<1, SCAN_T, 0, s>>>(g, t.rad);
     k_eddington<<<(2 * K + EDD_WARPS - 1) / EDD_WARPS, EDD_WARPS * 32, 0, s>>>(t.rad);
     k_speed_cdf<<<(2 * K + EDD_WARPS - 1) / EDD_WARPS, EDD_WARPS * 32, 0, s>>>(t.rad, t.vcdf);
-    k_disk_vertical<<<(VC_NK + 1 + 127) / 128, 128, 0, s>>>(g, t.iz);
-    k_disk_rotation<<<KD / 64, 64, 0, s>>>(g, t.rad, t.iz, t.disk);
+    k_disk_vertical<<<((VC_NK + 1) * 32 + 255) / 256, 256, 0, s>>>(g, t.iz);
+    k_disk_rotation<<<(KD * 32 + 255) / 256, 256, 0, s>>>(g, t.rad, t.iz, t.disk);
     k_disk_kappa<<<KD / 256, 256, 0, s>>>(g, t.disk);
     k_disk_kinematics<<<KD / 256, 256, 0, s>>>(g, t.disk);
     return cudaGetLastError() == cudaSuccess ? BONSAI_OK : BONSAI_ECUDA;
