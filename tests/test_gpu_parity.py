@@ -23,6 +23,15 @@ def _cases():
     out["coincident1500"] = (dup, np.full(1500, 1.0 / 1500), 0.01)
     mw = workloads.milky_way(30000, seed=77)
     out["milkyway30000"] = (mw.pos, mw.mass, 0.01)
+    # 118 clumps of 17 particles, 1e-5 across: each clump is a chain of
+    # single-child nodes down to the level that separates its particles,
+    # more nodes in all than the octree's first launch has room for.  The
+    # softening (0.5) keeps the pair forces inside a clump negligible: FP32
+    # coordinates relative to a group that spans several clumps resolve
+    # separations of 1e-5 only to about 1e-3.
+    centres = rng.uniform(-1, 1, (3, 118))
+    chains = (centres[:, :, None] + rng.normal(0, 1e-5, (3, 118, 17))).reshape(3, -1)
+    out["chains2006"] = (chains, rng.uniform(0.5, 1.5, chains.shape[1]), 0.5)
     return out
 
 
@@ -70,6 +79,18 @@ def test_multipoles_fp64(run):
     assert np.all(np.abs(gpu["com"] - mp["com"]) <= 1e-14 * L)
     side = mp["side"]
     assert np.all(np.abs(gpu["Q"] - mp["Q"]) <= 1e-13 * M * side * side + 1e-300)
+
+
+def test_node_storage_grows_for_deep_chains():
+    """The octree's first launch holds n/2 + 64 nodes; the clump chains need
+    more, so the build must report the overflow, grow its node arrays and
+    build again (the topology test checks the result against the oracle)."""
+    from gpu_helpers import gpu_run
+    pos, mass, eps = CASES["chains2006"]
+    gpu = gpu_run(pos, mass, theta=0.4, eps=eps)
+    assert gpu["stats"]["n_nodes"] > pos.shape[1] // 2 + 64
+    assert gpu["stats"]["depth"] >= 15
+    gpu["g"].close()
 
 
 def test_interaction_lists_match(run):
