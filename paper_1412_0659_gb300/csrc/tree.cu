@@ -492,7 +492,7 @@ __global__ void __launch_bounds__(256) k_group_write(const uint32_t *__restrict_
 // takes GPW consecutive groups: for each, all lanes load its members and
 // reduce their minima and maxima; lane k keeps those of group k, and the
 // FP64 epilogue then runs once per lane for the GPW groups at a time.
-template <int GPW>  // groups per warp: 32, or 1 when the groups are few (small N)
+template <int GPW>  // groups per warp: 32, 4 or 1, fewer when the groups are few
 __global__ void __launch_bounds__(256) k_group_box(const double *__restrict__ pos, int64_t n,
                                                    const uint32_t *__restrict__ gfirst,
                                                    uint32_t *__restrict__ gcount, int64_t ng,
@@ -715,12 +715,18 @@ int build_groups(bonsai_ctx *c) {
         return BONSAI_ENOMEM;
     const uint32_t *gid = c->grp_flag.p + (n + 1);
     k_group_write<<<grid_for(n, 256), 256, 0, c->stream>>>(c->grp_flag.p, gid, n, c->grp_first.p);
-    if (ng <= 16 * (int64_t)c->sm_count)  // few groups: a warp each
-        k_group_box<1><<<grid_for(ng * 32, 256), 256, 0, c->stream>>>(
+    // groups per warp: as many as still leave four warps per scheduler
+    const int64_t warps = 16 * (int64_t)c->sm_count;
+    if (ng / 32 >= warps)
+        k_group_box<32><<<grid_for((ng + 31) / 32 * 32, 256), 256, 0, c->stream>>>(
+            c->pos.p, n, c->grp_first.p, c->grp_count.p, ng, c->grp_centre.p, c->grp_box.p,
+            c->grp_half.p, c->grp_lo.p);
+    else if (ng / 4 >= warps)
+        k_group_box<4><<<grid_for((ng + 3) / 4 * 32, 256), 256, 0, c->stream>>>(
             c->pos.p, n, c->grp_first.p, c->grp_count.p, ng, c->grp_centre.p, c->grp_box.p,
             c->grp_half.p, c->grp_lo.p);
     else
-        k_group_box<32><<<grid_for((ng + 31) / 32 * 32, 256), 256, 0, c->stream>>>(
+        k_group_box<1><<<grid_for(ng * 32, 256), 256, 0, c->stream>>>(
             c->pos.p, n, c->grp_first.p, c->grp_count.p, ng, c->grp_centre.p, c->grp_box.p,
             c->grp_half.p, c->grp_lo.p);
     c->launches += 2;
