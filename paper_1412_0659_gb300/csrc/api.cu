@@ -181,8 +181,7 @@ static int rebuild_impl(bonsai_ctx *c, const double *pos, const double *mass, bo
     if (from_caller) {
         launch_gather_build(c, pos, mass, n);
     } else {
-        if (!scatter) launch_fix_ties(c, n);
-        launch_gather_step(c, n, scatter);
+        launch_gather_step(c, n, scatter);  // also puts equal-key runs in caller order
     }
     BGB_CUDA(cudaEventRecord(c->ev[1], c->stream));
     BGB_CUDA(cudaGetLastError());

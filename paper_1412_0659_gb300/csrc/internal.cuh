@@ -207,7 +207,6 @@ void exclusive_scan_u32(bonsai_ctx *c, const uint32_t *in, uint32_t *out, int64_
                         uint32_t *total_dev);
 void launch_gather_build(bonsai_ctx *c, const double *pos, const double *mass, int64_t n);
 void launch_gather_step(bonsai_ctx *c, int64_t n, bool exact);
-void launch_fix_ties(bonsai_ctx *c, int64_t n);
 // tree.cu
 int build_octree(bonsai_ctx *c);
 int build_groups(bonsai_ctx *c);

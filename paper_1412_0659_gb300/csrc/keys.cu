@@ -1,9 +1,10 @@
 // keys.cu -- bounding cube reduction and Peano-Hilbert keys (Sec. III.B.1:
 // the bounding box maps coordinates to PH keys; Fig. 2 shows the curve).
 //
-// Both kernels stream the FP64 SoA positions once (HBM-bound).  Every FP64
-// operation that feeds a key is an explicit round-to-nearest intrinsic so
-// the keys are bit-identical to any IEEE implementation of the same formula.
+// Both kernels stream the FP64 SoA positions once.  Every FP64 operation
+// that feeds a key is an explicit round-to-nearest intrinsic so the keys are
+// bit-identical to any IEEE implementation of the same formula; the Hilbert
+// transform runs as a table-driven state machine, two levels per lookup.
 #include <math.h>
 
 #include <climits>
@@ -152,6 +153,68 @@ __device__ inline uint32_t quantise(double x, double lo, double scale) {
     return (uint32_t)min(max(f, 0), (int)((1u << KEY_BITS) - 1u));
 }
 
+}  // namespace
+
+// Hilbert index of a 21-bit cell after J. Skilling, "Programming the Hilbert
+// curve" (AIP Conf. Proc. 707, 2004): the transpose form, then bit
+// interleaving with axis 0 most significant in each 3-bit digit.
+//
+// Evaluated as a finite-state machine over the levels, from the top.  At
+// each level Skilling's loop reads one bit per axis and then only inverts
+// the lower bits of axis 0 or swaps the lower bits of axis 0 with those of
+// axis i, the same for every lower bit; so the lower bits of the current
+// axes are always the original ones permuted (pi) and inverted (m), and the
+// final Gray step adds one bit of state, the parity P of the Gray code's
+// last axis above the level.  A state is (pi, m, P): 6 x 8 x 2 = 96 codes
+// (48 reachable).  With c_a = o_{pi(a)} ^ m_a the level's current bits (o
+// the original ones), the key digit is (g0 ^ P, g1 ^ P, g2 ^ P) with g0 =
+// c0, g1 = c0 ^ c1, g2 = c0 ^ c1 ^ c2; then P ^= g2, and for axis i = 0, 1,
+// 2: if c_i, m_0 is flipped, else (i > 0) the entries of axes 0 and i of
+// (pi, m) are swapped.
+namespace {
+
+// The six permutations of three axes, 2 bits per axis (pi(0) lowest).
+__device__ __forceinline__ uint32_t perm_code(int k) {
+    constexpr uint32_t P[6] = {0u | 1u << 2 | 2u << 4, 0u | 2u << 2 | 1u << 4,
+                               1u | 0u << 2 | 2u << 4, 1u | 2u << 2 | 0u << 4,
+                               2u | 0u << 2 | 1u << 4, 2u | 1u << 2 | 0u << 4};
+    return P[k];
+}
+
+// One level: state s = perm index * 16 + m * 2 + P, original bits o (axis a
+// in bit a) -> digit (3 bits) | next state << 3.
+__device__ uint32_t ph_level(uint32_t s, uint32_t o) {
+    uint32_t pi = perm_code((int)(s >> 4));
+    uint32_t m = (s >> 1) & 7u, P = s & 1u;
+    uint32_t c[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) c[a] = ((o >> ((pi >> (2 * a)) & 3u)) & 1u) ^ ((m >> a) & 1u);
+    const uint32_t g0 = c[0], g1 = c[0] ^ c[1], g2 = c[0] ^ c[1] ^ c[2];
+    const uint32_t digit = ((g0 ^ P) << 2) | ((g1 ^ P) << 1) | (g2 ^ P);
+    P ^= g2;
+    if (c[0]) m ^= 1u;
+#pragma unroll
+    for (int i = 1; i < 3; ++i) {
+        if (c[i]) {
+            m ^= 1u;
+        } else {  // swap axes 0 and i of pi and m
+            const uint32_t p0 = pi & 3u, pii = (pi >> (2 * i)) & 3u;
+            pi = (pi & ~(3u | (3u << (2 * i)))) | pii | (p0 << (2 * i));
+            const uint32_t m0 = m & 1u, mi = (m >> i) & 1u;
+            m = (m & ~(1u | (1u << i))) | mi | (m0 << i);
+        }
+    }
+    uint32_t k = 0;
+#pragma unroll
+    for (int j = 0; j < 6; ++j)
+        if (perm_code(j) == pi) k = (uint32_t)j;
+    return digit | ((k * 16u + m * 2u + P) << 3);
+}
+
+constexpr int PH_STATES = 96;
+
+}  // namespace
+
 // Spread the low 21 bits of v to every third bit of a 64-bit word.
 __device__ inline uint64_t spread3(uint32_t v) {
     uint64_t x = v & 0x1fffffu;
@@ -163,42 +226,42 @@ __device__ inline uint64_t spread3(uint32_t v) {
     return x;
 }
 
-}  // namespace
+// The machine's tables in shared memory: one level per entry (t1[s * 8 +
+// o]) and two levels per entry (t2[s * 64 + (o_high << 3 | o_low)] = 6
+// digit bits | next state << 6), built by each block from ph_level.
+struct PhTables {
+    uint16_t t1[PH_STATES * 8];
+    uint16_t t2[PH_STATES * 64];
+};
 
-// Hilbert index of a 21-bit cell after J. Skilling, "Programming the Hilbert
-// curve" (AIP Conf. Proc. 707, 2004): the transpose form, then bit
-// interleaving with axis 0 most significant in each 3-bit digit.  The Gray
-// step's running XOR is taken as a suffix-XOR scan of the last axis.
-__device__ __forceinline__ uint64_t ph_key(uint32_t x0, uint32_t x1, uint32_t x2) {
-#pragma unroll
-    for (uint32_t q = 1u << (KEY_BITS - 1); q > 1u; q >>= 1) {
-        const uint32_t p = q - 1u;
-        x0 = (x0 & q) ? (x0 ^ p) : x0;
-        {
-            uint32_t t = (x0 ^ x1) & p;
-            bool inv = (x1 & q) != 0u;
-            x0 = inv ? (x0 ^ p) : (x0 ^ t);
-            x1 = inv ? x1 : (x1 ^ t);
-        }
-        {
-            uint32_t t = (x0 ^ x2) & p;
-            bool inv = (x2 & q) != 0u;
-            x0 = inv ? (x0 ^ p) : (x0 ^ t);
-            x2 = inv ? x2 : (x2 ^ t);
-        }
+__device__ void ph_build(PhTables &T) {
+    for (int k = threadIdx.x; k < PH_STATES * 8; k += blockDim.x)
+        T.t1[k] = (uint16_t)ph_level((uint32_t)(k >> 3), (uint32_t)(k & 7));
+    __syncthreads();
+    for (int k = threadIdx.x; k < PH_STATES * 64; k += blockDim.x) {
+        const uint32_t s = (uint32_t)k >> 6, hi = ((uint32_t)k >> 3) & 7u, lo = (uint32_t)k & 7u;
+        const uint32_t e1 = T.t1[s * 8 + hi], e2 = T.t1[(e1 >> 3) * 8 + lo];
+        T.t2[k] = (uint16_t)((((e1 & 7u) << 3) | (e2 & 7u)) | ((e2 >> 3) << 6));
     }
-    x1 ^= x0;
-    x2 ^= x1;
-    uint32_t y = x2 >> 1;  // bit j of the mask = XOR of x2's bits above j
-    y ^= y >> 1;
-    y ^= y >> 2;
-    y ^= y >> 4;
-    y ^= y >> 8;
-    y ^= y >> 16;
-    x0 ^= y;
-    x1 ^= y;
-    x2 ^= y;
-    return (spread3(x0) << 2) | (spread3(x1) << 1) | spread3(x2);
+    __syncthreads();
+}
+
+// The key of cell (x0, x1, x2): the top level with t1, then ten pairs of
+// levels with t2, reading the original bits from the Morton interleaving
+// (axis a in bit a of each 3-bit group).
+__device__ __forceinline__ uint64_t ph_key(const PhTables &T, uint32_t x0, uint32_t x1,
+                                           uint32_t x2) {
+    const uint64_t mo = spread3(x0) | (spread3(x1) << 1) | (spread3(x2) << 2);
+    uint32_t e = T.t1[(uint32_t)(mo >> 60) & 7u];
+    uint64_t key = e & 7u;
+    uint32_t s = e >> 3;
+#pragma unroll
+    for (int l = 19; l > 0; l -= 2) {  // levels l and l - 1
+        e = T.t2[s * 64u + ((uint32_t)(mo >> (3 * (l - 1))) & 63u)];
+        key = (key << 6) | (e & 63u);
+        s = e >> 6;
+    }
+    return key;
 }
 
 namespace {
@@ -213,13 +276,15 @@ __global__ void __launch_bounds__(256) k_keys(const double *__restrict__ pos, in
                                               uint32_t *__restrict__ val,
                                               const uint32_t *__restrict__ id,
                                               uint32_t *__restrict__ inv) {
+    __shared__ PhTables T;
+    ph_build(T);
     const double lo0 = sc->lo[0], lo1 = sc->lo[1], lo2 = sc->lo[2], s = sc->scale;
     for (int64_t i = blockIdx.x * 256ll + threadIdx.x; i < n; i += (int64_t)gridDim.x * 256) {
         uint32_t q0 = quantise(pos[i], lo0, s);
         uint32_t q1 = quantise(pos[n + i], lo1, s);
         uint32_t q2 = quantise(pos[2 * n + i], lo2, s);
         const uint32_t o = id ? id[i] : (uint32_t)i;
-        key[o] = ph_key(q0, q1, q2);
+        key[o] = ph_key(T, q0, q1, q2);
         val[o] = o;
         if (id) inv[o] = (uint32_t)i;
     }
@@ -243,12 +308,12 @@ int launch_cube_keys_into(cudaStream_t s, int sm_count, const double *pos, const
     const int nb = grid_for(n, BOX_BLOCK * 4, cap);
     k_box_partial<<<nb, BOX_BLOCK, 0, s>>>(pos, mass, n, part);
     k_box_final<<<1, BOX_BLOCK, 0, s>>>(part, nb, dsc);
-    k_keys<<<grid_for(n, 256, sm_count * 16), 256, 0, s>>>(pos, n, dsc, key, val, nullptr, nullptr);
+    k_keys<<<grid_for(n, 256, sm_count * 4), 256, 0, s>>>(pos, n, dsc, key, val, nullptr, nullptr);
     return 3;
 }
 
 void launch_keys(bonsai_ctx *c, const double *pos, int64_t n, const uint32_t *id, uint32_t *inv) {
-    k_keys<<<grid_for(n, 256, c->sm_count * 16), 256, 0, c->stream>>>(pos, n, c->dsc, c->key.p,
+    k_keys<<<grid_for(n, 256, c->sm_count * 4), 256, 0, c->stream>>>(pos, n, c->dsc, c->key.p,
                                                                        c->val.p, id, inv);
     c->launches += 1;
 }

@@ -57,17 +57,28 @@ __global__ void __launch_bounds__(SORT_BLOCK) k_sort_counts(const uint64_t *__re
     __syncthreads();
     const int64_t stride = (int64_t)gridDim.x * SORT_BLOCK;
     const int64_t end = (n + 31) / 32 * 32;  // whole warps take part in the votes
-    for (int64_t i = (int64_t)blockIdx.x * SORT_BLOCK + threadIdx.x; i < end; i += stride) {
-        const bool valid = i < n;
-        const uint64_t k = valid ? kin[i] : 0ull;
+    constexpr int U = 4;  // keys loaded ahead, so that their loads overlap
+    for (int64_t i0 = (int64_t)blockIdx.x * SORT_BLOCK + threadIdx.x; i0 < end; i0 += U * stride) {
+        uint64_t ks[U];
+        bool vs[U];
 #pragma unroll
-        for (int p = 0; p < 8; ++p) {
-            const uint32_t d = valid ? (uint32_t)(k >> (8 * p)) & 255u : 256u;
-            const uint32_t d0 = __shfl_sync(0xffffffffu, d, 0);
-            if (__all_sync(0xffffffffu, d == d0)) {
-                if ((threadIdx.x & 31) == 0 && d0 < 256u) atomicAdd(&sc[p][d0], 32u);
-            } else if (d < 256u) {
-                atomicAdd(&sc[p][d], 1u);
+        for (int u = 0; u < U; ++u) {
+            const int64_t i = i0 + u * stride;
+            vs[u] = i < n;
+            ks[u] = vs[u] ? kin[i] : 0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (i0 + u * stride >= end) break;  // uniform within a warp
+#pragma unroll
+            for (int p = 0; p < 8; ++p) {
+                const uint32_t d = vs[u] ? (uint32_t)(ks[u] >> (8 * p)) & 255u : 256u;
+                const uint32_t d0 = __shfl_sync(0xffffffffu, d, 0);
+                if (__all_sync(0xffffffffu, d == d0)) {
+                    if ((threadIdx.x & 31) == 0 && d0 < 256u) atomicAdd(&sc[p][d0], 32u);
+                } else if (d < 256u) {
+                    atomicAdd(&sc[p][d], 1u);
+                }
             }
         }
     }
@@ -108,14 +119,19 @@ __global__ void __launch_bounds__(SORT_BLOCK, 3) k_sort_pass(const uint64_t *__r
     __syncthreads();
     const uint32_t tile = S.tile;
     const int64_t t0 = (int64_t)tile * SORT_TILE;
-    // 1. ranks within the warp's contiguous run (the keys are read again in
-    // step 3, from L2, rather than held in registers through the look-back)
+    // 1. ranks within the warp's contiguous run.  The digits of all rounds
+    // are loaded first, so that their loads are in flight together (the
+    // keys are read again in step 3, from L2, rather than held in registers
+    // through the look-back).
     uint32_t dr[ROUNDS];  // digit (bits 0-8, 256 = past the end) | rank in warp << 9
 #pragma unroll
     for (int r = 0; r < ROUNDS; ++r) {
         const int64_t i = t0 + warp * PER_WARP + r * 32 + lane;
-        const bool valid = i < n;
-        const uint32_t d = valid ? (uint32_t)(kin[i] >> shift) & 255u : 256u;
+        dr[r] = i < n ? (uint32_t)(kin[i] >> shift) & 255u : 256u;
+    }
+#pragma unroll
+    for (int r = 0; r < ROUNDS; ++r) {
+        const uint32_t d = dr[r];
         const uint32_t peers = __match_any_sync(0xffffffffu, d);
         const uint32_t prev = d < 256u ? S.wh[warp][d] : 0u;
         dr[r] = d | ((prev + __popc(peers & lt)) << 9);
@@ -318,15 +334,22 @@ __global__ void __launch_bounds__(256) k_gather_build(const double *__restrict__
 }
 
 // Re-sort of the context's state.  With inv (the exact path), perm holds the
-// caller index of each new slot and inv the old slot of each caller index;
-// without it, perm holds the old slot of each new slot and id_o the caller
-// index of each old slot.
+// caller index of each new slot and inv the old slot of each caller index.
+// Without it, perm holds the old slot of each new slot and id_o the caller
+// index of each old slot: the sort ran on (key, old slot) pairs in old-slot
+// order, so equal keys came out in old-slot order, and each slot of a run of
+// equal keys takes instead the run's element whose caller index has the
+// slot's rank in the run, which makes the order (key, caller index).  A run
+// longer than TIE_RUN_MAX is left alone and reported (ST_LONG_TIES): the
+// caller then sorts again by the exact path.
+constexpr int TIE_RUN_MAX = 32;
 __global__ void __launch_bounds__(256) k_gather_step(
     const double *__restrict__ pos_o, const double *__restrict__ vel_o,
     const double *__restrict__ mass_o, const uint32_t *__restrict__ inv,
-    const uint32_t *__restrict__ id_o, const uint32_t *__restrict__ perm, int64_t n,
-    double *__restrict__ pos, double *__restrict__ vel, double *__restrict__ mass,
-    uint32_t *__restrict__ id) {
+    const uint32_t *__restrict__ id_o, const uint32_t *__restrict__ perm,
+    const uint64_t *__restrict__ key, int64_t n, double *__restrict__ pos,
+    double *__restrict__ vel, double *__restrict__ mass, uint32_t *__restrict__ id,
+    int32_t *status) {
     for (int64_t i = blockIdx.x * 256ll + threadIdx.x; i < n; i += (int64_t)gridDim.x * 256) {
         uint32_t c, j;
         if (inv) {
@@ -334,6 +357,25 @@ __global__ void __launch_bounds__(256) k_gather_step(
             j = inv[c];
         } else {
             j = perm[i];
+            const uint64_t k = key[i];
+            if ((i > 0 && key[i - 1] == k) || (i + 1 < n && key[i + 1] == k)) {
+                int64_t s = i, e = i + 1;  // the run [s, e), looked for up to TIE_RUN_MAX + 1
+                while (s > 0 && e - s <= TIE_RUN_MAX && key[s - 1] == k) --s;
+                while (e < n && e - s <= TIE_RUN_MAX && key[e] == k) ++e;
+                if (e - s > TIE_RUN_MAX) {
+                    atomicOr(status, ST_LONG_TIES);
+                } else {
+                    for (int64_t a = s; a < e; ++a) {  // the element of rank i - s
+                        const uint32_t ca = id_o[perm[a]];
+                        int64_t r = 0;
+                        for (int64_t b = s; b < e; ++b) r += id_o[perm[b]] < ca ? 1 : 0;
+                        if (r == i - s) {
+                            j = perm[a];
+                            break;
+                        }
+                    }
+                }
+            }
             c = id_o[j];
         }
 #pragma unroll
@@ -343,38 +385,6 @@ __global__ void __launch_bounds__(256) k_gather_step(
         }
         mass[i] = mass_o[j];
         id[i] = c;
-    }
-}
-
-// Ties of the slot-order sort: the sort ran on (key, old slot) pairs in
-// old-slot order, so equal keys came out in old-slot order; each run of
-// equal keys is put in caller-index order (id: caller index of each old
-// slot), which makes the result the (key, caller index) order.  A run of
-// more than TIE_RUN_MAX pairs is left alone and reported (ST_LONG_TIES):
-// the caller then sorts again by the exact path.
-constexpr int TIE_RUN_MAX = 32;
-__global__ void __launch_bounds__(256) k_fix_ties(const uint64_t *__restrict__ key,
-                                                  uint32_t *__restrict__ val,
-                                                  const uint32_t *__restrict__ id, int64_t n,
-                                                  int32_t *status) {
-    for (int64_t i = blockIdx.x * 256ll + threadIdx.x; i < n; i += (int64_t)gridDim.x * 256) {
-        const uint64_t k = key[i];
-        if ((i > 0 && key[i - 1] == k) || i + 1 >= n || key[i + 1] != k) continue;
-        int64_t e = i + 2;  // [i, e): the run starting at i
-        while (e < n && e - i <= TIE_RUN_MAX && key[e] == k) ++e;
-        if (e - i > TIE_RUN_MAX) {
-            atomicOr(status, ST_LONG_TIES);
-            continue;
-        }
-        for (int64_t a = i + 1; a < e; ++a) {  // insertion sort by caller index
-            const uint32_t v = val[a], cv = id[v];
-            int64_t b = a - 1;
-            while (b >= i && id[val[b]] > cv) {
-                val[b + 1] = val[b];
-                --b;
-            }
-            val[b + 1] = v;
-        }
     }
 }
 
@@ -435,17 +445,10 @@ void launch_gather_build(bonsai_ctx *c, const double *pos, const double *mass, i
     c->launches += 1;
 }
 
-void launch_fix_ties(bonsai_ctx *c, int64_t n) {
-    k_fix_ties<<<grid_for(n, 256, c->sm_count * 16), 256, 0, c->stream>>>(c->key.p, c->val.p,
-                                                                         c->id.p, n,
-                                                                         &c->dsc->status);
-    c->launches += 1;
-}
-
 void launch_gather_step(bonsai_ctx *c, int64_t n, bool exact) {
     k_gather_step<<<grid_for(n, 256, c->sm_count * 16), 256, 0, c->stream>>>(
-        c->pos.p, c->vel.p, c->mass.p, exact ? c->inv_id.p : nullptr, c->id.p, c->val.p, n,
-        c->pos2.p, c->vel2.p, c->mass2.p, c->id2.p);
+        c->pos.p, c->vel.p, c->mass.p, exact ? c->inv_id.p : nullptr, c->id.p, c->val.p,
+        c->key.p, n, c->pos2.p, c->vel2.p, c->mass2.p, c->id2.p, &c->dsc->status);
     c->launches += 1;
     std::swap(c->pos, c->pos2);
     std::swap(c->vel, c->vel2);
