@@ -145,12 +145,18 @@ __global__ void __launch_bounds__(BOX_BLOCK) k_box_final(const BoxPartial *part,
 }
 
 // floor((x - lo) * scale) clamped to [0, 2^21 - 1], each FP64 step rounded
-// to nearest.  The conversion truncates toward zero and saturates (NaN gives
-// 0), which equals floor followed by the clamp: a negative product becomes
-// 0 or less either way, and a non-negative one truncates to its floor.
+// to nearest.  The floor and the clamp are taken on the bit pattern of the
+// product, on the integer pipes: negative values (and -0) and values below
+// 1 give 0, values of 2^21 or more give 2^21 - 1, and otherwise the
+// mantissa with its leading bit, shifted right by 52 minus the exponent, is
+// the integer part.  (A NaN, which the input check rejects, gives 2^21 - 1.)
 __device__ inline uint32_t quantise(double x, double lo, double scale) {
-    const int f = __double2int_rz(__dmul_rn(__dsub_rn(x, lo), scale));
-    return (uint32_t)min(max(f, 0), (int)((1u << KEY_BITS) - 1u));
+    const long long b = __double_as_longlong(__dmul_rn(__dsub_rn(x, lo), scale));
+    const int e = (int)((b >> 52) & 0x7ff) - 1023;
+    if (b < 0 || e < 0) return 0u;
+    if (e >= KEY_BITS) return (1u << KEY_BITS) - 1u;
+    const unsigned long long m = ((unsigned long long)b & 0xfffffffffffffull) | (1ull << 52);
+    return (uint32_t)(m >> (52 - e));
 }
 
 }  // namespace
