@@ -246,6 +246,10 @@ int forces_internal(bonsai_ctx *c, float theta, float eps, float *acc_c, float *
         c->have_forces = false;
         return BONSAI_EOVERFLOW;
     }
+    if (c->hsc->status & ST_TIMEOUT) {  // the walk order's sort gave up: forces incomplete
+        c->have_forces = false;
+        return BONSAI_ETIMEOUT;
+    }
     c->have_forces = true;
     c->last_theta = theta;
     c->last_eps = eps;
@@ -309,6 +313,7 @@ void bonsai_destroy(bonsai_ctx *c) {
         if (c->stage[k]) cudaFreeHost(c->stage[k]);
     release(c->nd_first); release(c->nd_count); release(c->nd_child); release(c->nd_nchild);
     release(c->nd_level); release(c->nd_parent); release(c->nd_scan); release(c->nd_arrive); release(c->nd_bounds);
+    release(c->grp_okey); release(c->grp_okey2); release(c->grp_order); release(c->grp_order2);
     release(c->nd_M); release(c->nd_com); release(c->nd_Q);
     release(c->cell_mac); release(c->cell_topo); release(c->cell_a); release(c->cell_b);
     release(c->cell_c);

@@ -136,6 +136,8 @@ struct bonsai_ctx {
     bgb::DBuf<float4> grp_half;      // {h_f.xyz (rounded up), 0}
     bgb::DBuf<float4> grp_lo;        // {c_lo.xyz, 0}: c = c_f + c_lo
     bgb::DBuf<int32_t> grp_npp, grp_npc;
+    bgb::DBuf<uint64_t> grp_okey, grp_okey2;  // walk order: sort keys of the groups
+    bgb::DBuf<uint32_t> grp_order, grp_order2;  // walk order: group indices, densest first
 
     // walk frontier scratch (per resident warp)
     bgb::DBuf<uint32_t> frontier;

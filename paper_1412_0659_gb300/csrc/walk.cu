@@ -66,6 +66,7 @@ struct WalkArgs {
     const float4 *body_hi, *body_lo;  // targets (the groups' particles)
     const float4 *src_hi, *src_lo;    // p-p sources (the tree's particles)
     const uint32_t *gfirst, *gcount;
+    const uint32_t *gorder;  // forward walk: the order in which groups are fetched (null: index order)
     const float4 *gbox, *ghalf, *glo;
     int64_t ngroups;
     int64_t n;
@@ -1198,7 +1199,8 @@ __global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(const WalkArgs A) {
         w = __shfl_sync(0xffffffffu, w, 0);
         const uint32_t parts = (uint32_t)A.parts;
         if (w >= (uint32_t)A.ngroups * parts) break;
-        const uint32_t g = w / parts, piece = w - g * parts;
+        const uint32_t gi = w / parts, piece = w - gi * parts;
+        const uint32_t g = A.gorder ? A.gorder[gi] : gi;
         const uint32_t gc = A.gcount[g], per = (gc + parts - 1u) / parts, tf = piece * per;
         if (tf >= gc) continue;
         ForwardPolicy<SELF> pol;
@@ -1283,6 +1285,7 @@ void fill_args(bonsai_ctx *c, float eps, WalkArgs &a) {
     a.src_lo = c->body_lo.p;
     a.accumulate = 0;
     a.parts = 1;
+    a.gorder = nullptr;
     a.gfirst = c->grp_first.p;
     a.gcount = c->grp_count.p;
     a.gbox = c->grp_box.p;
@@ -1353,6 +1356,37 @@ static int launch_blocks(const void *fn, bonsai_ctx *c) {
     return blocks < cap ? blocks : cap;
 }
 
+// Sort key of a group for the walk's fetch order: the largest FP32
+// half-size of its box (the bit pattern of a non-negative float orders as
+// the float).  64 particles in a small box sit in a dense region, whose
+// lists are the longest, so ascending keys take the costliest groups first
+// and leave the short walks for the end of the persistent grid's last wave.
+__global__ void __launch_bounds__(256) k_group_order_keys(const float4 *__restrict__ half,
+                                                          int64_t ng, uint64_t *__restrict__ key,
+                                                          uint32_t *__restrict__ val) {
+    for (int64_t g = blockIdx.x * 256ll + threadIdx.x; g < ng; g += (int64_t)gridDim.x * 256) {
+        const float4 h = half[g];
+        key[g] = (uint64_t)__float_as_uint(fmaxf(h.x, fmaxf(h.y, h.z)));
+        val[g] = (uint32_t)g;
+    }
+}
+
+// The groups in walk order (densest first) into grp_order; nullptr when the
+// order is not used (the walk then fetches groups in index order).
+static const uint32_t *walk_order(bonsai_ctx *c) {
+    const int64_t ng = c->n_groups;
+    if (ng < 2 || ensure(c->grp_okey, ng) || ensure(c->grp_okey2, ng) ||
+        ensure(c->grp_order, ng) || ensure(c->grp_order2, ng))
+        return nullptr;
+    k_group_order_keys<<<grid_for(ng, 256, c->sm_count * 4), 256, 0, c->stream>>>(
+        c->grp_half.p, ng, c->grp_okey.p, c->grp_order.p);
+    // the particle sort's scratch is free once the tree is built
+    c->launches += 1 + radix_sort_pairs_into(c->stream, c->sm_count, ng, c->grp_okey.p,
+                                             c->grp_okey2.p, c->grp_order.p, c->grp_order2.p,
+                                             c->hist.p, &c->dsc->status);
+    return c->grp_order.p;
+}
+
 // Pieces per group for the forward walk: when the groups are fewer than the
 // resident warps (small N), each group's targets are split over up to
 // MAX_PIECES warps that walk the same box (the same lists), so more warps
@@ -1373,6 +1407,13 @@ int walk_force(bonsai_ctx *c, float theta, float eps, float *acc_c, float *pot_c
     const void *fn = mask_self ? (const void *)k_walk<SELF_MASK> : (const void *)k_walk<SELF_SUB>;
     const int blocks = launch_blocks(fn, c);
     a.parts = walk_parts(c->n_groups, blocks);
+    // with a few groups per warp, densest first (the order changes no force):
+    // there the last wave's long walks are a visible tail (at 2^20, 7.5
+    // groups per warp: 7.49 -> 7.24 ms); with many groups per warp the tail
+    // is short and key order keeps neighbouring walks' records in L2 (at
+    // 2^23, 60 groups per warp: 61.60 ms in key order, 61.98 densest first)
+    const int64_t warps = (int64_t)blocks * WALK_WARPS;
+    if (a.parts == 1 && c->n_groups > warps && c->n_groups < 16 * warps) a.gorder = walk_order(c);
     cudaEventRecord(c->ev[8], c->stream);
     if (mask_self)
         k_walk<SELF_MASK><<<blocks, WALK_WARPS * 32, 0, c->stream>>>(a);
