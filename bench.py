@@ -45,8 +45,8 @@ if ROOT not in sys.path:
 # DRAM bytes (read + written) of one walk/force launch, from a one-pass ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum) of the benchmark
 # command, valid only for the walk source it was taken on (checked by hash).
-WALK_TRAFFIC = {"walk_cu_sha256": "f48b2fd4198c74e17b7022a20c204bbc7592a3fbeceeac026c5794bba611388a",
-                "bytes": {"milky-way-2^23": 819.767040e6 + 327.900160e6}}
+WALK_TRAFFIC = {"walk_cu_sha256": "78fb4ca7e02b789967878d0745c5cbe93a858430d70bf088fcb7f379e87f04b9",
+                "bytes": {"milky-way-2^23": 822.099712e6 + 327.303168e6}}
 
 METRIC = "tree-force Tflop/s (23 flops/p-p + 65 flops/p-c, Sec. VI.A) per full KDK step, theta=0.4"
 UNIT = "Tflop/s"
