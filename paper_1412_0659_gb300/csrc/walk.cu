@@ -66,7 +66,7 @@ struct WalkArgs {
     const float4 *body_hi, *body_lo;  // targets (the groups' particles)
     const float4 *src_hi, *src_lo;    // p-p sources (the tree's particles)
     const uint32_t *gfirst, *gcount;
-    const uint32_t *gorder;  // forward walk: the order in which groups are fetched (null: index order)
+    const uint32_t *gorder;  // forward and adjoint walks: the order of fetching groups (null: index order)
     const float4 *gbox, *ghalf, *glo;
     int64_t ngroups;
     int64_t n;
@@ -1225,7 +1225,8 @@ __global__ void __launch_bounds__(WALK_WARPS * 32, 4) k_walk_adjoint(const WalkA
         w = __shfl_sync(0xffffffffu, w, 0);
         const uint32_t parts = (uint32_t)A.parts;
         if (w >= (uint32_t)A.ngroups * parts) break;
-        const uint32_t g = w / parts, piece = w - g * parts;
+        const uint32_t gi = w / parts, piece = w - gi * parts;
+        const uint32_t g = A.gorder ? A.gorder[gi] : gi;
         const uint32_t gc = A.gcount[g], per = (gc + parts - 1u) / parts, tf = piece * per;
         if (tf >= gc) continue;
         AdjointPolicy pol;
@@ -1387,6 +1388,17 @@ static const uint32_t *walk_order(bonsai_ctx *c) {
     return c->grp_order.p;
 }
 
+// With a few groups per warp, densest first (the order changes no result):
+// there the last wave's long walks are a visible tail (at 2^20, 7.5 groups
+// per warp: 7.49 -> 7.24 ms); with many groups per warp the tail is short
+// and key order keeps neighbouring walks' records in L2 (at 2^23, 60 groups
+// per warp: 61.60 ms in key order, 61.98 densest first).
+static const uint32_t *walk_order_if_useful(bonsai_ctx *c, int parts, int blocks) {
+    const int64_t warps = (int64_t)blocks * WALK_WARPS;
+    if (parts == 1 && c->n_groups > warps && c->n_groups < 16 * warps) return walk_order(c);
+    return nullptr;
+}
+
 // Pieces per group for the forward walk: when the groups are fewer than the
 // resident warps (small N), each group's targets are split over up to
 // MAX_PIECES warps that walk the same box (the same lists), so more warps
@@ -1407,13 +1419,7 @@ int walk_force(bonsai_ctx *c, float theta, float eps, float *acc_c, float *pot_c
     const void *fn = mask_self ? (const void *)k_walk<SELF_MASK> : (const void *)k_walk<SELF_SUB>;
     const int blocks = launch_blocks(fn, c);
     a.parts = walk_parts(c->n_groups, blocks);
-    // with a few groups per warp, densest first (the order changes no force):
-    // there the last wave's long walks are a visible tail (at 2^20, 7.5
-    // groups per warp: 7.49 -> 7.24 ms); with many groups per warp the tail
-    // is short and key order keeps neighbouring walks' records in L2 (at
-    // 2^23, 60 groups per warp: 61.60 ms in key order, 61.98 densest first)
-    const int64_t warps = (int64_t)blocks * WALK_WARPS;
-    if (a.parts == 1 && c->n_groups > warps && c->n_groups < 16 * warps) a.gorder = walk_order(c);
+    a.gorder = walk_order_if_useful(c, a.parts, blocks);
     cudaEventRecord(c->ev[8], c->stream);
     if (mask_self)
         k_walk<SELF_MASK><<<blocks, WALK_WARPS * 32, 0, c->stream>>>(a);
@@ -1464,6 +1470,7 @@ int walk_adjoint(bonsai_ctx *c, float eps, const float *lam, const float *mu, fl
     a.part_adj = part_adj;
     const int blocks = launch_blocks((const void *)k_walk_adjoint, c);
     a.parts = walk_parts(c->n_groups, blocks);
+    a.gorder = walk_order_if_useful(c, a.parts, blocks);
     k_walk_adjoint<<<blocks, WALK_WARPS * 32, 0, c->stream>>>(a);
     c->launches += 1;
     return cudaPeekAtLastError() == cudaSuccess ? BONSAI_OK : BONSAI_ECUDA;
