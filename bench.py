@@ -45,8 +45,8 @@ if ROOT not in sys.path:
 # DRAM bytes (read + written) of one walk/force launch, from a one-pass ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum) of the benchmark
 # command, valid only for the walk source it was taken on (checked by hash).
-WALK_TRAFFIC = {"walk_cu_sha256": "78fb4ca7e02b789967878d0745c5cbe93a858430d70bf088fcb7f379e87f04b9",
-                "bytes": {"milky-way-2^23": 822.099712e6 + 327.303168e6}}
+WALK_TRAFFIC = {"walk_cu_sha256": "f3e50b2961f83dc556f74d353fdd631929d31e752f92fb8591f1e539ffa6231e",
+                "bytes": {"milky-way-2^23": 822.408192e6 + 327.783424e6}}
 
 METRIC = "tree-force Tflop/s (23 flops/p-p + 65 flops/p-c, Sec. VI.A) per full KDK step, theta=0.4"
 UNIT = "Tflop/s"
