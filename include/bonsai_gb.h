@@ -471,9 +471,9 @@ const char *bonsai_strerror(int code);
  * when another allocator already holds nearly all device memory; the first
  * call then returns ECUDA.  Once placed, the array stays on the device
  * until the process exits.  The first call on a device also looks up the
- * array's device address (with the device current) and caches it.  No
- * call can be captured into a CUDA graph: each one copies its status to
- * host memory and waits for the stream.  Every call on a device shares the same array, so calls whose
+ * array's device address (with the device current) and caches it; make
+ * that first call on each device before any stream capture begins.  Every
+ * call on a device shares the same array, so calls whose
  * work overlaps on the GPU (different streams or threads without ordering)
  * race and must not be issued; calls on one stream are ordered and safe.
  *
